@@ -1,0 +1,252 @@
+"""FP64 CPU oracle for the batched small-matrix operations (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA
+library: the arithmetic lives in ``glass_oracle.c`` (plain loops, FP64), and
+this module only marshals numpy arrays into it through ctypes.
+
+Every array is a flat, C-contiguous numpy buffer laid out column-major per
+problem, exactly as the device library stores its operands.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "glass_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
+_I = ctypes.POINTER(ctypes.c_int)
+_int = ctypes.c_int
+_ll = ctypes.c_longlong
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        sig = {
+            "oracle_set_threads": (None, [_int]),
+            "oracle_max_threads": (_int, []),
+            "oracle_gemm_f64": (None, [_int, _int, _int, _D, _int, _ll, _D, _int, _ll,
+                                       _D, _int, _ll, _int]),
+            "oracle_potrf_f64": (None, [_int, _D, _int, _ll, _I, _int]),
+            "oracle_trsm_f64": (None, [_int, _int, _D, _int, _ll, _D, _int, _ll, _int]),
+            "oracle_potrs_f64": (None, [_int, _int, _D, _int, _ll, _D, _int, _ll, _int]),
+            "oracle_posv_f64": (None, [_int, _int, _D, _int, _ll, _D, _int, _ll, _I, _int]),
+            "oracle_getrf_f64": (None, [_int, _D, _int, _ll, _I, _I, _D, _int]),
+            "oracle_getrf_f32": (None, [_int, _F, _int, _ll, _I, _I, _D, _int]),
+            "oracle_getrs_f64": (None, [_int, _int, _D, _int, _ll, _I, _D, _int, _ll, _int]),
+            "oracle_getrf_getrs_f64": (None, [_int, _int, _D, _int, _ll, _I, _D, _int, _ll,
+                                              _I, _int]),
+            "oracle_rot3_compose_f64": (None, [_int, _D, _ll, _D, _ll, _int]),
+            "oracle_se3_apply_f64": (None, [_int, _D, _ll, _int, _D, _ll, _D, _ll, _int]),
+            "oracle_mlp_nparams": (_ll, [_int, _int, _int]),
+            "oracle_mlp_fwd_f64": (None, [_int, _int, _int, _D, _int, _D, _D, _D, _D]),
+            "oracle_mlp_loss_grad_f64": (ctypes.c_double, [_int, _int, _int, _D, _int, _D,
+                                                           _D, _D, _D]),
+            "oracle_adam_step_f64": (None, [_ll, _D, _D, _D, _D, _int, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _dp(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _fp(a):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_F)
+
+
+def _ip(a):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64).copy()
+
+
+def set_threads(t: int) -> None:
+    _load().oracle_set_threads(int(t))
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+# ---------------------------------------------------------------- operations
+def gemm(m, n, k, A, B, batch, lda=None, ldb=None, ldc=None, sA=None, sB=None, sC=None):
+    lda = m if lda is None else lda
+    ldb = k if ldb is None else ldb
+    ldc = m if ldc is None else ldc
+    sA = lda * k if sA is None else sA
+    sB = ldb * n if sB is None else sB
+    sC = ldc * n if sC is None else sC
+    A = _f64(A)
+    B = _f64(B)
+    C = np.zeros(max(1, sC * batch), dtype=np.float64)
+    _load().oracle_gemm_f64(m, n, k, _dp(A), lda, sA, _dp(B), ldb, sB, _dp(C), ldc, sC, batch)
+    return C
+
+
+def potrf(n, A, batch, lda=None, sA=None):
+    lda = n if lda is None else lda
+    sA = lda * n if sA is None else sA
+    L = _f64(A)
+    info = np.zeros(max(1, batch), dtype=np.int32)
+    _load().oracle_potrf_f64(n, _dp(L), lda, sA, _ip(info), batch)
+    return L, info[:batch]
+
+
+def trsm(n, nrhs, L, B, batch, lda=None, sA=None, ldb=None, sB=None):
+    lda = n if lda is None else lda
+    sA = lda * n if sA is None else sA
+    ldb = n if ldb is None else ldb
+    sB = ldb * nrhs if sB is None else sB
+    X = _f64(B)
+    _load().oracle_trsm_f64(n, nrhs, _dp(_f64(L)), lda, sA, _dp(X), ldb, sB, batch)
+    return X
+
+
+def potrs(n, nrhs, L, B, batch, lda=None, sA=None, ldb=None, sB=None):
+    lda = n if lda is None else lda
+    sA = lda * n if sA is None else sA
+    ldb = n if ldb is None else ldb
+    sB = ldb * nrhs if sB is None else sB
+    X = _f64(B)
+    _load().oracle_potrs_f64(n, nrhs, _dp(_f64(L)), lda, sA, _dp(X), ldb, sB, batch)
+    return X
+
+
+def posv(n, nrhs, A, B, batch, lda=None, sA=None, ldb=None, sB=None):
+    lda = n if lda is None else lda
+    sA = lda * n if sA is None else sA
+    ldb = n if ldb is None else ldb
+    sB = ldb * nrhs if sB is None else sB
+    L = _f64(A)
+    X = _f64(B)
+    info = np.zeros(max(1, batch), dtype=np.int32)
+    _load().oracle_posv_f64(n, nrhs, _dp(L), lda, sA, _dp(X), ldb, sB, _ip(info), batch)
+    return L, X, info[:batch]
+
+
+def getrf(n, A, batch, lda=None, sA=None, precision="f64"):
+    """Returns (LU, ipiv[batch*n], info[batch], gap[batch])."""
+    lda = n if lda is None else lda
+    sA = lda * n if sA is None else sA
+    ipiv = np.zeros(max(1, batch * n), dtype=np.int32)
+    info = np.zeros(max(1, batch), dtype=np.int32)
+    gap = np.zeros(max(1, batch), dtype=np.float64)
+    if precision == "f64":
+        LU = _f64(A)
+        _load().oracle_getrf_f64(n, _dp(LU), lda, sA, _ip(ipiv), _ip(info), _dp(gap), batch)
+    elif precision == "f32":
+        LU = np.ascontiguousarray(A, dtype=np.float32).copy()
+        _load().oracle_getrf_f32(n, _fp(LU), lda, sA, _ip(ipiv), _ip(info), _dp(gap), batch)
+    else:
+        raise ValueError(precision)
+    return LU, ipiv[:batch * n], info[:batch], gap[:batch]
+
+
+def getrs(n, nrhs, LU, ipiv, B, batch, lda=None, sA=None, ldb=None, sB=None):
+    lda = n if lda is None else lda
+    sA = lda * n if sA is None else sA
+    ldb = n if ldb is None else ldb
+    sB = ldb * nrhs if sB is None else sB
+    X = _f64(B)
+    piv = np.ascontiguousarray(ipiv, dtype=np.int32)
+    _load().oracle_getrs_f64(n, nrhs, _dp(_f64(LU)), lda, sA, _ip(piv), _dp(X), ldb, sB, batch)
+    return X
+
+
+def getrf_getrs(n, nrhs, A, B, batch, lda=None, sA=None, ldb=None, sB=None):
+    lda = n if lda is None else lda
+    sA = lda * n if sA is None else sA
+    ldb = n if ldb is None else ldb
+    sB = ldb * nrhs if sB is None else sB
+    LU = _f64(A)
+    X = _f64(B)
+    ipiv = np.zeros(max(1, batch * n), dtype=np.int32)
+    info = np.zeros(max(1, batch), dtype=np.int32)
+    _load().oracle_getrf_getrs_f64(n, nrhs, _dp(LU), lda, sA, _ip(ipiv), _dp(X), ldb, sB,
+                                   _ip(info), batch)
+    return LU, ipiv[:batch * n], X, info[:batch]
+
+
+def rot3_compose(chain, Rs, batch, sRs=None, sR=9):
+    sRs = 9 * chain if sRs is None else sRs
+    R = np.zeros(max(1, sR * batch), dtype=np.float64)
+    _load().oracle_rot3_compose_f64(chain, _dp(_f64(Rs)), sRs, _dp(R), sR, batch)
+    return R
+
+
+def se3_apply(chain, T, npts, P, batch, sT=None, sP=None, sQ=None):
+    sT = 16 * chain if sT is None else sT
+    sP = 3 * npts if sP is None else sP
+    sQ = 3 * npts if sQ is None else sQ
+    Q = np.zeros(max(1, sQ * batch), dtype=np.float64)
+    _load().oracle_se3_apply_f64(chain, _dp(_f64(T)), sT, npts, _dp(_f64(P)), sP, _dp(Q),
+                                 sQ, batch)
+    return Q
+
+
+# ---------------------------------------------------------------- cost model
+def mlp_nparams(din, h, dout):
+    return int(_load().oracle_mlp_nparams(din, h, dout))
+
+
+def mlp_fwd(din, h, dout, w, X):
+    X = _f64(X)
+    rows = X.size // din
+    Y = np.zeros(rows * dout, dtype=np.float64)
+    _load().oracle_mlp_fwd_f64(din, h, dout, _dp(_f64(w)), rows, _dp(X), _dp(Y), None, None)
+    return Y.reshape(rows, dout)
+
+
+def mlp_loss_grad(din, h, dout, w, X, T, M):
+    X = _f64(X)
+    rows = X.size // din
+    g = np.zeros(mlp_nparams(din, h, dout), dtype=np.float64)
+    loss = _load().oracle_mlp_loss_grad_f64(din, h, dout, _dp(_f64(w)), rows, _dp(X),
+                                            _dp(_f64(T)), _dp(_f64(M)), _dp(g))
+    return float(loss), g
+
+
+def adam_step(w, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In place on w, m, v (float64 contiguous arrays)."""
+    _load().oracle_adam_step_f64(w.size, _dp(w), _dp(_f64(g)), _dp(m), _dp(v), int(t), lr,
+                                 b1, b2, eps)

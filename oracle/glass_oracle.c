@@ -1,0 +1,522 @@
+/*
+ * glass_oracle.c -- plain, slow, obviously-correct FP64 reference for the
+ * batched small-matrix operations of GLASS (arxiv 2609.28179).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The CUDA library
+ * shares no code, header, table or helper with this file, and this file
+ * includes nothing from it.
+ *
+ * Conventions (shared by contract, not by code, with the device library):
+ *   - every matrix is column-major: element (i,j) of problem b lives at
+ *     X[b*sX + j*ldX + i];
+ *   - Cholesky works on the lower triangle only; the strict upper triangle is
+ *     neither read nor written (LAPACK uplo='L');
+ *   - info[b] = 0 on success, j+1 when column j is the first that fails
+ *     (LAPACK convention);
+ *   - ipiv is 0-based with sequential-swap semantics: at step j rows j and
+ *     ipiv[j] were exchanged (the convention of scipy.linalg.lu_factor).
+ *
+ * Every routine is the textbook definition of the operation, with no
+ * blocking, fusion or reordering.  The batch loop is the only parallel loop
+ * (OpenMP), so results do not depend on the thread count.
+ *
+ * The paper names the operation classes (Sec. III-B: BLAS L1-L3, triangular
+ * and symmetric updates, factorizations, linear solves; SO(3)/SE(3) maps) and
+ * the measured POTRF/POSV/GEMM families (Sec. IV-A, IV-D); it prints no
+ * algorithm listing, so each routine below is the standard definition.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <string.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 0; /* 0 = OpenMP default */
+
+void oracle_set_threads(int t) { g_threads = t; }
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+#define OMP_FOR _Pragma("omp parallel for schedule(static) num_threads(oracle_max_threads())")
+
+/* ------------------------------------------------------------------------ */
+/* GEMM  C = A * B   (Sec. III-B "BLAS L1-L3"; Sec. IV-D GEMM)              */
+/* A is m x k, B is k x n, C is m x n; c_ij = sum_l a_il b_lj.               */
+/* ------------------------------------------------------------------------ */
+void oracle_gemm_f64(int m, int n, int k,
+                     const double *A, int lda, long long sA,
+                     const double *B, int ldb, long long sB,
+                     double *C, int ldc, long long sC, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *a = A + (long long)b * sA;
+        const double *bb = B + (long long)b * sB;
+        double *c = C + (long long)b * sC;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < k; ++l)
+                    s += a[l * lda + i] * bb[j * ldb + l];
+                c[j * ldc + i] = s;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* POTRF  A = L L^T, lower, in place  (Sec. III-B factorizations; POTRF is    */
+/* one of the measured destructive ops of Sec. IV-A).                        */
+/*   for j: d = a_jj - sum_{k<j} l_jk^2 ; d <= 0 or NaN -> info = j+1, stop  */
+/*          l_jj = sqrt(d) ; l_ij = (a_ij - sum_{k<j} l_ik l_jk) / l_jj      */
+/* ------------------------------------------------------------------------ */
+static int potrf_one(int n, double *a, int lda)
+{
+    for (int j = 0; j < n; ++j) {
+        double d = a[j * lda + j];
+        for (int k = 0; k < j; ++k)
+            d -= a[k * lda + j] * a[k * lda + j];
+        if (!(d > 0.0))            /* also catches NaN */
+            return j + 1;
+        double ljj = sqrt(d);
+        a[j * lda + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double s = a[j * lda + i];
+            for (int k = 0; k < j; ++k)
+                s -= a[k * lda + i] * a[k * lda + j];
+            a[j * lda + i] = s / ljj;
+        }
+    }
+    return 0;
+}
+
+void oracle_potrf_f64(int n, double *A, int lda, long long sA, int *info, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b)
+        info[b] = potrf_one(n, A + (long long)b * sA, lda);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Triangular solves with the lower factor L (Sec. III-B "triangular ...     */
+/* updates", "linear solves").                                              */
+/*   forward : y_i = (b_i - sum_{k<i} l_ik y_k) / l_ii                       */
+/*   backward: x_i = (y_i - sum_{k>i} l_ki x_k) / l_ii   (solves L^T x = y)   */
+/* ------------------------------------------------------------------------ */
+static void forward_lower(int n, const double *l, int lda, double *x, int unit)
+{
+    for (int i = 0; i < n; ++i) {
+        double s = x[i];
+        for (int k = 0; k < i; ++k)
+            s -= l[k * lda + i] * x[k];
+        x[i] = unit ? s : s / l[i * lda + i];
+    }
+}
+
+static void backward_lower_transposed(int n, const double *l, int lda, double *x)
+{
+    for (int i = n - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int k = i + 1; k < n; ++k)
+            s -= l[i * lda + k] * x[k];
+        x[i] = s / l[i * lda + i];
+    }
+}
+
+/* TRSM: left side, lower, no transpose, non-unit diagonal: L X = B, B <- X. */
+void oracle_trsm_f64(int n, int nrhs, const double *L, int lda, long long sA,
+                     double *B, int ldb, long long sB, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b)
+        for (int c = 0; c < nrhs; ++c)
+            forward_lower(n, L + (long long)b * sA, lda,
+                          B + (long long)b * sB + (long long)c * ldb, 0);
+}
+
+/* POTRS: L L^T X = B with the factor from POTRF, B <- X. */
+void oracle_potrs_f64(int n, int nrhs, const double *L, int lda, long long sA,
+                      double *B, int ldb, long long sB, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b)
+        for (int c = 0; c < nrhs; ++c) {
+            const double *l = L + (long long)b * sA;
+            double *x = B + (long long)b * sB + (long long)c * ldb;
+            forward_lower(n, l, lda, x, 0);
+            backward_lower_transposed(n, l, lda, x);
+        }
+}
+
+/* POSV = POTRF then POTRS (Sec. III-A names glass::posv; Sec. IV-D POSV).
+ * A <- L, B <- X; a matrix whose factorization fails keeps B unspecified. */
+void oracle_posv_f64(int n, int nrhs, double *A, int lda, long long sA,
+                     double *B, int ldb, long long sB, int *info, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        double *l = A + (long long)b * sA;
+        info[b] = potrf_one(n, l, lda);
+        if (info[b] != 0)
+            continue;
+        for (int c = 0; c < nrhs; ++c) {
+            double *x = B + (long long)b * sB + (long long)c * ldb;
+            forward_lower(n, l, lda, x, 0);
+            backward_lower_transposed(n, l, lda, x);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* GETRF with partial pivoting, GETRS (Sec. III-B "factorizations, and       */
+/* linear solves").  The step order is the unblocked right-looking textbook */
+/* algorithm (LAPACK xGETF2):                                                */
+/*   for j: p = argmax_{i>=j} |a_ij| (smallest i on ties); ipiv[j] = p;      */
+/*          swap rows j and p in all n columns;                              */
+/*          a_jj == 0 -> info = j+1 (first), column left unscaled (it is all */
+/*          zero below the diagonal, so the update is a no-op);              */
+/*          else a_ij /= a_jj (i>j); a_ik -= a_ij a_jk (i,k > j).            */
+/* `gap` (optional, per problem) receives min over steps of                  */
+/*  (|best| - |second best|) / |best| among the candidates, used by tests to */
+/*  select inputs whose pivot choice is unambiguous.                         */
+/* The routine is written once as a macro body so that the same steps can be */
+/* run in FP64 and in FP32 (where a test needs the pivot decision taken in   */
+/* the device's precision).                                                  */
+/* ------------------------------------------------------------------------ */
+#define DEFINE_GETRF_ONE(NAME, T, FABS)                                        \
+static int NAME(int n, T *a, int lda, int *ipiv, double *gap)                 \
+{                                                                             \
+    int info = 0;                                                             \
+    double g = 1.0;                                                           \
+    for (int j = 0; j < n; ++j) {                                             \
+        int p = j;                                                            \
+        T best = FABS(a[j * lda + j]);                                        \
+        T second = (T)0;                                                      \
+        for (int i = j + 1; i < n; ++i) {                                     \
+            T v = FABS(a[j * lda + i]);                                       \
+            if (v > best) { second = best; best = v; p = i; }                 \
+            else if (v > second) { second = v; }                              \
+        }                                                                     \
+        if (j + 1 < n && best > (T)0) {                                       \
+            double r = ((double)best - (double)second) / (double)best;        \
+            if (r < g) g = r;                                                 \
+        }                                                                     \
+        ipiv[j] = p;                                                          \
+        if (p != j)                                                           \
+            for (int c = 0; c < n; ++c) {                                     \
+                T t = a[c * lda + j];                                         \
+                a[c * lda + j] = a[c * lda + p];                              \
+                a[c * lda + p] = t;                                           \
+            }                                                                 \
+        T piv = a[j * lda + j];                                               \
+        if (piv == (T)0) {                                                    \
+            if (info == 0) info = j + 1;                                      \
+            continue;                                                         \
+        }                                                                     \
+        for (int i = j + 1; i < n; ++i)                                       \
+            a[j * lda + i] = a[j * lda + i] / piv;                            \
+        for (int k = j + 1; k < n; ++k)                                       \
+            for (int i = j + 1; i < n; ++i)                                   \
+                a[k * lda + i] -= a[j * lda + i] * a[k * lda + j];            \
+    }                                                                         \
+    if (gap) *gap = g;                                                        \
+    return info;                                                              \
+}
+
+DEFINE_GETRF_ONE(getrf_one_f64, double, fabs)
+DEFINE_GETRF_ONE(getrf_one_f32, float, fabsf)
+
+void oracle_getrf_f64(int n, double *A, int lda, long long sA, int *ipiv,
+                      int *info, double *gap, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b)
+        info[b] = getrf_one_f64(n, A + (long long)b * sA, lda,
+                                ipiv + (long long)b * n, gap ? gap + b : NULL);
+}
+
+/* The same steps in FP32 arithmetic (no FMA contraction: see the build
+ * flags), for tests that need the pivot decision in single precision. */
+void oracle_getrf_f32(int n, float *A, int lda, long long sA, int *ipiv,
+                      int *info, double *gap, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b)
+        info[b] = getrf_one_f32(n, A + (long long)b * sA, lda,
+                                ipiv + (long long)b * n, gap ? gap + b : NULL);
+}
+
+/* GETRS: apply the row swaps to B in order j = 0..n-1, then forward solve
+ * with the unit lower factor and backward solve with the upper factor. */
+static void getrs_one(int n, const double *lu, int lda, const int *ipiv, double *x)
+{
+    for (int j = 0; j < n; ++j) {
+        int p = ipiv[j];
+        if (p != j) { double t = x[j]; x[j] = x[p]; x[p] = t; }
+    }
+    forward_lower(n, lu, lda, x, 1);
+    for (int i = n - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int k = i + 1; k < n; ++k)
+            s -= lu[k * lda + i] * x[k];
+        x[i] = s / lu[i * lda + i];
+    }
+}
+
+void oracle_getrs_f64(int n, int nrhs, const double *LU, int lda, long long sA,
+                      const int *ipiv, double *B, int ldb, long long sB, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b)
+        for (int c = 0; c < nrhs; ++c)
+            getrs_one(n, LU + (long long)b * sA, lda, ipiv + (long long)b * n,
+                      B + (long long)b * sB + (long long)c * ldb);
+}
+
+/* GETRF + GETRS in one call (the device library's fused getrf_getrs). */
+void oracle_getrf_getrs_f64(int n, int nrhs, double *A, int lda, long long sA,
+                            int *ipiv, double *B, int ldb, long long sB,
+                            int *info, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        double *a = A + (long long)b * sA;
+        int *pv = ipiv + (long long)b * n;
+        info[b] = getrf_one_f64(n, a, lda, pv, NULL);
+        if (info[b] != 0)
+            continue;
+        for (int c = 0; c < nrhs; ++c)
+            getrs_one(n, a, lda, pv, B + (long long)b * sB + (long long)c * ldb);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rotation composition (Sec. III-B: SO(3) maps).  A chain of `chain` 3x3    */
+/* column-major rotations R_0..R_{c-1} per problem, stored back to back      */
+/* (9 values each), composes to R = R_0 R_1 ... R_{c-1}: R_{c-1} acts first. */
+/* ------------------------------------------------------------------------ */
+static void mat3_mul(const double *x, const double *y, double *z)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < 3; ++l)
+                s += x[l * 3 + i] * y[j * 3 + l];
+            z[j * 3 + i] = s;
+        }
+}
+
+void oracle_rot3_compose_f64(int chain, const double *Rs, long long sRs,
+                             double *R, long long sR, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *in = Rs + (long long)b * sRs;
+        double acc[9], tmp[9];
+        memcpy(acc, in, sizeof acc);
+        for (int c = 1; c < chain; ++c) {
+            mat3_mul(acc, in + 9 * c, tmp);
+            memcpy(acc, tmp, sizeof acc);
+        }
+        memcpy(R + (long long)b * sR, acc, sizeof acc);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* SE(3) apply (Sec. III-B: SE(3) maps).  A chain of `chain` 4x4 column-major*/
+/* homogeneous transforms T_0..T_{c-1} per problem composes to               */
+/* T = T_0 ... T_{c-1}; then q_i = R p_i + t with R = T[0:3,0:3],            */
+/* t = T[0:3,3].  Points are 3 x npts column-major (x,y,z of point i at      */
+/* 3i..3i+2).  The bottom row of each input transform is not read: it is     */
+/* taken to be (0,0,0,1).                                                    */
+/* ------------------------------------------------------------------------ */
+void oracle_se3_apply_f64(int chain, const double *T, long long sT, int npts,
+                          const double *P, long long sP, double *Q, long long sQ,
+                          int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *tin = T + (long long)b * sT;
+        double r[9], t[3];
+        for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 3; ++i)
+                r[j * 3 + i] = tin[j * 4 + i];
+        for (int i = 0; i < 3; ++i)
+            t[i] = tin[12 + i];
+        for (int c = 1; c < chain; ++c) {
+            const double *tc = tin + 16 * c;
+            double rc[9], nr[9], nt[3];
+            for (int j = 0; j < 3; ++j)
+                for (int i = 0; i < 3; ++i)
+                    rc[j * 3 + i] = tc[j * 4 + i];
+            /* [r t] [rc tc] = [r rc, r tc + t] */
+            mat3_mul(r, rc, nr);
+            for (int i = 0; i < 3; ++i) {
+                double s = t[i];
+                for (int l = 0; l < 3; ++l)
+                    s += r[l * 3 + i] * tc[12 + l];
+                nt[i] = s;
+            }
+            memcpy(r, nr, sizeof r);
+            memcpy(t, nt, sizeof t);
+        }
+        const double *p = P + (long long)b * sP;
+        double *q = Q + (long long)b * sQ;
+        for (int k = 0; k < npts; ++k)
+            for (int i = 0; i < 3; ++i) {
+                double s = t[i];
+                for (int l = 0; l < 3; ++l)
+                    s += r[l * 3 + i] * p[3 * k + l];
+                q[3 * k + i] = s;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Placement cost model: a 3-layer perceptron din -> h -> h -> dout with     */
+/* ReLU, trained on log-latency with a masked mean-squared error and Adam.   */
+/* The paper has no learned model (placements come from exhaustive offline  */
+/* measurement, Sec. III-A); this is the plain definition of that network.   */
+/* Weight layout (row-major, out x in):                                      */
+/*   W1[h][din] b1[h] W2[h][h] b2[h] W3[dout][h] b3[dout], packed in order.  */
+/* ------------------------------------------------------------------------ */
+static void mlp_offsets(int din, int h, int dout, long long off[6])
+{
+    off[0] = 0;                        /* W1 */
+    off[1] = off[0] + (long long)h * din;    /* b1 */
+    off[2] = off[1] + h;               /* W2 */
+    off[3] = off[2] + (long long)h * h;      /* b2 */
+    off[4] = off[3] + h;               /* W3 */
+    off[5] = off[4] + (long long)dout * h;   /* b3 */
+}
+
+long long oracle_mlp_nparams(int din, int h, int dout)
+{
+    long long off[6];
+    mlp_offsets(din, h, dout, off);
+    return off[5] + dout;
+}
+
+/* Forward for `rows` inputs X[rows][din] -> Y[rows][dout]. Optional H1, H2
+ * ([rows][h]) receive the post-ReLU activations. */
+void oracle_mlp_fwd_f64(int din, int h, int dout, const double *w, int rows,
+                        const double *X, double *Y, double *H1, double *H2)
+{
+    long long off[6];
+    mlp_offsets(din, h, dout, off);
+    const double *W1 = w + off[0], *b1 = w + off[1], *W2 = w + off[2];
+    const double *b2 = w + off[3], *W3 = w + off[4], *b3 = w + off[5];
+    OMP_FOR
+    for (int r = 0; r < rows; ++r) {
+        double *h1 = (double *)malloc(sizeof(double) * h);
+        double *h2 = (double *)malloc(sizeof(double) * h);
+        const double *x = X + (long long)r * din;
+        for (int o = 0; o < h; ++o) {
+            double s = b1[o];
+            for (int i = 0; i < din; ++i) s += W1[(long long)o * din + i] * x[i];
+            h1[o] = s > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < h; ++o) {
+            double s = b2[o];
+            for (int i = 0; i < h; ++i) s += W2[(long long)o * h + i] * h1[i];
+            h2[o] = s > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < dout; ++o) {
+            double s = b3[o];
+            for (int i = 0; i < h; ++i) s += W3[(long long)o * h + i] * h2[i];
+            Y[(long long)r * dout + o] = s;
+        }
+        if (H1) memcpy(H1 + (long long)r * h, h1, sizeof(double) * h);
+        if (H2) memcpy(H2 + (long long)r * h, h2, sizeof(double) * h);
+        free(h1);
+        free(h2);
+    }
+}
+
+/* Masked MSE: loss = sum_{r,o} m_ro (y_ro - t_ro)^2 / max(1, sum m).
+ * Returns the loss and writes dL/dw into grad (same layout as w). */
+double oracle_mlp_loss_grad_f64(int din, int h, int dout, const double *w, int rows,
+                                const double *X, const double *Tgt, const double *M,
+                                double *grad)
+{
+    long long off[6];
+    mlp_offsets(din, h, dout, off);
+    long long np = off[5] + dout;
+    const double *W2 = w + off[2], *W3 = w + off[4];
+    double *H1 = (double *)malloc(sizeof(double) * (size_t)rows * h);
+    double *H2 = (double *)malloc(sizeof(double) * (size_t)rows * h);
+    double *Y = (double *)malloc(sizeof(double) * (size_t)rows * dout);
+    oracle_mlp_fwd_f64(din, h, dout, w, rows, X, Y, H1, H2);
+    double msum = 0.0;
+    for (long long i = 0; i < (long long)rows * dout; ++i) msum += M[i];
+    double denom = msum > 1.0 ? msum : 1.0;
+    memset(grad, 0, sizeof(double) * (size_t)np);
+    double loss = 0.0;
+    double *dy = (double *)malloc(sizeof(double) * dout);
+    double *d2 = (double *)malloc(sizeof(double) * h);
+    double *d1 = (double *)malloc(sizeof(double) * h);
+    for (int r = 0; r < rows; ++r) {
+        const double *x = X + (long long)r * din;
+        const double *h1 = H1 + (long long)r * h, *h2 = H2 + (long long)r * h;
+        for (int o = 0; o < dout; ++o) {
+            long long q = (long long)r * dout + o;
+            double e = Y[q] - Tgt[q];
+            loss += M[q] * e * e;
+            dy[o] = 2.0 * M[q] * e / denom;
+        }
+        /* layer 3 */
+        for (int o = 0; o < dout; ++o) {
+            for (int i = 0; i < h; ++i)
+                grad[off[4] + (long long)o * h + i] += dy[o] * h2[i];
+            grad[off[5] + o] += dy[o];
+        }
+        for (int i = 0; i < h; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < dout; ++o) s += W3[(long long)o * h + i] * dy[o];
+            d2[i] = h2[i] > 0.0 ? s : 0.0;          /* ReLU'(z) = [z > 0] */
+        }
+        /* layer 2 */
+        for (int o = 0; o < h; ++o) {
+            for (int i = 0; i < h; ++i)
+                grad[off[2] + (long long)o * h + i] += d2[o] * h1[i];
+            grad[off[3] + o] += d2[o];
+        }
+        for (int i = 0; i < h; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < h; ++o) s += W2[(long long)o * h + i] * d2[o];
+            d1[i] = h1[i] > 0.0 ? s : 0.0;
+        }
+        /* layer 1 */
+        for (int o = 0; o < h; ++o) {
+            for (int i = 0; i < din; ++i)
+                grad[off[0] + (long long)o * din + i] += d1[o] * x[i];
+            grad[off[1] + o] += d1[o];
+        }
+    }
+    free(dy); free(d2); free(d1);
+    free(H1); free(H2); free(Y);
+    return loss / denom;
+}
+
+/* One Adam step (Kingma & Ba 2015, Algorithm 1) at step count t >= 1:
+ *   m = b1 m + (1-b1) g ; v = b2 v + (1-b2) g^2 ;
+ *   w -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)                   */
+void oracle_adam_step_f64(long long np, double *w, const double *g, double *m,
+                          double *v, int t, double lr, double b1, double b2,
+                          double eps)
+{
+    double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (long long i = 0; i < np; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}

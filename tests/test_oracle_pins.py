@@ -1,0 +1,480 @@
+"""Pins of the FP64 oracle against what mathematics fixes (CPU only).
+
+Each test checks the oracle against something other than itself: SciPy/NumPy
+library routines, hand-worked examples (tests/golden), exact-integer and
+dyadic constructions whose factors are known without factorizing, closed
+forms, and brute force on tiny inputs.  A plausible slip in the oracle (a
+dropped term, a wrong index, a transposed operand, a wrong pivot rule) fails
+at least one of them.
+"""
+from fractions import Fraction
+import itertools
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+from paper_2609_28179_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            out[key] = [float(Fraction(v)) for v in vals]
+    return out
+
+
+def _cm(mats):
+    return W.colmajor(np.asarray(mats, dtype=np.float64), dtype=np.float64)
+
+
+def _mats(flat, batch, r, c):
+    return W.from_colmajor(flat, batch, r, c)
+
+
+# ----------------------------------------------------------------- golden
+def test_golden_cholesky_3x3():
+    g = _golden("cholesky_3x3.txt")
+    A = np.array(g["A"]).reshape(3, 3)
+    L, info = oracle.potrf(3, _cm([A]), 1)
+    assert info[0] == 0
+    Lm = np.tril(_mats(L, 1, 3, 3)[0])
+    assert np.array_equal(Lm, np.array(g["L"]).reshape(3, 3))
+    _, X, info = oracle.posv(3, 1, _cm([A]), np.array(g["b"]), 1)
+    np.testing.assert_allclose(X, g["x"], rtol=0, atol=1e-15)
+
+
+def test_golden_lu_3x3():
+    g = _golden("lu_3x3.txt")
+    A = np.array(g["A"]).reshape(3, 3)
+    LU, ipiv, info, _ = oracle.getrf(3, _cm([A]), 1)
+    assert info[0] == 0
+    assert list(ipiv) == [int(v) for v in g["ipiv"]]
+    np.testing.assert_allclose(_mats(LU, 1, 3, 3)[0], np.array(g["LU"]).reshape(3, 3),
+                               rtol=0, atol=1e-15)
+    _, _, X, _ = oracle.getrf_getrs(3, 1, _cm([A]), np.array(g["b"]), 1)
+    np.testing.assert_allclose(X, g["x"], rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------------------------- gemm
+@pytest.mark.parametrize("m,n,k", [(3, 3, 3), (7, 5, 6), (64, 64, 64), (1, 9, 2)])
+def test_gemm_vs_numpy(m, n, k):
+    g = W.rng(1)
+    b = 5
+    A = g.standard_normal((b, m, k))
+    B = g.standard_normal((b, k, n))
+    C = oracle.gemm(m, n, k, _cm(A), _cm(B), b)
+    np.testing.assert_allclose(_mats(C, b, m, n), A @ B, rtol=1e-12, atol=1e-12)
+
+
+def test_gemm_integer_exact_and_structure():
+    n, b = 64, 3
+    A = W.int_matrix(n, n, b, 2)
+    B = W.int_matrix(n, n, b, 3)
+    C = oracle.gemm(n, n, n, _cm(A), _cm(B), b)
+    assert np.array_equal(_mats(C, b, n, n), A @ B)
+    # identity on the left, permutation on the right
+    I = np.broadcast_to(np.eye(n), (b, n, n))
+    C = oracle.gemm(n, n, n, _cm(I), _cm(B), b)
+    assert np.array_equal(_mats(C, b, n, n), B)
+    perm = W.rng(4).permutation(n)
+    P = np.eye(n)[:, perm][None].repeat(b, 0)
+    C = oracle.gemm(n, n, n, _cm(A), _cm(P), b)
+    assert np.array_equal(_mats(C, b, n, n), A[:, :, perm])
+
+
+def test_gemm_strided_leading_dims():
+    # padded lda/ldb/ldc and batch strides larger than the matrix
+    m, n, k, b = 5, 4, 3, 2
+    g = W.rng(5)
+    lda, ldb, ldc = 7, 6, 9
+    A = g.standard_normal(b * lda * k + 11)
+    B = g.standard_normal(b * ldb * n + 13)
+    C = oracle.gemm(m, n, k, A, B, b, lda=lda, ldb=ldb, ldc=ldc,
+                    sA=lda * k + 11 // b, sB=ldb * n + 13 // b, sC=ldc * n + 1)
+    for bb in range(b):
+        a = A[bb * (lda * k + 5):][: lda * k].reshape(k, lda).T[:m]
+        bm = B[bb * (ldb * n + 6):][: ldb * n].reshape(n, ldb).T[:k]
+        c = C[bb * (ldc * n + 1):][: ldc * n].reshape(n, ldc).T[:m]
+        np.testing.assert_allclose(c, a @ bm, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------ potrf
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 7, 12, 24, 64])
+def test_potrf_vs_scipy(n):
+    b = 4
+    A = _mats(W.spd(n, b, 10 + n).astype(np.float64), b, n, n)
+    L, info = oracle.potrf(n, _cm(A), b)
+    assert (info == 0).all()
+    Lm = np.tril(_mats(L, b, n, n))
+    for i in range(b):
+        ref = sla.cholesky(A[i], lower=True)
+        np.testing.assert_allclose(Lm[i], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_potrf_leaves_upper_untouched():
+    n = 6
+    A = _mats(W.spd(n, 1, 3).astype(np.float64), 1, n, n)[0].copy()
+    A[np.triu_indices(n, 1)] = 12345.0
+    L, info = oracle.potrf(n, _cm([A]), 1)
+    Lm = _mats(L, 1, n, n)[0]
+    assert info[0] == 0
+    assert (Lm[np.triu_indices(n, 1)] == 12345.0).all()
+
+
+@pytest.mark.parametrize("n", [2, 5, 16, 64])
+def test_potrf_integer_exact(n):
+    A, L0 = W.int_cholesky_factor(n, 6, 20 + n)
+    L, info = oracle.potrf(n, _cm(A), 6)
+    assert (info == 0).all()
+    assert np.array_equal(np.tril(_mats(L, 6, n, n)), L0)
+
+
+def test_potrf_2x2_closed_form():
+    g = W.rng(7)
+    for _ in range(20):
+        M = g.standard_normal((2, 2))
+        A = M @ M.T + 0.5 * np.eye(2)
+        L, info = oracle.potrf(2, _cm([A]), 1)
+        l11 = np.sqrt(A[0, 0])
+        l21 = A[1, 0] / l11
+        l22 = np.sqrt(A[1, 1] - l21 ** 2)
+        Lm = _mats(L, 1, 2, 2)[0]
+        np.testing.assert_allclose([Lm[0, 0], Lm[1, 0], Lm[1, 1]], [l11, l21, l22],
+                                   rtol=1e-14)
+
+
+@pytest.mark.parametrize("j", [0, 1, 4, 7])
+def test_potrf_info_non_spd(j):
+    n = 8
+    A, L0 = W.int_cholesky_factor(n, 1, 30 + j)
+    A = A[0].copy()
+    A[j, j] -= L0[0, j, j] ** 2 + 1.0        # pivot at column j becomes -1
+    L, info = oracle.potrf(n, _cm([A]), 1)
+    assert info[0] == j + 1
+    A[j, j] += 1.0                           # pivot exactly 0 is also a failure
+    L, info = oracle.potrf(n, _cm([A]), 1)
+    assert info[0] == j + 1
+    A[j, j] = np.nan
+    L, info = oracle.potrf(n, _cm([A]), 1)
+    assert info[0] == j + 1
+
+
+# ---------------------------------------------------------- trsm / potrs
+@pytest.mark.parametrize("n,k", [(1, 1), (3, 2), (12, 12), (64, 5)])
+def test_trsm_vs_scipy(n, k):
+    b = 3
+    g = W.rng(40 + n)
+    L = np.tril(g.standard_normal((b, n, n))) + 3 * np.eye(n)
+    B = g.standard_normal((b, n, k))
+    X = oracle.trsm(n, k, _cm(L), _cm(B), b)
+    Xm = _mats(X, b, n, k)
+    for i in range(b):
+        ref = sla.solve_triangular(L[i], B[i], lower=True)
+        np.testing.assert_allclose(Xm[i], ref, rtol=1e-11, atol=1e-11)
+
+
+def test_trsm_ignores_upper_triangle():
+    n, k = 5, 2
+    g = W.rng(41)
+    L = np.tril(g.standard_normal((1, n, n))) + 3 * np.eye(n)
+    Lg = L.copy()
+    Lg[0][np.triu_indices(n, 1)] = np.nan
+    B = g.standard_normal((1, n, k))
+    np.testing.assert_array_equal(oracle.trsm(n, k, _cm(Lg), _cm(B), 1),
+                                  oracle.trsm(n, k, _cm(L), _cm(B), 1))
+
+
+@pytest.mark.parametrize("n", [1, 4, 17, 64])
+def test_trsm_integer_exact(n):
+    k, b = 3, 4
+    L = W.int_lower_pow2_diag(n, b, 50 + n)
+    X0 = W.int_matrix(n, k, b, 51 + n, -3, 3)
+    B = L @ X0
+    X = oracle.trsm(n, k, _cm(L), _cm(B), b)
+    assert np.array_equal(_mats(X, b, n, k), X0)
+
+
+@pytest.mark.parametrize("n", [2, 9, 32, 64])
+def test_potrs_exact_and_vs_scipy(n):
+    k, b = 2, 3
+    L = W.int_lower_pow2_diag(n, b, 60 + n, positive=True)
+    X0 = W.int_matrix(n, k, b, 61 + n, -3, 3)
+    B = L @ np.transpose(L, (0, 2, 1)) @ X0
+    X = oracle.potrs(n, k, _cm(L), _cm(B), b)
+    assert np.array_equal(_mats(X, b, n, k), X0)
+    A = _mats(W.spd(n, b, 62 + n).astype(np.float64), b, n, n)
+    Bg = W.rng(63).standard_normal((b, n, k))
+    Lf, info = oracle.potrf(n, _cm(A), b)
+    X = oracle.potrs(n, k, Lf, _cm(Bg), b)
+    for i in range(b):
+        ref = sla.cho_solve((sla.cholesky(A[i], lower=True), True), Bg[i])
+        np.testing.assert_allclose(_mats(X, b, n, k)[i], ref, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [6, 33, 64])
+def test_posv_residual_and_factor(n):
+    b, k = 5, 4
+    A = _mats(W.spd(n, b, 70 + n).astype(np.float64), b, n, n)
+    B = W.rng(71).standard_normal((b, n, k))
+    L, X, info = oracle.posv(n, k, _cm(A), _cm(B), b)
+    assert (info == 0).all()
+    Lm = np.tril(_mats(L, b, n, n))
+    Xm = _mats(X, b, n, k)
+    np.testing.assert_allclose(Lm @ np.transpose(Lm, (0, 2, 1)), A, rtol=1e-12, atol=1e-10)
+    res = np.abs(A @ Xm - B).max() / (np.abs(A).sum(-1).max() * np.abs(Xm).max())
+    assert res < 1e-14
+
+
+# ------------------------------------------------------------------ getrf
+def _lu_unpack(LUm):
+    n = LUm.shape[-1]
+    L = np.tril(LUm, -1) + np.eye(n)
+    U = np.triu(LUm)
+    return L, U
+
+
+def _perm_from_ipiv(ipiv, n):
+    perm = np.arange(n)
+    for j in range(n):
+        p = ipiv[j]
+        perm[[j, p]] = perm[[p, j]]
+    return perm
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 14, 32, 64])
+def test_getrf_vs_scipy(n):
+    b = 4
+    A = _mats(W.rng(80 + n).standard_normal(b * n * n), b, n, n)
+    LU, ipiv, info, gap = oracle.getrf(n, _cm(A), b)
+    assert (info == 0).all()
+    for i in range(b):
+        lu, piv = sla.lu_factor(A[i])
+        assert np.array_equal(piv, ipiv[i * n:(i + 1) * n])
+        np.testing.assert_allclose(_mats(LU, b, n, n)[i], lu, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("n", [2, 6, 12, 24, 64])
+def test_getrf_dyadic_exact(n):
+    b = 5
+    A, perm, L0, U0 = W.dyadic_lu(n, b, 90 + n)
+    for prec in ("f64", "f32"):
+        LU, ipiv, info, gap = oracle.getrf(n, _cm(A), b, precision=prec)
+        assert (info == 0).all()
+        LUm = _mats(LU, b, n, n)
+        for i in range(b):
+            assert np.array_equal(_perm_from_ipiv(ipiv[i * n:(i + 1) * n], n), perm[i])
+            L, U = _lu_unpack(LUm[i])
+            assert np.array_equal(L, L0[i]) and np.array_equal(U, U0[i])
+        assert (gap >= 0.5).all()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_getrf_brute_force_tiny(n):
+    """Enumerate every row order; partial pivoting is the unique order whose
+    unpivoted LU has all |l_ij| <= 1 (inputs are generic)."""
+    g = W.rng(100 + n)
+    for _ in range(25):
+        A = g.standard_normal((n, n))
+        winners = []
+        for perm in itertools.permutations(range(n)):
+            Ap = A[list(perm)]
+            # Doolittle, closed form for n <= 3
+            U = np.zeros((n, n))
+            L = np.eye(n)
+            for i in range(n):
+                for j in range(i, n):
+                    U[i, j] = Ap[i, j] - L[i, :i] @ U[:i, j]
+                for j in range(i + 1, n):
+                    L[j, i] = (Ap[j, i] - L[j, :i] @ U[:i, i]) / U[i, i]
+            if np.abs(np.tril(L, -1)).max(initial=0.0) <= 1.0:
+                winners.append((perm, L, U))
+        assert len(winners) == 1
+        perm, L0, U0 = winners[0]
+        LU, ipiv, info, _ = oracle.getrf(n, _cm([A]), 1)
+        assert tuple(_perm_from_ipiv(ipiv, n)) == perm
+        L, U = _lu_unpack(_mats(LU, 1, n, n)[0])
+        np.testing.assert_allclose(L, L0, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(U, U0, rtol=1e-12, atol=1e-12)
+
+
+def test_getrf_tie_takes_smallest_row_and_singular_info():
+    # column 0 has equal magnitudes at rows 1 and 2: row 1 must win
+    A = np.array([[1.0, 2.0, 0.0], [-3.0, 1.0, 1.0], [3.0, 0.0, 2.0]])
+    _, ipiv, info, gap = oracle.getrf(3, _cm([A]), 1)
+    assert ipiv[0] == 1 and info[0] == 0 and gap[0] == 0.0
+    # exactly singular: second column is a multiple of the first
+    A = np.array([[1.0, 2.0, 1.0], [2.0, 4.0, 0.0], [4.0, 8.0, 3.0]])
+    _, ipiv, info, _ = oracle.getrf(3, _cm([A]), 1)
+    assert info[0] == 2
+
+
+@pytest.mark.parametrize("n", [3, 12, 64])
+def test_getrs_vs_scipy(n):
+    b, k = 3, 3
+    A = _mats(W.general(n, b, 110 + n).astype(np.float64), b, n, n)
+    B = W.rng(111).standard_normal((b, n, k))
+    LU, ipiv, X, info = oracle.getrf_getrs(n, k, _cm(A), _cm(B), b)
+    for i in range(b):
+        ref = sla.lu_solve(sla.lu_factor(A[i]), B[i])
+        np.testing.assert_allclose(_mats(X, b, n, k)[i], ref, rtol=1e-10, atol=1e-12)
+    # split path gives the same answer
+    LU2, ipiv2, info2, _ = oracle.getrf(n, _cm(A), b)
+    X2 = oracle.getrs(n, k, LU2, ipiv2, _cm(B), b)
+    np.testing.assert_array_equal(X, X2)
+
+
+# -------------------------------------------------------------- geometry
+def _rz(a):
+    c, s = np.cos(a), np.sin(a)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def test_rot3_rz_addition():
+    g = W.rng(120)
+    for _ in range(10):
+        a, b = g.uniform(-np.pi, np.pi, 2)
+        R = oracle.rot3_compose(2, _cm([_rz(a), _rz(b)]), 1)
+        np.testing.assert_allclose(_mats(R, 1, 3, 3)[0], _rz(a + b), atol=1e-14)
+
+
+@pytest.mark.parametrize("chain", [1, 2, 3, 7, 64])
+def test_rot3_chain_orthonormal_and_order(chain):
+    b = 6
+    Rs = W.rotations(b * chain, 121 + chain).astype(np.float64)
+    R = _mats(oracle.rot3_compose(chain, Rs, b), b, 3, 3)
+    mats = _mats(Rs, b * chain, 3, 3).reshape(b, chain, 3, 3)
+    for i in range(b):
+        ref = np.eye(3)
+        for c in range(chain):
+            ref = ref @ mats[i, c]
+        np.testing.assert_allclose(R[i], ref, atol=1e-12)
+        np.testing.assert_allclose(R[i].T @ R[i], np.eye(3), atol=1e-6)
+        assert abs(np.linalg.det(R[i]) - 1.0) < 1e-6
+    if chain >= 2:  # order matters: R0 R1 != R1 R0 in general
+        swapped = mats[:, [1, 0] + list(range(2, chain))]
+        R2 = _mats(oracle.rot3_compose(chain, _cm(swapped.reshape(-1, 3, 3)), b), b, 3, 3)
+        assert np.abs(R2 - R).max() > 1e-3
+
+
+def test_se3_inverse_identity_translation():
+    b, npts = 4, 50
+    T = W.se3_transforms(b, 130).astype(np.float64)
+    P = W.gaussian(b * 3 * npts, 131).astype(np.float64)
+    Q = oracle.se3_apply(1, T, npts, P, b)
+    Tm = _mats(T, b, 4, 4)
+    Tinv = np.zeros_like(Tm)
+    for i in range(b):
+        R, t = Tm[i, :3, :3], Tm[i, :3, 3]
+        Ri = np.linalg.inv(R)   # inputs are FP32-rounded: R^T is not exact
+        Tinv[i, :3, :3] = Ri
+        Tinv[i, :3, 3] = -Ri @ t
+        Tinv[i, 3, 3] = 1.0
+    P2 = oracle.se3_apply(1, _cm(Tinv), npts, Q, b)
+    np.testing.assert_allclose(P2, P, atol=1e-12)
+    I = np.broadcast_to(np.eye(4), (b, 4, 4))
+    np.testing.assert_array_equal(oracle.se3_apply(1, _cm(I), npts, P, b), P)
+    Tt = np.broadcast_to(np.eye(4), (b, 4, 4)).copy()
+    Tt[:, :3, 3] = [1.5, -2.0, 0.25]
+    Qt = oracle.se3_apply(1, _cm(Tt), npts, P, b).reshape(b, npts, 3)
+    np.testing.assert_allclose(Qt, P.reshape(b, npts, 3) + np.array([1.5, -2.0, 0.25]),
+                               atol=1e-15)
+
+
+@pytest.mark.parametrize("chain", [2, 5])
+def test_se3_chain_equals_sequential_application(chain):
+    """Composing T0..T_{c-1} then applying equals applying T_{c-1} first, then
+    ..., T0 last, one transform at a time."""
+    b, npts = 3, 20
+    T = W.se3_transforms(b * chain, 140 + chain).astype(np.float64)
+    Tm = _mats(T, b * chain, 4, 4).reshape(b, chain, 4, 4)
+    Tm[:, :, 3, :] = 777.0                  # the bottom row must never be read
+    P = W.gaussian(b * 3 * npts, 141).astype(np.float64)
+    Q = oracle.se3_apply(chain, _cm(Tm.reshape(-1, 4, 4)), npts, P, b)
+    cur = P
+    for c in reversed(range(chain)):
+        cur = oracle.se3_apply(1, _cm(Tm[:, c]), npts, cur, b)
+    np.testing.assert_allclose(Q, cur, atol=1e-12)
+
+
+# ------------------------------------------------------------- cost model
+DIN, H, DOUT = 8, 64, 12
+
+
+def _mlp_case(rows=7, seed=150):
+    g = W.rng(seed)
+    w = g.standard_normal(oracle.mlp_nparams(DIN, H, DOUT)) * 0.3
+    X = g.standard_normal((rows, DIN))
+    T = g.standard_normal((rows, DOUT))
+    M = (g.random((rows, DOUT)) > 0.3).astype(np.float64)
+    return w, X, T, M
+
+
+def test_mlp_param_count():
+    assert oracle.mlp_nparams(8, 64, 12) == 5516
+
+
+def test_mlp_closed_form_bias_only():
+    w = np.zeros(oracle.mlp_nparams(DIN, H, DOUT))
+    w[-DOUT:] = np.arange(DOUT) * 0.5          # only b3 non-zero: y = b3
+    X = W.rng(151).standard_normal((3, DIN))
+    Y = oracle.mlp_fwd(DIN, H, DOUT, w, X)
+    np.testing.assert_array_equal(Y, np.broadcast_to(w[-DOUT:], (3, DOUT)))
+    T = np.zeros((3, DOUT))
+    M = np.ones((3, DOUT))
+    loss, g = oracle.mlp_loss_grad(DIN, H, DOUT, w, X, T, M)
+    assert loss == pytest.approx(np.sum(w[-DOUT:] ** 2) * 3 / (3 * DOUT))
+    np.testing.assert_allclose(g[-DOUT:], 2 * 3 * w[-DOUT:] / (3 * DOUT))
+    assert np.all(g[:-DOUT] == 0)
+
+
+def test_mlp_forward_matches_numpy_layers():
+    w, X, _, _ = _mlp_case()
+    o = [0, H * DIN, H * DIN + H, H * DIN + H + H * H, H * DIN + 2 * H + H * H,
+         H * DIN + 2 * H + H * H + DOUT * H]
+    W1 = w[o[0]:o[1]].reshape(H, DIN); b1 = w[o[1]:o[2]]
+    W2 = w[o[2]:o[3]].reshape(H, H); b2 = w[o[3]:o[4]]
+    W3 = w[o[4]:o[5]].reshape(DOUT, H); b3 = w[o[5]:]
+    ref = np.maximum(np.maximum(X @ W1.T + b1, 0) @ W2.T + b2, 0) @ W3.T + b3
+    np.testing.assert_allclose(oracle.mlp_fwd(DIN, H, DOUT, w, X), ref, rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_gradient_vs_central_differences():
+    w, X, T, M = _mlp_case()
+    _, g = oracle.mlp_loss_grad(DIN, H, DOUT, w, X, T, M)
+    idx = W.rng(152).choice(w.size, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        wp = w.copy(); wp[i] += h
+        wm = w.copy(); wm[i] -= h
+        lp, _ = oracle.mlp_loss_grad(DIN, H, DOUT, wp, X, T, M)
+        lm, _ = oracle.mlp_loss_grad(DIN, H, DOUT, wm, X, T, M)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_adam_first_step_closed_form_and_training_decreases():
+    w = np.array([1.0, -2.0, 3.0])
+    g = np.array([0.5, -4.0, 0.0])
+    m = np.zeros(3); v = np.zeros(3)
+    oracle.adam_step(w, g, m, v, 1, lr=0.1)
+    # step 1: m_hat = g, v_hat = g^2 -> update = lr * g / (|g| + eps)
+    np.testing.assert_allclose(w, [1.0 - 0.1 * 0.5 / (0.5 + 1e-8),
+                                   -2.0 + 0.1 * 4.0 / (4.0 + 1e-8), 3.0])
+    wv, X, T, M = _mlp_case(rows=64, seed=153)
+    mm = np.zeros_like(wv); vv = np.zeros_like(wv)
+    l0, _ = oracle.mlp_loss_grad(DIN, H, DOUT, wv, X, T, M)
+    for t in range(1, 101):
+        _, gr = oracle.mlp_loss_grad(DIN, H, DOUT, wv, X, T, M)
+        oracle.adam_step(wv, gr, mm, vv, t, lr=1e-2)
+    l1, _ = oracle.mlp_loss_grad(DIN, H, DOUT, wv, X, T, M)
+    assert l1 < 0.5 * l0
