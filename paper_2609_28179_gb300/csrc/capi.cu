@@ -1,0 +1,506 @@
+// capi.cu -- the library's C ABI: argument validation, placement
+// resolution and dispatch to the batched kernels.  See include/glass.h for
+// the contract of every entry point.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "placement_table.h"
+
+namespace glass {
+
+// Device status word (bounded waits that gave up, ...), one per device.
+__device__ unsigned g_device_status;
+
+namespace {
+
+const glass_opts kDefaultOpts = {GLASS_F32, GLASS_MATH_FP32, GLASS_LAYOUT_COLMAJOR, {GLASS_SCOPE_AUTO, 0}, 0, 0, 0};
+
+const glass_opts &opts_or_default(const glass_opts *o) { return o ? *o : kDefaultOpts; }
+
+glass_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return GLASS_OK;
+    if (e == cudaErrorInvalidConfiguration) return GLASS_ERR_INVALID_VALUE;
+    if (e == cudaErrorNotSupported) return GLASS_ERR_UNSUPPORTED;
+    return GLASS_ERR_CUDA;
+}
+
+bool valid_pack(int p) { return p == 1 || p == 2 || p == 4 || p == 8; }
+
+Mat make_mat(const void *p, int ld, long long s, int rows, int cols, int layout) {
+    Mat m;
+    m.p = const_cast<float *>(static_cast<const float *>(p));
+    m.ld = ld;
+    m.s = s;
+    m.rows = rows;
+    m.cols = cols;
+    m.layout = layout;
+    if (layout == GLASS_LAYOUT_INTERLEAVED32) {
+        m.ld = rows;
+        m.s = (long long)rows * cols;
+    }
+    return m;
+}
+
+// Checks of one column-major operand: ld >= rows and, for an output, a batch
+// stride that keeps problems disjoint (inputs may share storage, s == 0).
+bool operand_ok(const void *p, int ld, long long s, int rows, int cols, bool output, int layout) {
+    if (p == nullptr) return false;
+    if (layout == GLASS_LAYOUT_INTERLEAVED32) return true;
+    if (ld < rows || s < 0) return false;
+    if (output && s < (long long)ld * (cols - 1) + rows) return false;
+    return true;
+}
+
+bool feasible(int op, int n, int k, Placement pl) {
+    switch (op) {
+        case GLASS_OP_GEMM: return feasible_gemm(n, n, k, pl);
+        case GLASS_OP_POSV:
+        case GLASS_OP_POTRF:
+        case GLASS_OP_POTRS:
+        case GLASS_OP_TRSM: return feasible_chol(op, n, k, pl);
+        case GLASS_OP_GETRF_GETRS: return feasible_lu(n, k, pl);
+        case GLASS_OP_ROT3: return feasible_geom(0, k, pl);
+        case GLASS_OP_SE3: return feasible_geom(1, k, pl);
+        default: return false;
+    }
+}
+
+// ------------------------------------------------------- learned model
+struct Learned {
+    bool set = false;
+    float w[5516];
+    float mean[8], stdv[8];
+};
+Learned g_learned;
+std::mutex g_learned_mu;
+
+// Row of the placement table / output index of the cost model.
+int table_op(int op) {
+    switch (op) {
+        case GLASS_OP_POTRF:
+        case GLASS_OP_POTRS: return GLASS_OP_POSV;
+        default: return op;
+    }
+}
+
+// Model index of a matrix op (gemm, posv, trsm, getrf_getrs) or -1.
+int model_op(int op) {
+    switch (table_op(op)) {
+        case GLASS_OP_GEMM: return 0;
+        case GLASS_OP_POSV: return 1;
+        case GLASS_OP_TRSM: return 2;
+        case GLASS_OP_GETRF_GETRS: return 3;
+        default: return -1;
+    }
+}
+
+void learned_predict(const Learned &L, const float x[8], float y[12]) {
+    const float *W1 = L.w, *b1 = W1 + 64 * 8, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64, *b3 = W3 + 12 * 64;
+    float h1[64], h2[64];
+    for (int o = 0; o < 64; ++o) {
+        float s = b1[o];
+        for (int i = 0; i < 8; ++i) s += W1[o * 8 + i] * x[i];
+        h1[o] = s > 0.f ? s : 0.f;
+    }
+    for (int o = 0; o < 64; ++o) {
+        float s = b2[o];
+        for (int i = 0; i < 64; ++i) s += W2[o * 64 + i] * h1[i];
+        h2[o] = s > 0.f ? s : 0.f;
+    }
+    for (int o = 0; o < 12; ++o) {
+        float s = b3[o];
+        for (int i = 0; i < 64; ++i) s += W3[o * 64 + i] * h2[i];
+        y[o] = s;
+    }
+}
+
+bool on_grid(int op, int n, int batch) {
+    (void)op;
+    bool gn = false, gb = false;
+    for (int i = 0; i < kTableNumN; ++i) gn |= kTableN[i] == n;
+    for (int i = 0; i < kTableNumB; ++i) gb |= kTableB[i] == batch;
+    return gn && gb;
+}
+
+int nearest_index(const int *grid, int cnt, double v) {
+    int best = 0;
+    double bd = 1e300;
+    for (int i = 0; i < cnt; ++i) {
+        const double d = fabs(log2((double)grid[i]) - log2(v));
+        if (d < bd - 1e-12) { bd = d; best = i; }
+    }
+    return best;
+}
+
+Placement decode(unsigned char code) { return Placement{code >> 2, 1 << (code & 3)}; }
+
+Placement resolve(int op, int n, int k, int batch, int use_learned) {
+    const int top = table_op(op);
+    if (use_learned && model_op(op) >= 0 && !on_grid(op, n, batch)) {
+        std::lock_guard<std::mutex> lk(g_learned_mu);
+        if (g_learned.set) {
+            float x[8] = {0, 0, 0, 0, (float)log2((double)n), (float)log2((double)(k > 0 ? k : 1)),
+                          (float)log2((double)(batch > 0 ? batch : 1)), 0.f};
+            x[model_op(op)] = 1.f;
+            for (int i = 0; i < 8; ++i) x[i] = (x[i] - g_learned.mean[i]) / g_learned.stdv[i];
+            float y[12];
+            learned_predict(g_learned, x, y);
+            int best = -1;
+            for (int p = 0; p < 12; ++p) {
+                const Placement pl = decode((unsigned char)p);
+                if (!feasible(op, n, k, pl)) continue;
+                if (best < 0 || y[p] < y[best]) best = p;
+            }
+            if (best >= 0) return decode((unsigned char)best);
+        }
+    }
+    const int ni = nearest_index(kTableN, kTableNumN, (top == GLASS_OP_ROT3 || top == GLASS_OP_SE3) ? k : n);
+    const int bi = nearest_index(kTableB, kTableNumB, batch > 0 ? batch : 1);
+    Placement pl = decode(kTable[top][ni][bi]);
+    if (feasible(op, n, k, pl)) return pl;
+    // nearest feasible: widen the scope, keep the pack if possible
+    for (int s = pl.scope; s <= SCOPE_BLOCK; ++s)
+        for (int pk = pl.pack; pk >= 1; pk >>= 1) {
+            const Placement q{s, pk};
+            if (feasible(op, n, k, q)) return q;
+        }
+    return Placement{SCOPE_WARP, 1};
+}
+
+// Placement of a call: explicit (validated) or resolved from the table.
+glass_status placement_of(int op, int n, int k, int batch, const glass_opts &o, Placement &pl) {
+    if (o.placement.scope == GLASS_SCOPE_AUTO) {
+        pl = resolve(op, n, k, batch, o.use_learned);
+        if (o.placement.pack != 0) {
+            if (!valid_pack(o.placement.pack)) return GLASS_ERR_INVALID_VALUE;
+            pl.pack = o.placement.pack;
+        }
+    } else {
+        if (o.placement.scope < GLASS_SCOPE_THREAD || o.placement.scope > GLASS_SCOPE_BLOCK)
+            return GLASS_ERR_INVALID_VALUE;
+        pl.scope = o.placement.scope;
+        pl.pack = o.placement.pack == 0 ? 1 : o.placement.pack;
+        if (!valid_pack(pl.pack)) return GLASS_ERR_INVALID_VALUE;
+    }
+    if (!feasible(op, n, k, pl)) return GLASS_ERR_INVALID_VALUE;
+    return GLASS_OK;
+}
+
+glass_status check_common(const glass_opts &o) {
+    if (o.layout != GLASS_LAYOUT_COLMAJOR && o.layout != GLASS_LAYOUT_INTERLEAVED32) return GLASS_ERR_INVALID_VALUE;
+    if (o.dtype != GLASS_F32 && o.dtype != GLASS_F64 && o.dtype != GLASS_BF16) return GLASS_ERR_INVALID_VALUE;
+    if (o.math < GLASS_MATH_FP32 || o.math > GLASS_MATH_3XTF32_TC) return GLASS_ERR_INVALID_VALUE;
+    return GLASS_OK;
+}
+
+glass_status check_order(int n) {
+    if (n < 1) return GLASS_ERR_INVALID_VALUE;
+    if (n > 64) return GLASS_ERR_UNSUPPORTED;
+    return GLASS_OK;
+}
+
+}  // namespace
+}  // namespace glass
+
+using namespace glass;
+
+#define GLASS_TRY(x) do { glass_status _s = (x); if (_s != GLASS_OK) return _s; } while (0)
+
+extern "C" {
+
+glass_status glass_batched_gemm(int m, int n, int k, const void *A, int lda, long long sA, const void *B, int ldb,
+                                long long sB, void *C, int ldc, long long sC, int batch, const glass_opts *opts,
+                                glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if (m < 1 || n < 1 || k < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (m > 64 || n > 64 || k > 64) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (o.math != GLASS_MATH_FP32) {
+        if (!(m == n && n == k && (n == 16 || n == 32 || n == 64))) return GLASS_ERR_UNSUPPORTED;
+        if (o.layout != GLASS_LAYOUT_COLMAJOR) return GLASS_ERR_UNSUPPORTED;
+        if (o.math == GLASS_MATH_BF16_TC && o.dtype != GLASS_BF16) return GLASS_ERR_INVALID_VALUE;
+        if (o.math != GLASS_MATH_BF16_TC && o.dtype != GLASS_F32) return GLASS_ERR_INVALID_VALUE;
+        if (!A || !B || !C) return GLASS_ERR_INVALID_VALUE;
+        if (lda != n || ldb != n || ldc != n || sA != (long long)n * n || sB != (long long)n * n ||
+            sC != (long long)n * n)
+            return GLASS_ERR_UNSUPPORTED;
+        return from_cuda(launch_gemm_tc(n, o.math, A, B, static_cast<float *>(C), batch, st));
+    }
+    if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
+    if (!operand_ok(A, lda, sA, m, k, false, o.layout) || !operand_ok(B, ldb, sB, k, n, false, o.layout) ||
+        !operand_ok(C, ldc, sC, m, n, true, o.layout))
+        return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    const int nn = m > n ? (m > k ? m : k) : (n > k ? n : k);
+    if (o.placement.scope == GLASS_SCOPE_AUTO) {
+        pl = resolve(GLASS_OP_GEMM, nn, nn, batch, o.use_learned);
+        if (o.placement.pack != 0) pl.pack = o.placement.pack;
+        if (!feasible_gemm(m, n, k, pl)) {
+            pl = Placement{SCOPE_WARP, 1};
+            if (!feasible_gemm(m, n, k, pl)) pl = Placement{SCOPE_BLOCK, 1};
+        }
+    } else {
+        GLASS_TRY(placement_of(GLASS_OP_GEMM, nn, nn, batch, o, pl));
+    }
+    if (!feasible_gemm(m, n, k, pl)) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_gemm(m, n, k, make_mat(A, lda, sA, m, k, o.layout), make_mat(B, ldb, sB, k, n, o.layout),
+                                 make_mat(C, ldc, sC, m, n, o.layout), batch, pl, st));
+}
+
+glass_status glass_batched_potrf(int n, void *A, int lda, long long sA, int *info, int batch, const glass_opts *opts,
+                                 glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    GLASS_TRY(check_order(n));
+    if (batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
+    if (!operand_ok(A, lda, sA, n, n, true, o.layout) || info == nullptr) return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    GLASS_TRY(placement_of(GLASS_OP_POTRF, n, 1, batch, o, pl));
+    return from_cuda(launch_potrf(n, make_mat(A, lda, sA, n, n, o.layout), info, batch, pl, o.fp64_diag,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_batched_potrs(int n, int nrhs, const void *L, int lda, long long sA, void *B, int ldb, long long sB,
+                                 int batch, const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    GLASS_TRY(check_order(n));
+    if (nrhs < 0 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (batch == 0 || nrhs == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
+    if (!operand_ok(L, lda, sA, n, n, false, o.layout) || !operand_ok(B, ldb, sB, n, nrhs, true, o.layout))
+        return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    GLASS_TRY(placement_of(GLASS_OP_POTRS, n, nrhs, batch, o, pl));
+    return from_cuda(launch_potrs(n, nrhs, make_mat(L, lda, sA, n, n, o.layout),
+                                  make_mat(B, ldb, sB, n, nrhs, o.layout), batch, pl,
+                                  reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_batched_posv(int n, int nrhs, void *A, int lda, long long sA, void *B, int ldb, long long sB,
+                                int *info, int batch, const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    GLASS_TRY(check_order(n));
+    if (nrhs < 0 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (o.refine_steps < 0 || o.refine_steps > 1) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
+    if (!operand_ok(A, lda, sA, n, n, true, o.layout) || info == nullptr) return GLASS_ERR_INVALID_VALUE;
+    if (nrhs > 0 && !operand_ok(B, ldb, sB, n, nrhs, true, o.layout)) return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    GLASS_TRY(placement_of(GLASS_OP_POSV, n, nrhs > 0 ? nrhs : 1, batch, o, pl));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (nrhs == 0)
+        return from_cuda(launch_potrf(n, make_mat(A, lda, sA, n, n, o.layout), info, batch, pl, o.fp64_diag, st));
+    return from_cuda(launch_posv(n, nrhs, make_mat(A, lda, sA, n, n, o.layout), make_mat(B, ldb, sB, n, nrhs, o.layout),
+                                 info, batch, pl, o.fp64_diag, o.refine_steps, st));
+}
+
+glass_status glass_batched_trsm(int n, int nrhs, const void *L, int lda, long long sA, void *B, int ldb, long long sB,
+                                int batch, const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    GLASS_TRY(check_order(n));
+    if (nrhs < 0 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (nrhs > 4096) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0 || nrhs == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
+    if (!operand_ok(L, lda, sA, n, n, false, o.layout) || !operand_ok(B, ldb, sB, n, nrhs, true, o.layout))
+        return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    GLASS_TRY(placement_of(GLASS_OP_TRSM, n, nrhs, batch, o, pl));
+    return from_cuda(launch_trsm(n, nrhs, make_mat(L, lda, sA, n, n, o.layout),
+                                 make_mat(B, ldb, sB, n, nrhs, o.layout), batch, pl,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_batched_getrf_getrs(int n, int nrhs, void *A, int lda, long long sA, int *ipiv, void *B, int ldb,
+                                       long long sB, int *info, int batch, const glass_opts *opts,
+                                       glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    GLASS_TRY(check_order(n));
+    if (nrhs < 0 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
+    if (!operand_ok(A, lda, sA, n, n, true, o.layout) || ipiv == nullptr || info == nullptr)
+        return GLASS_ERR_INVALID_VALUE;
+    if (nrhs > 0 && !operand_ok(B, ldb, sB, n, nrhs, true, o.layout)) return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    GLASS_TRY(placement_of(GLASS_OP_GETRF_GETRS, n, nrhs, batch, o, pl));
+    const Mat Bm = nrhs > 0 ? make_mat(B, ldb, sB, n, nrhs, o.layout) : make_mat(A, lda, sA, n, n, o.layout);
+    return from_cuda(launch_getrf_getrs(n, nrhs, make_mat(A, lda, sA, n, n, o.layout), ipiv, Bm, info, batch, pl,
+                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_batched_rot3_compose(int chain, const void *Rs, long long sRs, void *R, long long sR, int batch,
+                                        const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if (chain < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (chain > 64) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.layout != GLASS_LAYOUT_COLMAJOR || o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
+    if (!Rs || !R || sRs < 0 || sR < 9) return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    GLASS_TRY(placement_of(GLASS_OP_ROT3, 3, chain, batch, o, pl));
+    return from_cuda(launch_rot3(chain, make_mat(Rs, 3, sRs, 3, 3 * chain, GLASS_LAYOUT_COLMAJOR),
+                                 make_mat(R, 3, sR, 3, 3, GLASS_LAYOUT_COLMAJOR), batch, pl,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_batched_se3_apply(int chain, const void *T, long long sT, int npts, const void *P, long long sP,
+                                     void *Q, long long sQ, int batch, const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if (chain < 1 || npts < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (chain > 64) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.layout != GLASS_LAYOUT_COLMAJOR || o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
+    if (!T || !P || !Q || sT < 0 || sP < 0 || sQ < 3LL * npts) return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    GLASS_TRY(placement_of(GLASS_OP_SE3, 4, chain, batch, o, pl));
+    return from_cuda(launch_se3(chain, make_mat(T, 4, sT, 4, 4 * chain, GLASS_LAYOUT_COLMAJOR), npts,
+                                make_mat(P, 3, sP, 3, npts, GLASS_LAYOUT_COLMAJOR),
+                                make_mat(Q, 3, sQ, 3, npts, GLASS_LAYOUT_COLMAJOR), batch, pl,
+                                reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_to_interleaved32(int rows, int cols, const float *src, float *dst, int batch,
+                                    glass_stream_t stream) {
+    if (rows < 1 || cols < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if ((long long)rows * cols > (1 << 24)) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (!src || !dst) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_to_interleaved(rows, cols, src, dst, batch, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_from_interleaved32(int rows, int cols, const float *src, float *dst, int batch,
+                                      glass_stream_t stream) {
+    if (rows < 1 || cols < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if ((long long)rows * cols > (1 << 24)) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (!src || !dst) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_from_interleaved(rows, cols, src, dst, batch, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t glass_posv_varsize_workspace(int batch) { return batch <= 0 ? 256 : varsize_workspace(batch); }
+
+glass_status glass_posv_varsize(int batch, const int *n_dev, const long long *offA_dev, const long long *offB_dev,
+                                int nrhs, void *A, void *B, int *info, void *ws, size_t ws_bytes,
+                                const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if (batch < 0 || nrhs < 1) return GLASS_ERR_INVALID_VALUE;
+    if (nrhs > 16) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32 || o.layout != GLASS_LAYOUT_COLMAJOR) return GLASS_ERR_UNSUPPORTED;
+    if (!n_dev || !offA_dev || !offB_dev || !A || !B || !info) return GLASS_ERR_INVALID_VALUE;
+    if (!ws || ws_bytes < varsize_workspace(batch) || (reinterpret_cast<uintptr_t>(ws) & 255))
+        return GLASS_ERR_WORKSPACE;
+    int wpc = 8;
+    if (o.placement.scope == GLASS_SCOPE_WARP && o.placement.pack != 0) {
+        if (!valid_pack(o.placement.pack)) return GLASS_ERR_INVALID_VALUE;
+        wpc = o.placement.pack;
+    } else if (o.placement.scope != GLASS_SCOPE_AUTO) {
+        return GLASS_ERR_UNSUPPORTED;
+    }
+    unsigned *status = nullptr;
+    if (cudaGetSymbolAddress(reinterpret_cast<void **>(&status), g_device_status) != cudaSuccess)
+        return GLASS_ERR_CUDA;
+    return from_cuda(launch_posv_varsize(batch, n_dev, offA_dev, offB_dev, nrhs, static_cast<float *>(A),
+                                         static_cast<float *>(B), info, ws, wpc, status,
+                                         reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_get_placement(int op, int n, int k, int batch, int dtype, int use_learned, glass_placement *out) {
+    if (out == nullptr || op < 0 || op >= GLASS_NUM_OPS || batch < 0 || k < 0) return GLASS_ERR_INVALID_VALUE;
+    if (dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
+    if (op == GLASS_OP_ROT3 || op == GLASS_OP_SE3) {
+        if (k < 1 || k > 64) return GLASS_ERR_INVALID_VALUE;
+    } else {
+        GLASS_TRY(check_order(n));
+    }
+    const Placement pl = resolve(op, n, k > 0 ? k : 1, batch, use_learned);
+    out->scope = pl.scope;
+    out->pack = pl.pack;
+    return GLASS_OK;
+}
+
+int glass_placement_feasible(int op, int n, int k, glass_placement p) {
+    if (op < 0 || op >= GLASS_NUM_OPS) return 0;
+    return feasible(op, n, k, Placement{p.scope, p.pack}) ? 1 : 0;
+}
+
+glass_status glass_set_learned_model(const float *weights, int nweights, const float *feat_mean,
+                                     const float *feat_std) {
+    if (!weights || nweights != 5516 || !feat_mean || !feat_std) return GLASS_ERR_INVALID_VALUE;
+    for (int i = 0; i < 8; ++i)
+        if (!(feat_std[i] > 0.f)) return GLASS_ERR_INVALID_VALUE;
+    std::lock_guard<std::mutex> lk(g_learned_mu);
+    memcpy(g_learned.w, weights, sizeof(g_learned.w));
+    memcpy(g_learned.mean, feat_mean, sizeof(g_learned.mean));
+    memcpy(g_learned.stdv, feat_std, sizeof(g_learned.stdv));
+    g_learned.set = true;
+    return GLASS_OK;
+}
+
+size_t glass_mlp_workspace(int rows) { return rows <= 0 ? 256 : mlp_workspace(rows); }
+
+glass_status glass_mlp_forward(int din, const float *w, int rows, const float *X, float *Y, glass_stream_t stream) {
+    if (din != 8 || rows < 0) return din != 8 ? GLASS_ERR_UNSUPPORTED : GLASS_ERR_INVALID_VALUE;
+    if (rows == 0) return GLASS_OK;
+    if (!w || !X || !Y) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_mlp_forward(din, w, rows, X, Y, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_mlp_loss_grad(int din, const float *w, int rows, const float *X, const float *T, const float *M,
+                                 float *grad, float *loss_dev, void *ws, size_t ws_bytes, glass_stream_t stream) {
+    if (din != 8) return GLASS_ERR_UNSUPPORTED;
+    if (rows < 1 || !w || !X || !T || !M || !grad || !loss_dev) return GLASS_ERR_INVALID_VALUE;
+    if (!ws || ws_bytes < mlp_workspace(rows) || (reinterpret_cast<uintptr_t>(ws) & 255)) return GLASS_ERR_WORKSPACE;
+    return from_cuda(launch_mlp_loss_grad(din, w, rows, X, T, M, grad, loss_dev, ws,
+                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_mlp_adam(int nparams, float *w, const float *grad, float *m, float *v, int t, float lr, float beta1,
+                            float beta2, float eps, glass_stream_t stream) {
+    if (nparams < 0 || t < 1 || !(lr > 0.f) || !(eps > 0.f)) return GLASS_ERR_INVALID_VALUE;
+    if (nparams == 0) return GLASS_OK;
+    if (!w || !grad || !m || !v) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_mlp_adam(nparams, w, grad, m, v, t, lr, beta1, beta2, eps,
+                                     reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_last_device_status(glass_stream_t stream) {
+    if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return GLASS_ERR_CUDA;
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_device_status, sizeof v) != cudaSuccess) return GLASS_ERR_CUDA;
+    const unsigned zero = 0;
+    if (cudaMemcpyToSymbol(g_device_status, &zero, sizeof zero) != cudaSuccess) return GLASS_ERR_CUDA;
+    return v == 0 ? GLASS_OK : (glass_status)v;
+}
+
+const char *glass_status_string(glass_status s) {
+    switch (s) {
+        case GLASS_OK: return "GLASS_OK";
+        case GLASS_ERR_INVALID_VALUE: return "GLASS_ERR_INVALID_VALUE";
+        case GLASS_ERR_UNSUPPORTED: return "GLASS_ERR_UNSUPPORTED";
+        case GLASS_ERR_CUDA: return "GLASS_ERR_CUDA";
+        case GLASS_ERR_TIMEOUT: return "GLASS_ERR_TIMEOUT";
+        case GLASS_ERR_WORKSPACE: return "GLASS_ERR_WORKSPACE";
+        default: return "GLASS_ERR_UNKNOWN";
+    }
+}
+
+const char *glass_version(void) { return "glass sm_103a"; }
+
+}  // extern "C"

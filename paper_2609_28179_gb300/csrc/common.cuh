@@ -1,0 +1,243 @@
+// common.cuh -- internal helpers shared by the device kernels of the library.
+//
+// Operand addressing, cooperative HBM <-> shared-memory staging, team
+// synchronisation for the three execution scopes (one problem per thread,
+// per warp, per team of threads; Sec. III-A), and the launcher declarations
+// used by the C ABI in capi.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/glass.h"
+
+#define GLASS_FULL_MASK 0xffffffffu
+
+namespace glass {
+
+enum Scope { SCOPE_THREAD = 0, SCOPE_WARP = 1, SCOPE_BLOCK = 2 };
+
+struct Placement {
+    int scope;
+    int pack;
+};
+
+// A batch of rows x cols operands.  Column-major with leading dimension ld
+// and batch stride s (elements), or -- layout == INTERLEAVED32 -- element
+// (i,j) of problem b at ((b/32)*rows*cols + j*rows + i)*32 + b%32.
+struct Mat {
+    float *p;
+    int ld;
+    long long s;
+    int rows;
+    int cols;
+    int layout;
+
+    __device__ __forceinline__ long long off(int b, int i, int j) const {
+        if (layout == GLASS_LAYOUT_COLMAJOR)
+            return (long long)b * s + (long long)j * ld + i;
+        return ((long long)(b >> 5) * rows * cols + (long long)j * rows + i) * 32 + (b & 31);
+    }
+    __device__ __forceinline__ float get(int b, int i, int j) const { return p[off(b, i, j)]; }
+    __device__ __forceinline__ void set(int b, int i, int j, float v) const { p[off(b, i, j)] = v; }
+    // Packed column-major: the whole batch is one contiguous array.
+    __host__ __device__ __forceinline__ bool packed() const {
+        return layout == GLASS_LAYOUT_COLMAJOR && ld == rows && s == (long long)rows * cols;
+    }
+};
+
+// ------------------------------------------------------------- team sync
+// T == 1: a lone thread; T == 32: a warp; T > 32: a named barrier shared by
+// the T threads of one team (barrier 0 is left to __syncthreads).
+template <int T>
+__device__ __forceinline__ void team_sync(int bar_id) {
+    if constexpr (T == 32) {
+        __syncwarp();
+    } else if constexpr (T > 32) {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(T) : "memory");
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GLASS_FULL_MASK, v, o);
+    return v;
+}
+
+// Odd per-problem stride in shared memory: problem t's element e sits at
+// t*S + e, so 32 threads reading the same e hit 32 distinct banks.
+__host__ __device__ __forceinline__ int odd_stride(int per) { return per | 1; }
+
+// q = e / d, r = e % d for 0 <= e < 2^24 using a float reciprocal and one
+// correction step (exact: the fractional distance to the next integer is at
+// least 1/d, far above the float rounding of e * (1/d) at these sizes).
+__device__ __forceinline__ void divmod_small(int e, int d, float inv_d, int &q, int &r) {
+    q = __float2int_rz(((float)e + 0.5f) * inv_d);
+    r = e - q * d;
+    if (r < 0) { --q; r += d; }
+    else if (r >= d) { ++q; r -= d; }
+}
+
+// --------------------------------------------------------------- staging
+// Copy problems b0 .. b0+cnt-1 of M (rows x cols each) into shared memory,
+// problem p at sm + p*S, column-major with leading dimension `rows`.  Uses
+// 16-byte streaming loads when the batch is packed and aligned.  All
+// threads of the CTA take part; the caller synchronises afterwards.
+__device__ __forceinline__ void stage_in(float *sm, int S, const Mat &M, int b0, int cnt) {
+    const int per = M.rows * M.cols;
+    const int total = cnt * per;
+    const float inv = 1.0f / (float)per;
+    if (M.packed()) {
+        const float *g = M.p + (long long)b0 * per;
+        if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+            const int nv = total >> 2;
+            const float4 *g4 = reinterpret_cast<const float4 *>(g);
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                float4 x = __ldcs(g4 + v);
+                int p, q;
+                divmod_small(v * 4, per, inv, p, q);
+                float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    sm[p * S + q] = xs[u];
+                    if (++q == per) { q = 0; ++p; }
+                }
+            }
+            for (int e = (nv << 2) + threadIdx.x; e < total; e += blockDim.x) {
+                int p, q;
+                divmod_small(e, per, inv, p, q);
+                sm[p * S + q] = __ldcs(g + e);
+            }
+        } else {
+            for (int e = threadIdx.x; e < total; e += blockDim.x) {
+                int p, q;
+                divmod_small(e, per, inv, p, q);
+                sm[p * S + q] = __ldcs(g + e);
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            int p, q;
+            divmod_small(e, per, inv, p, q);
+            const int j = q / M.rows, i = q - j * M.rows;
+            sm[p * S + q] = M.get(b0 + p, i, j);
+        }
+    }
+}
+
+// Inverse of stage_in: write the staged problems back to M.
+__device__ __forceinline__ void stage_out(const float *sm, int S, const Mat &M, int b0, int cnt) {
+    const int per = M.rows * M.cols;
+    const int total = cnt * per;
+    const float inv = 1.0f / (float)per;
+    if (M.packed()) {
+        float *g = M.p + (long long)b0 * per;
+        if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+            const int nv = total >> 2;
+            float4 *g4 = reinterpret_cast<float4 *>(g);
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                int p, q;
+                divmod_small(v * 4, per, inv, p, q);
+                float xs[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    xs[u] = sm[p * S + q];
+                    if (++q == per) { q = 0; ++p; }
+                }
+                __stcs(g4 + v, make_float4(xs[0], xs[1], xs[2], xs[3]));
+            }
+            for (int e = (nv << 2) + threadIdx.x; e < total; e += blockDim.x) {
+                int p, q;
+                divmod_small(e, per, inv, p, q);
+                __stcs(g + e, sm[p * S + q]);
+            }
+        } else {
+            for (int e = threadIdx.x; e < total; e += blockDim.x) {
+                int p, q;
+                divmod_small(e, per, inv, p, q);
+                __stcs(g + e, sm[p * S + q]);
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            int p, q;
+            divmod_small(e, per, inv, p, q);
+            const int j = q / M.rows, i = q - j * M.rows;
+            M.set(b0 + p, i, j, sm[p * S + q]);
+        }
+    }
+}
+
+// Diagonal square root and reciprocal of a Cholesky pivot d > 0, in FP32 or
+// (fp64 == true) in FP64 rounded once to FP32.
+__device__ __forceinline__ void chol_diag(float d, bool fp64, float &l, float &r) {
+    if (fp64) {
+        const double s = sqrt((double)d);
+        l = (float)s;
+        r = (float)(1.0 / s);
+    } else {
+        l = sqrtf(d);
+        r = 1.0f / l;
+    }
+}
+
+// ------------------------------------------------------- launch helpers
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Problems per CTA and threads per CTA of a placement for a team size T.
+struct Geometry {
+    int per_cta;   // problems per CTA
+    int threads;   // threads per CTA
+    int grid;      // CTAs
+};
+
+// Team size of the block scope for an operation of order n.
+inline int block_team(int n) { return n <= 16 ? 64 : (n <= 32 ? 128 : 256); }
+
+// --------------------------------------------------- launchers (by file)
+// Each returns cudaSuccess or the launch error; none allocates or syncs.
+// k_chol.cu
+cudaError_t launch_potrf(int n, Mat A, int *info, int batch, Placement pl, int fp64diag,
+                         cudaStream_t st);
+cudaError_t launch_potrs(int n, int nrhs, Mat L, Mat B, int batch, Placement pl, cudaStream_t st);
+cudaError_t launch_trsm(int n, int nrhs, Mat L, Mat B, int batch, Placement pl, cudaStream_t st);
+cudaError_t launch_posv(int n, int nrhs, Mat A, Mat B, int *info, int batch, Placement pl,
+                        int fp64diag, int refine, cudaStream_t st);
+size_t smem_chol(int op, int n, int nrhs, Placement pl);
+bool feasible_chol(int op, int n, int nrhs, Placement pl);
+// k_lu.cu
+cudaError_t launch_getrf_getrs(int n, int nrhs, Mat A, int *ipiv, Mat B, int *info, int batch,
+                               Placement pl, cudaStream_t st);
+bool feasible_lu(int n, int nrhs, Placement pl);
+// k_gemm.cu
+cudaError_t launch_gemm(int m, int n, int k, Mat A, Mat B, Mat C, int batch, Placement pl,
+                        cudaStream_t st);
+bool feasible_gemm(int m, int n, int k, Placement pl);
+// k_gemm_tc.cu
+cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float *C, int batch,
+                           cudaStream_t st);
+// k_geom.cu
+cudaError_t launch_rot3(int chain, Mat Rs, Mat R, int batch, Placement pl, cudaStream_t st);
+cudaError_t launch_se3(int chain, Mat T, int npts, Mat P, Mat Q, int batch, Placement pl,
+                       cudaStream_t st);
+bool feasible_geom(int op, int chain, Placement pl);
+cudaError_t launch_to_interleaved(int rows, int cols, const float *src, float *dst, int batch,
+                                  cudaStream_t st);
+cudaError_t launch_from_interleaved(int rows, int cols, const float *src, float *dst, int batch,
+                                    cudaStream_t st);
+// k_varsize.cu
+size_t varsize_workspace(int batch);
+cudaError_t launch_posv_varsize(int batch, const int *n_dev, const long long *offA,
+                                const long long *offB, int nrhs, float *A, float *B, int *info,
+                                void *ws, int warps_per_cta, unsigned *status, cudaStream_t st);
+// k_mlp.cu
+size_t mlp_workspace(int rows);
+cudaError_t launch_mlp_forward(int din, const float *w, int rows, const float *X, float *Y,
+                               cudaStream_t st);
+cudaError_t launch_mlp_loss_grad(int din, const float *w, int rows, const float *X,
+                                 const float *T, const float *M, float *grad, float *loss,
+                                 void *ws, cudaStream_t st);
+cudaError_t launch_mlp_adam(int np, float *w, const float *g, float *m, float *v, int t,
+                            float lr, float b1, float b2, float eps, cudaStream_t st);
+
+}  // namespace glass

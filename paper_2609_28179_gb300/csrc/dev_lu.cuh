@@ -1,0 +1,334 @@
+// dev_lu.cuh -- LU factorization with partial pivoting and the matching
+// solve, at thread, warp and block scope (Sec. III-A scopes; Sec. III-B
+// "factorizations, and linear solves").
+//
+// Pivot rule (all scopes): at step j the row with the largest |a_ij| among
+// the rows still to be eliminated wins, the smallest current row index on
+// ties; ipiv[j] records the exchanged row in sequential-swap form.
+//
+// Warp scope keeps every row in the registers of one lane and never moves
+// it: a pivot exchange only relabels logical positions (pos[]), the
+// multipliers stay with their physical row, and the final packed factor is
+// written out row by row at each row's logical position.  This is the same
+// factorization as the explicit-swap algorithm (rows carry their
+// multipliers with them in both), without 2n shuffles per exchange.
+#pragma once
+
+#include "common.cuh"
+
+namespace glass {
+namespace thread {
+
+// Full n x n matrix a[i][k] in registers.  piv[j] = row exchanged at step j,
+// rinv[j] = 1 / u_jj.  Returns info (first exactly-zero pivot).
+template <int NMAX, bool EXACT>
+__device__ __forceinline__ int getrf(float (&a)[NMAX][NMAX], int (&piv)[NMAX], float (&rinv)[NMAX], int n_rt) {
+    const int n = EXACT ? NMAX : n_rt;
+    int info = 0;
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+            int p = j;
+            float best = fabsf(a[j][j]);
+#pragma unroll
+            for (int r = j + 1; r < NMAX; ++r)
+                if (r < n) {
+                    const float v = fabsf(a[r][j]);
+                    if (v > best) { best = v; p = r; }
+                }
+            piv[j] = p;
+            // exchange rows j and p (p >= j, a runtime index: select chains)
+#pragma unroll
+            for (int c = 0; c < NMAX; ++c) {
+                const float vj = a[j][c];
+                float vp = vj;
+#pragma unroll
+                for (int r = j + 1; r < NMAX; ++r)
+                    if (r == p) vp = a[r][c];
+#pragma unroll
+                for (int r = j + 1; r < NMAX; ++r)
+                    if (r == p) a[r][c] = vj;
+                a[j][c] = vp;
+            }
+            const float pv = a[j][j];
+            if (pv == 0.f) {
+                if (info == 0) info = j + 1;
+                rinv[j] = 0.f;
+            } else {
+                const float rc = 1.0f / pv;
+                rinv[j] = rc;
+#pragma unroll
+                for (int r = j + 1; r < NMAX; ++r) {
+                    if (r < n) {
+                        a[r][j] *= rc;
+#pragma unroll
+                        for (int c = j + 1; c < NMAX; ++c)
+                            if (c < n) a[r][c] = fmaf(-a[r][j], a[j][c], a[r][c]);
+                    }
+                }
+            }
+        }
+    }
+    return info;
+}
+
+// x <- U^{-1} L^{-1} P x for one right-hand side.
+template <int NMAX, bool EXACT>
+__device__ __forceinline__ void getrs(const float (&a)[NMAX][NMAX], const int (&piv)[NMAX], const float (&rinv)[NMAX],
+                                      float (&x)[NMAX], int n_rt) {
+    const int n = EXACT ? NMAX : n_rt;
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+            const int p = piv[j];
+            float vp = x[j];
+#pragma unroll
+            for (int r = j + 1; r < NMAX; ++r)
+                if (r == p) vp = x[r];
+#pragma unroll
+            for (int r = j + 1; r < NMAX; ++r)
+                if (r == p) x[r] = x[j];
+            x[j] = vp;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i)
+        if (i < n)
+#pragma unroll
+            for (int r = i + 1; r < NMAX; ++r)
+                if (r < n) x[r] = fmaf(-a[r][i], x[i], x[r]);
+#pragma unroll
+    for (int i = NMAX - 1; i >= 0; --i)
+        if (i < n) {
+            x[i] *= rinv[i];
+#pragma unroll
+            for (int r = 0; r < i; ++r) x[r] = fmaf(-a[r][i], x[i], x[r]);
+        }
+}
+
+}  // namespace thread
+
+namespace warp {
+
+// Sort key of a pivot candidate: larger |v| first, then smaller logical
+// position; the low bits carry the physical row.  0 = not a candidate.
+__device__ __forceinline__ unsigned long long piv_key(float absv, int pos, int phys) {
+    return ((unsigned long long)__float_as_uint(absv) << 32) | (1u << 12) | ((unsigned)(63 - pos) << 6) |
+           (unsigned)phys;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(GLASS_FULL_MASK, k, o);
+        k = v > k ? v : k;
+    }
+    return k;
+}
+
+template <int NMAX>
+struct LU {
+    static constexpr int R = (NMAX + 31) / 32;
+};
+
+// Rows lane+32q in a[q][*]; pos[q] receives each row's final logical
+// position; pp[j] = physical row chosen at step j; prc[j] = 1 / u_jj.
+// ipiv_out (may be null) receives ipiv[0..n).  Returns info (uniform).
+template <int NMAX>
+__device__ __forceinline__ int getrf(float (&a)[LU<NMAX>::R][NMAX], int (&pos)[LU<NMAX>::R], int (&pp)[NMAX],
+                                     float (&prc)[NMAX], int *ipiv_out, int n) {
+    constexpr int R = LU<NMAX>::R;
+    const int lane = threadIdx.x & 31;
+    bool done[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) { pos[q] = lane + 32 * q; done[q] = false; }
+    int info = 0;
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+            unsigned long long key = 0;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = lane + 32 * q;
+                if (!done[q] && i < n) {
+                    const unsigned long long kq = piv_key(fabsf(a[q][j]), pos[q], i);
+                    key = kq > key ? kq : key;
+                }
+            }
+            key = warp_max_u64(key);
+            const int pphys = (int)(key & 63u);
+            const int ppos = 63 - (int)((key >> 6) & 63u);
+            if (ipiv_out != nullptr && lane == 0) ipiv_out[j] = ppos;
+            pp[j] = pphys;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = lane + 32 * q;
+                if (pos[q] == j) pos[q] = ppos;
+                if (i == pphys) { pos[q] = j; done[q] = true; }
+            }
+            const int pq = pphys >> 5, pl = pphys & 31;
+            float pvsel = a[0][j];
+#pragma unroll
+            for (int q = 1; q < R; ++q)
+                if (pq == q) pvsel = a[q][j];
+            const float pv = __shfl_sync(GLASS_FULL_MASK, pvsel, pl);
+            if (pv == 0.f) {
+                if (info == 0) info = j + 1;
+                prc[j] = 0.f;
+                continue;
+            }
+            const float rc = 1.0f / pv;
+            prc[j] = rc;
+            float m[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                m[q] = a[q][j] * rc;
+                if (!done[q]) a[q][j] = m[q];
+            }
+#pragma unroll
+            for (int k = j + 1; k < NMAX; ++k) {
+                if (k < n) {
+                    float sel = a[0][k];
+#pragma unroll
+                    for (int q = 1; q < R; ++q)
+                        if (pq == q) sel = a[q][k];
+                    const float pk = __shfl_sync(GLASS_FULL_MASK, sel, pl);
+#pragma unroll
+                    for (int q = 0; q < R; ++q)
+                        if (!done[q]) a[q][k] = fmaf(-m[q], pk, a[q][k]);
+                }
+            }
+        }
+    }
+    return info;
+}
+
+// One right-hand side held by physical row (x[q] = b of row lane+32q, the
+// row's ORIGINAL index): on return x[q] is the solution component at
+// logical position pos[q].
+template <int NMAX>
+__device__ __forceinline__ void getrs(const float (&a)[LU<NMAX>::R][NMAX], const int (&pos)[LU<NMAX>::R],
+                                      const int (&pp)[NMAX], const float (&prc)[NMAX], float (&x)[LU<NMAX>::R],
+                                      int n) {
+    constexpr int R = LU<NMAX>::R;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+            const int pq = pp[j] >> 5;
+            float sel = x[0];
+#pragma unroll
+            for (int q = 1; q < R; ++q)
+                if (pq == q) sel = x[q];
+            const float yj = __shfl_sync(GLASS_FULL_MASK, sel, pp[j] & 31);
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+                if (pos[q] > j && lane + 32 * q < n) x[q] = fmaf(-a[q][j], yj, x[q]);
+        }
+    }
+#pragma unroll
+    for (int j = NMAX - 1; j >= 0; --j) {
+        if (j < n) {
+            const int pq = pp[j] >> 5;
+            float sel = x[0];
+#pragma unroll
+            for (int q = 1; q < R; ++q)
+                if (pq == q) sel = x[q];
+            const float xj = __shfl_sync(GLASS_FULL_MASK, sel, pp[j] & 31) * prc[j];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = lane + 32 * q;
+                if (i == pp[j]) x[q] = xj;
+                else if (pos[q] < j && i < n) x[q] = fmaf(-a[q][j], xj, x[q]);
+            }
+        }
+    }
+}
+
+}  // namespace warp
+
+namespace block {
+
+// Team LU in shared memory (column-major, leading dimension lda).  Per
+// step: the team's first warp finds the pivot, then the exchange and the
+// column scaling, then the trailing update, each phase closed by the team
+// barrier.  sc: 4 words of team scratch in shared memory.
+template <int T>
+__device__ __forceinline__ int getrf(float *a, int lda, int n, int *piv_s, float *rinv_s, int rank, int bar,
+                                     float *sc) {
+    constexpr int TI = T >= 64 ? 64 : T;
+    constexpr int TK = T / TI;
+    const int ti = rank % TI, tk = rank / TI;
+    int info = 0;
+    for (int j = 0; j < n; ++j) {
+        if (rank < 32) {
+            unsigned long long key = 0;
+            for (int i = j + rank; i < n; i += 32) {
+                const unsigned long long k = warp::piv_key(fabsf(a[j * lda + i]), i, i);
+                key = k > key ? k : key;
+            }
+            key = warp::warp_max_u64(key);
+            if (rank == 0) {
+                const int p = (int)(key & 63u);
+                piv_s[j] = p;
+                sc[0] = a[j * lda + j];  // old a_jj (moves to row p)
+                sc[1] = a[j * lda + p];  // the pivot value
+            }
+        }
+        team_sync<T>(bar);
+        const int p = piv_s[j];
+        const float old_jj = sc[0], pv = sc[1];
+        const float rc = pv != 0.f ? 1.0f / pv : 0.f;
+        if (pv == 0.f && info == 0) info = j + 1;
+        // exchange rows j and p in every column but j; column j is rewritten
+        // with the scaled multipliers directly.
+        if (p != j)
+            for (int c = rank; c < n; c += T)
+                if (c != j) {
+                    const float t = a[c * lda + j];
+                    a[c * lda + j] = a[c * lda + p];
+                    a[c * lda + p] = t;
+                }
+        if (pv != 0.f)
+            for (int i = j + 1 + rank; i < n; i += T) {
+                const float v = (i == p) ? old_jj : a[j * lda + i];
+                a[j * lda + i] = v * rc;
+            }
+        if (rank == 0) { a[j * lda + j] = pv; rinv_s[j] = rc; }
+        team_sync<T>(bar);
+        if (pv != 0.f)
+            for (int k = j + 1 + tk; k < n; k += TK) {
+                const float ujk = a[k * lda + j];
+                for (int i = j + 1 + ti; i < n; i += TI) a[k * lda + i] = fmaf(-a[j * lda + i], ujk, a[k * lda + i]);
+            }
+        team_sync<T>(bar);
+    }
+    return info;
+}
+
+// One right-hand side x (shared): swaps, unit-lower forward, upper backward.
+template <int T>
+__device__ __forceinline__ void getrs(const float *a, int lda, const int *piv_s, const float *rinv_s, float *x, int n,
+                                      int rank, int bar) {
+    if (rank == 0)
+        for (int j = 0; j < n; ++j) {
+            const int p = piv_s[j];
+            if (p != j) { const float t = x[j]; x[j] = x[p]; x[p] = t; }
+        }
+    team_sync<T>(bar);
+    for (int i = 0; i < n; ++i) {
+        const float yi = x[i];
+        for (int r = i + 1 + rank; r < n; r += T) x[r] = fmaf(-a[i * lda + r], yi, x[r]);
+        team_sync<T>(bar);
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        const float xi = x[i] * rinv_s[i];
+        for (int r = rank; r < i; r += T) x[r] = fmaf(-a[i * lda + r], xi, x[r]);
+        team_sync<T>(bar);
+        if (rank == 0) x[i] = xi;
+    }
+    team_sync<T>(bar);
+}
+
+}  // namespace block
+}  // namespace glass

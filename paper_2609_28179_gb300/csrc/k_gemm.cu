@@ -1,0 +1,240 @@
+// k_gemm.cu -- batched SIMT GEMM C = A B (FP32) at thread, warp and block
+// scope (Sec. III-B BLAS-3; the GEMM family of Sec. IV-D).
+//
+// Thread scope: one product per thread; A in registers, B and C streamed a
+// column at a time through the CTA's staging buffers.
+// Warp / block scope: a team of T threads per product.  A (column-major)
+// and B (transposed, so that a row of B is contiguous) are staged into the
+// team's shared memory with coalesced loads; each thread accumulates a
+// TM x TN register tile of C from 16-byte shared-memory fragments (the
+// warp's lanes share rows and columns, so fragments are mostly broadcasts);
+// C goes back through shared memory for fully coalesced streaming stores.
+#include "common.cuh"
+
+namespace glass {
+namespace {
+
+// ------------------------------------------------------------ thread scope
+template <int NMAX, bool EXACT>
+__global__ void __launch_bounds__(256) k_gemm_thread(int m_rt, int n_rt, int k_rt, Mat A, Mat B, Mat C, int batch) {
+    extern __shared__ float smem[];
+    const int m = EXACT ? NMAX : m_rt, n = EXACT ? NMAX : n_rt, k = EXACT ? NMAX : k_rt;
+    const int G = blockDim.x;
+    const int b0 = blockIdx.x * G;
+    const int cnt = min(G, batch - b0);
+    const int t = threadIdx.x;
+    const bool staged = A.layout == GLASS_LAYOUT_COLMAJOR;
+    const int SA = odd_stride(m * k), SB = odd_stride(k * n), SC = odd_stride(m * n);
+    float *sa = smem, *sb = sa + G * SA, *sc = sb + G * SB;
+    if (staged) {
+        stage_in(sa, SA, A, b0, cnt);
+        stage_in(sb, SB, B, b0, cnt);
+        __syncthreads();
+    }
+    if (t < cnt) {
+        const int b = b0 + t;
+        float a[NMAX][NMAX];
+#pragma unroll
+        for (int l = 0; l < NMAX; ++l)
+#pragma unroll
+            for (int i = 0; i < NMAX; ++i)
+                a[i][l] = (i < m && l < k) ? (staged ? sa[t * SA + l * m + i] : A.get(b, i, l)) : 0.f;
+        for (int j = 0; j < n; ++j) {
+            float bc[NMAX];
+#pragma unroll
+            for (int l = 0; l < NMAX; ++l) bc[l] = (l < k) ? (staged ? sb[t * SB + j * k + l] : B.get(b, l, j)) : 0.f;
+#pragma unroll
+            for (int i = 0; i < NMAX; ++i) {
+                if (i < m) {
+                    float c = 0.f;
+#pragma unroll
+                    for (int l = 0; l < NMAX; ++l)
+                        if (l < k) c = fmaf(a[i][l], bc[l], c);
+                    if (staged) sc[t * SC + j * m + i] = c;
+                    else C.set(b, i, j, c);
+                }
+            }
+        }
+    }
+    if (staged) {
+        __syncthreads();
+        stage_out(sc, SC, C, b0, cnt);
+    }
+}
+
+// ------------------------------------------------------ warp / block scope
+// Thread tile of a team of T threads on an NMAX x NMAX product.
+template <int NMAX, int T>
+struct Tile {
+    static constexpr int area = NMAX * NMAX / T;  // C elements per thread
+    static constexpr int TM = area >= 64 ? 8 : (area >= 16 ? 4 : (area >= 4 ? 2 : 1));
+    static constexpr int TN = area / TM;
+    static constexpr int RG = NMAX / TM;  // row groups
+    static constexpr int CG = NMAX / TN;  // column groups
+    static_assert(RG * CG == T, "tile does not cover the product");
+    static constexpr int LD = NMAX + 4;  // smem leading dimension (16-byte rows)
+    static constexpr int per = 2 * NMAX * LD;  // floats of staging per team
+};
+
+template <int N>
+__device__ __forceinline__ void load_frag(float (&r)[N], const float *p) {
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int u = 0; u < N; u += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p + u);
+            r[u] = v.x; r[u + 1] = v.y; r[u + 2] = v.z; r[u + 3] = v.w;
+        }
+    } else if constexpr (N == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        r[0] = v.x; r[1] = v.y;
+    } else {
+#pragma unroll
+        for (int u = 0; u < N; ++u) r[u] = p[u];
+    }
+}
+
+template <int NMAX, int T>
+__global__ void __launch_bounds__(256) k_gemm_team(int m, int n, int k, Mat A, Mat B, Mat C, int batch) {
+    using TL = Tile<NMAX, T>;
+    extern __shared__ __align__(16) float smem[];
+    const int team = threadIdx.x / T, rank = threadIdx.x % T;
+    const int P = blockDim.x / T;
+    const int b = blockIdx.x * P + team;
+    const int bar = 1 + team;
+    float *As = smem + team * TL::per;        // As[l*LD + i] = A(i, l)
+    float *Bt = As + NMAX * TL::LD;           // Bt[l*LD + j] = B(l, j)
+    if (b >= batch) return;
+    // stage (zero padding outside m x k / k x n)
+    const bool pk = A.packed() && B.packed();
+    for (int e = rank; e < NMAX * NMAX; e += T) {
+        const int l = e / NMAX, i = e - l * NMAX;
+        float v = 0.f;
+        if (i < m && l < k) v = pk ? __ldcs(A.p + (long long)b * A.s + l * m + i) : A.get(b, i, l);
+        As[l * TL::LD + i] = v;
+    }
+    for (int e = rank; e < NMAX * NMAX; e += T) {
+        const int j = e / NMAX, l = e - j * NMAX;
+        float v = 0.f;
+        if (l < k && j < n) v = pk ? __ldcs(B.p + (long long)b * B.s + j * k + l) : B.get(b, l, j);
+        Bt[l * TL::LD + j] = v;
+    }
+    team_sync<T>(bar);
+    const int rg = rank / TL::CG, cg = rank % TL::CG;
+    const int i0 = rg * TL::TM, j0 = cg * TL::TN;
+    float acc[TL::TM][TL::TN];
+#pragma unroll
+    for (int r = 0; r < TL::TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TL::TN; ++c) acc[r][c] = 0.f;
+#pragma unroll 4
+    for (int l = 0; l < NMAX; ++l) {
+        float af[TL::TM], bf[TL::TN];
+        load_frag<TL::TM>(af, As + l * TL::LD + i0);
+        load_frag<TL::TN>(bf, Bt + l * TL::LD + j0);
+#pragma unroll
+        for (int r = 0; r < TL::TM; ++r)
+#pragma unroll
+            for (int c = 0; c < TL::TN; ++c) acc[r][c] = fmaf(af[r], bf[c], acc[r][c]);
+    }
+    team_sync<T>(bar);
+    // C tile -> shared (column-major, ld = m) -> coalesced stores
+    float *Cs = As;
+#pragma unroll
+    for (int c = 0; c < TL::TN; ++c)
+#pragma unroll
+        for (int r = 0; r < TL::TM; ++r) {
+            const int i = i0 + r, j = j0 + c;
+            if (i < m && j < n) Cs[j * m + i] = acc[r][c];
+        }
+    team_sync<T>(bar);
+    if (C.packed()) {
+        float *g = C.p + (long long)b * C.s;
+        const int tot = m * n;
+        if (((reinterpret_cast<uintptr_t>(g) & 15) == 0) && (tot & 3) == 0) {
+            for (int v = rank; v < (tot >> 2); v += T)
+                __stcs(reinterpret_cast<float4 *>(g) + v, *reinterpret_cast<const float4 *>(Cs + 4 * v));
+        } else {
+            for (int e = rank; e < tot; e += T) __stcs(g + e, Cs[e]);
+        }
+    } else {
+        for (int e = rank; e < m * n; e += T) {
+            const int j = e / m, i = e - j * m;
+            C.set(b, i, j, Cs[e]);
+        }
+    }
+}
+
+template <typename K>
+cudaError_t go(K kern, int grid, int threads, size_t smem, cudaStream_t st, int m, int n, int k, const Mat &A,
+               const Mat &B, const Mat &C, int batch) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, threads, smem, st>>>(m, n, k, A, B, C, batch);
+    return cudaPeekAtLastError();
+}
+
+constexpr size_t kMaxSmem = 227 * 1024;
+
+int bucket(int d) { return d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : 64; }
+
+// Team size of a scope for bucket N.
+int team_of(int scope, int N) {
+    if (scope == SCOPE_WARP) return 32;
+    return N <= 16 ? 64 : (N <= 32 ? 128 : 256);
+}
+
+size_t smem_gemm(int m, int n, int k, Placement pl) {
+    const int N = bucket(m > n ? (m > k ? m : k) : (n > k ? n : k));
+    if (pl.scope == SCOPE_THREAD)
+        return (size_t)32 * pl.pack * (odd_stride(m * k) + odd_stride(k * n) + odd_stride(m * n)) * 4;
+    return (size_t)pl.pack * 2 * N * (N + 4) * 4;
+}
+
+}  // namespace
+
+bool feasible_gemm(int m, int n, int k, Placement pl) {
+    if (m < 1 || n < 1 || k < 1 || m > 64 || n > 64 || k > 64) return false;
+    if (pl.pack != 1 && pl.pack != 2 && pl.pack != 4 && pl.pack != 8) return false;
+    const int N = bucket(m > n ? (m > k ? m : k) : (n > k ? n : k));
+    if (pl.scope == SCOPE_THREAD && N > 8 && !(m == n && n == k && m <= 12)) return false;
+    if (pl.scope != SCOPE_THREAD && team_of(pl.scope, N) * pl.pack > 256) return false;
+    if (pl.scope == SCOPE_WARP && N < 8) return false;
+    return smem_gemm(m, n, k, pl) <= kMaxSmem;
+}
+
+cudaError_t launch_gemm(int m, int n, int k, Mat A, Mat B, Mat C, int batch, Placement pl, cudaStream_t st) {
+    if (!feasible_gemm(m, n, k, pl)) return cudaErrorInvalidConfiguration;
+    const size_t smem = smem_gemm(m, n, k, pl);
+    const int N = bucket(m > n ? (m > k ? m : k) : (n > k ? n : k));
+    if (pl.scope == SCOPE_THREAD) {
+        const int G = 32 * pl.pack;
+        const int grid = ceil_div(batch, G);
+        const size_t sm = A.layout == GLASS_LAYOUT_COLMAJOR ? smem : 0;
+        if (m == n && n == k) {
+            switch (n) {
+                case 3: return go(k_gemm_thread<3, true>, grid, G, sm, st, m, n, k, A, B, C, batch);
+                case 6: return go(k_gemm_thread<6, true>, grid, G, sm, st, m, n, k, A, B, C, batch);
+                case 7: return go(k_gemm_thread<7, true>, grid, G, sm, st, m, n, k, A, B, C, batch);
+                case 12: return go(k_gemm_thread<12, true>, grid, G, sm, st, m, n, k, A, B, C, batch);
+                default: break;
+            }
+            if (n > 8) return go(k_gemm_thread<12, false>, grid, G, sm, st, m, n, k, A, B, C, batch);
+        }
+        if (N <= 4 && m <= 4 && n <= 4 && k <= 4)
+            return go(k_gemm_thread<4, false>, grid, G, sm, st, m, n, k, A, B, C, batch);
+        return go(k_gemm_thread<8, false>, grid, G, sm, st, m, n, k, A, B, C, batch);
+    }
+    const int T = team_of(pl.scope, N);
+    const int grid = ceil_div(batch, pl.pack);
+    const int th = T * pl.pack;
+#define GL_G(NN, TT) go(k_gemm_team<NN, TT>, grid, th, smem, st, m, n, k, A, B, C, batch)
+    if (N == 8) return T == 32 ? GL_G(8, 32) : GL_G(8, 64);
+    if (N == 16) return T == 32 ? GL_G(16, 32) : GL_G(16, 64);
+    if (N == 32) return T == 32 ? GL_G(32, 32) : GL_G(32, 128);
+    return T == 32 ? GL_G(64, 32) : GL_G(64, 256);
+#undef GL_G
+}
+
+}  // namespace glass
