@@ -1,0 +1,441 @@
+"""Benchmark of the batched small-matrix hot path on GB300.
+
+One step = one pass over every cell of the placement sweep at the largest
+sweep batch: the six operations {gemm, posv (potrf+potrs), trsm, getrf+getrs,
+rotation-chain compose, SE(3) apply} at n in {3,6,7,12,14,24,32,64} on 16384
+independent problems each (48 launches), every launch with the placement the
+library's measured table selects ("tuned").  The same step with one fixed
+placement (one thread per problem where feasible, else one warp: "plain") is
+timed beside it.
+
+Reported (one JSON line):
+  value       batched matrices/s of the tuned step, inputs resident in HBM;
+  e2e         the same through host buffers (pinned H2D of every input and
+              D2H of every result inside the timed region);
+  roofline    of the dominant kernel (largest share of the step), from CUDA
+              events around its launches;
+  cpu_baseline  the FP64 C oracle on a bounded sample, all host cores;
+  plain       the plain step and the tuned/plain speedup.
+`--impl reference` times the oracle (the reference arm of this task) on the
+same workload, one bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched matrices/s and % of HBM/FP32 roofline, tuned vs plain at 1e-4 rel error"
+BATCH = 16384
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0))}
+    return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 SIMT peak: SMs x 128 FP32 lanes x 2 flop (FFMA) x clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ setup
+def cell_list(ops, sizes, batch):
+    return [(op, n, batch) for op in ops for n in sizes]
+
+
+def plain_placement(cell):
+    import paper_2609_28179_gb300 as g
+    for scope in (g.GLASS_SCOPE_THREAD, g.GLASS_SCOPE_WARP):
+        if cell.feasible(scope, 1):
+            return scope, 1
+    return g.GLASS_SCOPE_BLOCK, 1
+
+
+def resolved_placement(cell):
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300.cells import OP_ID
+    nn = cell.n if cell.op not in ("rot3", "se3") else (3 if cell.op == "rot3" else 4)
+    s, pl = g.glass_get_placement(OP_ID[cell.op], nn, cell.k, cell.batch)
+    g.check(s, "get_placement")
+    return pl
+
+
+def time_steps(cells, placements, steps, warmup, stream_events=True):
+    """Run warmup + steps passes; returns (total_ms, per-cell mean ms)."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    nc = len(cells)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+          for _ in range(nc)]
+    for w in range(warmup):
+        for c, (s, p) in zip(cells, placements):
+            g.check(c.launch(w, s, p), f"{c.op} n={c.n}")
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for st in range(steps):
+        for ci, (c, (s, p)) in enumerate(zip(cells, placements)):
+            ev[ci][st][0].record()
+            c.launch(warmup + st, s, p)
+            ev[ci][st][1].record()
+    t1.record()
+    torch.cuda.synchronize()
+    total = t0.elapsed_time(t1)
+    per = [statistics.mean(a.elapsed_time(b) for a, b in ev[ci]) for ci in range(nc)]
+    return total, per
+
+
+def e2e_steps(cells, steps, warmup):
+    """End to end through the public API with host buffers: per step, pinned
+    H2D of every cell's inputs, the launches, D2H of every result."""
+    import torch
+    pinned_in, pinned_out, outs = [], [], []
+    h2d = d2h = 0
+    for c in cells:
+        pin = {k: torch.from_numpy(v).pin_memory() for k, v in c.host.items()}
+        pinned_in.append(pin)
+        h2d += sum(t.numel() * 4 for t in pin.values())
+        res = []
+        w = c.work[0]
+        if c.op in ("gemm", "rot3", "se3"):
+            res.append(c.out)
+        elif c.op == "posv":
+            res += [w["A"], w["B"], c.info]
+        elif c.op == "trsm":
+            res.append(w["B"])
+        else:
+            res += [w["A"], w["B"], c.ipiv, c.info]
+        outs.append(res)
+        po = [torch.empty(r.shape, dtype=r.dtype).pin_memory() for r in res]
+        pinned_out.append(po)
+        d2h += sum(r.numel() * r.element_size() for r in res)
+
+    def one_step():
+        for c, pin, res, po in zip(cells, pinned_in, outs, pinned_out):
+            w = c.work[0]
+            for k, t in pin.items():
+                w[k].copy_(t, non_blocking=True)
+            c.launch(0)
+            for r, p in zip(res, po):
+                p.copy_(r, non_blocking=True)
+
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        one_step()
+    t1.record()
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1), h2d, d2h
+
+
+# ------------------------------------------------------------ cpu oracle
+def oracle_cell_time(op, n, host, batch, sample):
+    """Seconds the FP64 oracle takes for `sample` problems of a cell."""
+    import numpy as np
+    import oracle
+    from paper_2609_28179_gb300.cells import NPTS, rhs_of
+    k = rhs_of(op, n)
+    s = min(sample, batch)
+    f64 = lambda key, per: host[key][: s * per].astype(np.float64)
+    t = time.perf_counter()
+    if op == "gemm":
+        oracle.gemm(n, n, n, f64("A", n * n), f64("B", n * n), s)
+    elif op == "posv":
+        oracle.posv(n, 1, f64("A", n * n), f64("B", n), s)
+    elif op == "trsm":
+        oracle.trsm(n, k, f64("A", n * n), f64("B", n * k), s)
+    elif op == "getrf_getrs":
+        oracle.getrf_getrs(n, 1, f64("A", n * n), f64("B", n), s)
+    elif op == "rot3":
+        oracle.rot3_compose(k, f64("A", 9 * k), s)
+    elif op == "se3":
+        oracle.se3_apply(k, f64("A", 16 * k), NPTS, f64("B", 3 * NPTS), s)
+    return time.perf_counter() - t, s
+
+
+def cpu_baseline(hosts, ops_sizes, batch, budget_s=12.0):
+    """Oracle matrices/s over the step's cells, each on an adaptively sized
+    sample (scaled to the full batch)."""
+    import oracle
+    oracle.build()
+    per_cell = budget_s / max(1, len(ops_sizes))
+    full_time, samples = 0.0, []
+    for (op, n), host in zip(ops_sizes, hosts):
+        sample = 16
+        while True:
+            dt, s = oracle_cell_time(op, n, host, batch, sample)
+            if dt >= per_cell * 0.5 or s >= batch:
+                break
+            sample = min(batch, sample * max(2, int(per_cell * 0.6 / max(dt, 1e-4))))
+        full_time += dt / s * batch
+        samples.append(f"{op}{n}:{s}")
+    value = len(ops_sizes) * batch / full_time
+    return {"value": value, "unit": "matrices/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"per cell an adaptive prefix of the {batch} problems ({', '.join(samples)}), "
+                      f"scaled to the full batch"}
+
+
+# ------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2609_28179_gb300.cells import make_inputs
+    oracle.build()
+    ops_sizes = [(op, n) for op, n, _ in cell_list(args.ops, args.sizes, args.batch)]
+    sample = max(1, args.batch // args.ref_sample_div)
+    hosts = [make_inputs(op, n, sample, 1002) for op, n in ops_sizes]
+    times = []
+    for st in range(args.warmup + args.steps):
+        t = 0.0
+        for (op, n), h in zip(ops_sizes, hosts):
+            dt, _ = oracle_cell_time(op, n, h, sample, sample)
+            t += dt
+        if st >= args.warmup:
+            times.append(t)
+    per_step = statistics.mean(times)
+    problems = sample * len(ops_sizes)
+    value = problems / per_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, sample_note=f"oracle sample of {sample} problems per cell"),
+            "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{sample} of {args.batch} problems per cell, every cell, each step"},
+            "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_of(args, sample_note=None):
+    c = {"workload": f"placement sweep: {len(args.ops)} ops x n in {args.sizes} (chain length for rot3/se3, "
+                     f"1024 points for se3), batch {args.batch} per cell, tuned placements",
+         "ops": args.ops, "sizes": args.sizes, "batch": args.batch,
+         "rhs": "posv/getrs 1, trsm n, gemm square n x n x n",
+         "l2": "step working set > 1 GB >> 129 MB L2; destructive cells read a fresh input copy every step"}
+    if sample_note:
+        c["sample"] = sample_note
+    return c
+
+
+def kernel_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2609_28179_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or
+    None when the kernels changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d.get("cells", {}).get(kernel_key)
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="glass", choices=["glass", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--ops", nargs="+", default=None)
+    ap.add_argument("--sizes", nargs="+", type=int, default=None)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-sample-div", type=int, default=64)
+    args = ap.parse_args()
+    from paper_2609_28179_gb300.cells import OPS, SWEEP_N
+    args.ops = args.ops or OPS
+    args.sizes = args.sizes or SWEEP_N
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2609_28179_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300.cells import Cell
+    g.lib()
+
+    sets = args.steps + args.warmup
+    cells = [Cell(op, n, b, sets=sets) for op, n, b in cell_list(args.ops, args.sizes, args.batch)]
+    tuned = [resolved_placement(c) for c in cells]
+    plain = [plain_placement(c) for c in cells]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # tuned step (the headline), clocks sampled during the timed region
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as cs:
+        t_tuned, per_tuned = time_steps(cells, tuned, args.steps, args.warmup)
+    clocks = cs.summary()
+    barrier()
+    for c in cells:
+        c.restore()
+    torch.cuda.synchronize()
+    t_plain, per_plain = time_steps(cells, plain, args.steps, args.warmup)
+    t_e2e = h2d = d2h = None
+    if not args.no_e2e:
+        t_e2e, h2d, d2h = e2e_steps(cells, args.steps, args.warmup)
+
+    def maxr(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t_tuned, t_plain = maxr(t_tuned), maxr(t_plain)
+    if t_e2e is not None:
+        t_e2e = maxr(t_e2e)
+    problems = len(cells) * args.batch * world
+    ms_step = t_tuned / args.steps
+    value = problems * args.steps / (t_tuned / 1e3)
+
+    peaks = load_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = fp32_peak_tflops(sms, peaks["sm_max_mhz"])
+    rows = []
+    for c, (s, p), us_t, (ps, pp), us_p in zip(cells, tuned, per_tuned, plain, per_plain):
+        t_bw = c.bytes / (peaks["hbm_gbs"] * 1e9)
+        t_fl = c.flops / (fp32_peak * 1e12)
+        bound = "hbm" if t_bw >= t_fl else "alu"
+        t_roof = max(t_bw, t_fl)
+        rows.append({"op": c.op, "n": c.n, "placement": f"{g.SCOPE_NAMES[s]}x{p}", "us": round(us_t * 1e3, 2),
+                     "matrices_per_s": c.batch / (us_t / 1e3), "gbs": c.bytes / (us_t / 1e3) / 1e9,
+                     "gflops": c.flops / (us_t / 1e3) / 1e9, "bound": bound,
+                     "frac": t_roof / (us_t / 1e3), "plain": f"{g.SCOPE_NAMES[ps]}x{pp}",
+                     "plain_us": round(us_p * 1e3, 2), "speedup_vs_plain": us_p / us_t})
+    dom = max(range(len(cells)), key=lambda i: per_tuned[i])
+    dc, dr = cells[dom], rows[dom]
+    dur = per_tuned[dom] / 1e3
+    if dr["bound"] == "hbm":
+        roof = {"bound": "hbm", "achieved": dc.bytes / dur / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        roof = {"bound": "alu", "achieved": dc.flops / dur / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["peak_src"] = (f"{peaks['src']} HBM copy" if roof["bound"] == "hbm" else
+                        f"FP32 SIMT {sms} SMs x 128 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz")
+    key = f"{dc.op}:{dc.n}:{dr['placement']}"
+    roof["kernel"] = key
+    roof["traffic"] = traffic_for(key)
+    roof["step_share"] = per_tuned[dom] / sum(per_tuned)
+    line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(args), "roofline": roof, "gpu_launches": len(cells) * args.steps,
+            "clocks": clocks,
+            "plain": {"value": problems * args.steps / (t_plain / 1e3), "ms_per_step": t_plain / args.steps,
+                      "speedup_tuned_over_plain": t_plain / t_tuned},
+            "hbm_weighted_frac": sum(r["frac"] * r["us"] for r in rows) / sum(r["us"] for r in rows)}
+    if t_e2e is not None:
+        line["e2e"] = {"value": problems * args.steps / (t_e2e / 1e3), "unit": "matrices/s",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": t_e2e / args.steps}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline([c.host for c in cells], [(c.op, c.n) for c in cells], args.batch)
+    line["cells"] = rows
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -182,6 +182,16 @@ __device__ __forceinline__ void chol_diag(float d, bool fp64, float &l, float &r
 }
 
 // ------------------------------------------------------- launch helpers
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` once per
+// (device, kernel); later calls are a lookup, so launches recorded into a
+// CUDA graph never call into the runtime's attribute API.
+cudaError_t prepare_kernel(const void *fn, size_t bytes);
+
+template <typename K>
+inline cudaError_t prepare(K kern, size_t bytes) {
+    return bytes > 48 * 1024 ? prepare_kernel(reinterpret_cast<const void *>(kern), bytes) : cudaSuccess;
+}
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Problems per CTA and threads per CTA of a placement for a team size T.

@@ -316,8 +316,8 @@ __global__ void __launch_bounds__(1024) k_chol_block(int n, int nrhs, Mat A, Mat
 template <typename K>
 cudaError_t launch_k(K kern, int grid, int threads, size_t smem, cudaStream_t st, int n, int nrhs,
                      const Mat &A, const Mat &B, int *info, int batch, int fp64diag, int refine) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = prepare(kern, smem);
         if (e != cudaSuccess) return e;
     }
     kern<<<grid, threads, smem, st>>>(n, nrhs, A, B, info, batch, fp64diag, refine);
@@ -360,8 +360,7 @@ cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info
     const int grid = ceil_div(batch, pack);
     if (OP == C_TRSM) {
 #define GL_TW(N) do { auto kern = k_trsm_warp<N>; size_t sm = (size_t)pack * (N * N + N) * 4;                 \
-        if (sm > 48 * 1024) { cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-            if (e != cudaSuccess) return e; }                                                                    \
+        { cudaError_t e = prepare(kern, sm); if (e != cudaSuccess) return e; }                                 \
         kern<<<grid, threads, sm, st>>>(n, nrhs, A, B, batch); return cudaPeekAtLastError(); } while (0)
         if (n <= 8) GL_TW(8);
         if (n <= 16) GL_TW(16);

@@ -167,8 +167,8 @@ __global__ void __launch_bounds__(256) k_gemm_team(int m, int n, int k, Mat A, M
 template <typename K>
 cudaError_t go(K kern, int grid, int threads, size_t smem, cudaStream_t st, int m, int n, int k, const Mat &A,
                const Mat &B, const Mat &C, int batch) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = prepare(kern, smem);
         if (e != cudaSuccess) return e;
     }
     kern<<<grid, threads, smem, st>>>(m, n, k, A, B, C, batch);

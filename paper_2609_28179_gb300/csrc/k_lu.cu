@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(1024) k_lu_block(int n, int nrhs, Mat A, int *
 template <typename K>
 cudaError_t go(K kern, int grid, int threads, size_t smem, cudaStream_t st, int n, int nrhs, const Mat &A, int *ipiv,
                const Mat &B, int *info, int batch) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = prepare(kern, smem);
         if (e != cudaSuccess) return e;
     }
     kern<<<grid, threads, smem, st>>>(n, nrhs, A, ipiv, B, info, batch);
