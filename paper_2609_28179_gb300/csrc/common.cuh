@@ -39,6 +39,13 @@ struct Mat {
         return ((long long)(b >> 5) * rows * cols + (long long)j * rows + i) * 32 + (b & 31);
     }
     __device__ __forceinline__ float get(int b, int i, int j) const { return p[off(b, i, j)]; }
+    // Column-major only (warp and block scopes accept no other layout).
+    __device__ __forceinline__ float cget(int b, int i, int j) const {
+        return p[(long long)b * s + (long long)j * ld + i];
+    }
+    __device__ __forceinline__ void cset(int b, int i, int j, float v) const {
+        p[(long long)b * s + (long long)j * ld + i] = v;
+    }
     __device__ __forceinline__ void set(int b, int i, int j, float v) const { p[off(b, i, j)] = v; }
     // Packed column-major: the whole batch is one contiguous array.
     __host__ __device__ __forceinline__ bool packed() const {
@@ -200,9 +207,6 @@ struct Geometry {
     int threads;   // threads per CTA
     int grid;      // CTAs
 };
-
-// Team size of the block scope for an operation of order n.
-inline int block_team(int n) { return n <= 16 ? 64 : (n <= 32 ? 128 : 256); }
 
 // --------------------------------------------------- launchers (by file)
 // Each returns cudaSuccess or the launch error; none allocates or syncs.

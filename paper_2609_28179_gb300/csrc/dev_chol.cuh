@@ -4,9 +4,11 @@
 //   glass::thread : one problem per thread, operand in registers (n <= 16);
 //   glass::warp   : one problem per warp, row i of the operand in the
 //                   registers of lane i % 32 (two rows per lane above 32),
-//                   columns broadcast with shuffles;
-//   glass::block  : one problem per team of T threads, operand resident in
-//                   shared memory, steps separated by named barriers.
+//                   columns broadcast through a per-warp shared buffer
+//                   (shuffles at two rows per lane);
+//                   many right-hand sides: one column of X per thread with
+//                   L broadcast from shared memory;
+//   block scope   : a 64-thread row team per problem (dev_rows.cuh).
 // All scopes follow one convention: lower factor, column-major operand,
 // L L^T = A (the paper's shared-convention rule, Sec. III-A).  The
 // arithmetic is the right-looking form of the textbook recurrences
@@ -103,11 +105,18 @@ struct Rows {
 
 // In-place Cholesky with row lane+32r of the operand in a[r][*] (only the
 // entries k <= row are meaningful).  rd[r] receives 1 / l_rr of that row.
+// The trailing update at step j needs l_kj from the lane that holds row k.
+// Up to NMAX = 32 that column goes through the warp's NMAX-float shared
+// buffer `col` (16-byte aligned): every lane publishes its l_ij and reads
+// the l_kj back as 16-byte broadcasts (one load per four columns instead of
+// one shuffle per column).  At NMAX = 64 (two rows per lane) the shuffle
+// form keeps the 128-entry row block in registers, so it is used there.
 // Returns info, identical in every lane.
 template <int NMAX>
 __device__ __forceinline__ int potrf(float (&a)[Rows<NMAX>::R][NMAX], float (&rd)[Rows<NMAX>::R], int n,
-                                     bool fp64diag) {
+                                     bool fp64diag, float *col) {
     constexpr int R = Rows<NMAX>::R;
+    constexpr bool kSmem = NMAX <= 32;
     const int lane = threadIdx.x & 31;
     int info = 0;
 #pragma unroll
@@ -122,15 +131,34 @@ __device__ __forceinline__ int potrf(float (&a)[Rows<NMAX>::R][NMAX], float (&rd
                 const int i = lane + 32 * q;
                 if (i == j) { a[q][j] = l; rd[q] = r; }
                 else if (i > j) a[q][j] *= r;
+                if (kSmem && i < NMAX) col[i] = a[q][j];
             }
+            if constexpr (kSmem) {
+                __syncwarp();
 #pragma unroll
-            for (int k = j + 1; k < NMAX; ++k) {
-                if (k < n) {
-                    const float lk = __shfl_sync(GLASS_FULL_MASK, a[k / 32][j], k % 32);
+                for (int k4 = (j + 1) / 4; k4 < NMAX / 4; ++k4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(col + 4 * k4);
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        const int i = lane + 32 * q;
-                        if (i >= k) a[q][k] = fmaf(-a[q][j], lk, a[q][k]);
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = 4 * k4 + u;
+                        if (k > j) {
+                            const int i = lane;
+                            if (i >= k) a[0][k] = fmaf(-a[0][j], vv[u], a[0][k]);
+                        }
+                    }
+                }
+                __syncwarp();
+            } else {
+#pragma unroll
+                for (int k = j + 1; k < NMAX; ++k) {
+                    if (k < n) {
+                        const float lk = __shfl_sync(GLASS_FULL_MASK, a[k / 32][j], k % 32);
+#pragma unroll
+                        for (int q = 0; q < R; ++q) {
+                            const int i = lane + 32 * q;
+                            if (i >= k) a[q][k] = fmaf(-a[q][j], lk, a[q][k]);
+                        }
                     }
                 }
             }
@@ -185,97 +213,59 @@ __device__ __forceinline__ void backward_t(const float (&a)[Rows<NMAX>::R][NMAX]
     }
 }
 
-// Triangular solve with many right-hand sides: lane c owns column c of X
-// (x[0..NMAX)) and reads L (column-major, leading dimension ldl, in shared
-// memory) and dinv (shared) by broadcast.  x <- L^{-1} x.
+// Triangular solves with many right-hand sides: each thread owns one
+// column x[0..NMAX) of X and reads L (column-major, leading dimension
+// NMAX, 16-byte aligned, shared memory) and dinv (shared) by broadcast.
+// x <- L^{-1} x, right-looking: after x_i is final, the trailing entries
+// take -l_ri x_i, the l_ri read four at a time from column i.
 template <int NMAX>
-__device__ __forceinline__ void forward_cols(const float *Ls, int ldl, const float *dinv_s,
-                                             float (&x)[NMAX], int n) {
+__device__ __forceinline__ void forward_cols(const float *Ls, const float *dinv_s, float (&x)[NMAX], int n) {
 #pragma unroll
     for (int i = 0; i < NMAX; ++i) {
         if (i < n) {
             x[i] *= dinv_s[i];
-            const float *col = Ls + i * ldl;
+            const float4 *c4 = reinterpret_cast<const float4 *>(Ls + i * NMAX);
 #pragma unroll
-            for (int r = i + 1; r < NMAX; ++r)
-                if (r < n) x[r] = fmaf(-col[r], x[i], x[r]);
+            for (int q4 = (i + 1) / 4; q4 < NMAX / 4; ++q4) {
+                const float4 v = c4[q4];
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = 4 * q4 + u;
+                    if (r > i && r < n) x[r] = fmaf(-vv[u], x[i], x[r]);
+                }
+            }
+        }
+    }
+}
+
+// x <- L^{-T} x, dot-product form: x_i = (y_i - sum_{k>i} l_ki x_k) / l_ii,
+// column i of L read four at a time, two partial sums for ILP.
+template <int NMAX>
+__device__ __forceinline__ void backward_t_cols(const float *Ls, const float *dinv_s, float (&x)[NMAX], int n) {
+#pragma unroll
+    for (int i = NMAX - 1; i >= 0; --i) {
+        if (i < n) {
+            const float4 *c4 = reinterpret_cast<const float4 *>(Ls + i * NMAX);
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int q4 = (i + 1) / 4; q4 < NMAX / 4; ++q4) {
+                const float4 v = c4[q4];
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = 4 * q4 + u;
+                    if (k > i && k < n) {
+                        if (u & 1) s1 = fmaf(vv[u], x[k], s1);
+                        else s0 = fmaf(vv[u], x[k], s0);
+                    }
+                }
+            }
+            x[i] = (x[i] - (s0 + s1)) * dinv_s[i];
         }
     }
 }
 
 }  // namespace warp
 
-namespace block {
-
-// Team of T threads on one problem resident in shared memory (column-major,
-// leading dimension lda).  rank = thread index within the team; bar = the
-// team's named barrier.  Every function ends with the team synchronised.
-
-// Threads laid out as TI rows x TK column groups for trailing updates.
-template <int T>
-struct Grid2 {
-    static constexpr int TI = T >= 64 ? 64 : T;
-    static constexpr int TK = T / TI;
-};
-
-template <int T>
-__device__ __forceinline__ int potrf(float *a, int lda, int n, int rank, int bar, bool fp64diag,
-                                     float *dinv_s) {
-    using G = Grid2<T>;
-    int info = 0;
-    const int ti = rank % G::TI, tk = rank / G::TI;
-    for (int j = 0; j < n; ++j) {
-        const float d = a[j * lda + j];
-        if (!(d > 0.f) && info == 0) info = j + 1;
-        float l, r;
-        chol_diag(d, fp64diag, l, r);
-        team_sync<T>(bar);  // everyone has read a_jj
-        if (rank == 0) { a[j * lda + j] = l; dinv_s[j] = r; }
-        for (int i = j + 1 + rank; i < n; i += T) a[j * lda + i] *= r;
-        team_sync<T>(bar);
-        for (int k = j + 1 + tk; k < n; k += G::TK) {
-            const float lkj = a[j * lda + k];
-            for (int i = ti; i < n; i += G::TI)
-                if (i >= k) a[k * lda + i] = fmaf(-a[j * lda + i], lkj, a[k * lda + i]);
-        }
-        team_sync<T>(bar);
-    }
-    return info;
-}
-
-// dinv_s[i] = 1 / l_ii for a given factor.
-template <int T>
-__device__ __forceinline__ void diag_inverse(const float *a, int lda, int n, int rank, int bar,
-                                             float *dinv_s) {
-    for (int i = rank; i < n; i += T) dinv_s[i] = 1.0f / a[i * lda + i];
-    team_sync<T>(bar);
-}
-
-// One right-hand side x (shared) <- L^{-1} x, rows updated in parallel.
-template <int T>
-__device__ __forceinline__ void forward(const float *a, int lda, const float *dinv_s, float *x, int n,
-                                        int rank, int bar, bool unit = false) {
-    for (int i = 0; i < n; ++i) {
-        const float yi = unit ? x[i] : x[i] * dinv_s[i];
-        for (int r = i + 1 + rank; r < n; r += T) x[r] = fmaf(-a[i * lda + r], yi, x[r]);
-        team_sync<T>(bar);
-        if (rank == 0) x[i] = yi;
-    }
-    team_sync<T>(bar);
-}
-
-// One right-hand side x (shared) <- L^{-T} x.
-template <int T>
-__device__ __forceinline__ void backward_t(const float *a, int lda, const float *dinv_s, float *x, int n,
-                                           int rank, int bar) {
-    for (int i = n - 1; i >= 0; --i) {
-        const float xi = x[i] * dinv_s[i];
-        for (int r = rank; r < i; r += T) x[r] = fmaf(-a[r * lda + i], xi, x[r]);
-        team_sync<T>(bar);
-        if (rank == 0) x[i] = xi;
-    }
-    team_sync<T>(bar);
-}
-
-}  // namespace block
 }  // namespace glass

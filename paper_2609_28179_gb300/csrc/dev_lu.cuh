@@ -132,13 +132,20 @@ struct LU {
 };
 
 // Rows lane+32q in a[q][*]; pos[q] receives each row's final logical
-// position; pp[j] = physical row chosen at step j; prc[j] = 1 / u_jj.
-// ipiv_out (may be null) receives ipiv[0..n).  Returns info (uniform).
+// position.  sm: the warp's shared scratch, 2*NMAX words: pp[j] = physical
+// row chosen at step j, prc[j] = 1 / u_jj (read back by getrs).
+// The pivot is found with two warp reductions (redux.sync): the largest
+// |a_ij| bit pattern among candidate rows (|x| orders like its IEEE bits),
+// then the smallest logical position carrying it -- exactly "largest
+// magnitude, smallest row index on ties".  ipiv_out (may be null) receives
+// ipiv[0..n).  Returns info (uniform).
 template <int NMAX>
-__device__ __forceinline__ int getrf(float (&a)[LU<NMAX>::R][NMAX], int (&pos)[LU<NMAX>::R], int (&pp)[NMAX],
-                                     float (&prc)[NMAX], int *ipiv_out, int n) {
+__device__ __forceinline__ int getrf(float (&a)[LU<NMAX>::R][NMAX], int (&pos)[LU<NMAX>::R], int *sm,
+                                     int *ipiv_out, int n) {
     constexpr int R = LU<NMAX>::R;
     const int lane = threadIdx.x & 31;
+    int *pp = sm;
+    float *prc = reinterpret_cast<float *>(sm + NMAX);
     bool done[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) { pos[q] = lane + 32 * q; done[q] = false; }
@@ -146,20 +153,27 @@ __device__ __forceinline__ int getrf(float (&a)[LU<NMAX>::R][NMAX], int (&pos)[L
 #pragma unroll
     for (int j = 0; j < NMAX; ++j) {
         if (j < n) {
-            unsigned long long key = 0;
+            // candidate key: |a_ij| bits + 1 (0 = no candidate); per lane the
+            // best of its rows, smaller position on equal keys
+            unsigned key = 0, kpos = 0xffffffffu;
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int i = lane + 32 * q;
                 if (!done[q] && i < n) {
-                    const unsigned long long kq = piv_key(fabsf(a[q][j]), pos[q], i);
-                    key = kq > key ? kq : key;
+                    const unsigned kq = __float_as_uint(fabsf(a[q][j])) + 1u;
+                    if (kq > key || (kq == key && (unsigned)pos[q] < kpos)) { key = kq; kpos = pos[q]; }
                 }
             }
-            key = warp_max_u64(key);
-            const int pphys = (int)(key & 63u);
-            const int ppos = 63 - (int)((key >> 6) & 63u);
+            const unsigned kmax = __reduce_max_sync(GLASS_FULL_MASK, key);
+            const int ppos = (int)__reduce_min_sync(GLASS_FULL_MASK, key == kmax ? kpos : 0xffffffffu);
             if (ipiv_out != nullptr && lane == 0) ipiv_out[j] = ppos;
-            pp[j] = pphys;
+            // physical row of the winner
+            int pphys = 0;
+#pragma unroll
+            for (int q = R - 1; q >= 0; --q) {
+                const unsigned m = __ballot_sync(GLASS_FULL_MASK, !done[q] && lane + 32 * q < n && pos[q] == ppos);
+                if (m) pphys = 32 * q + __ffs(m) - 1;
+            }
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int i = lane + 32 * q;
@@ -172,13 +186,12 @@ __device__ __forceinline__ int getrf(float (&a)[LU<NMAX>::R][NMAX], int (&pos)[L
             for (int q = 1; q < R; ++q)
                 if (pq == q) pvsel = a[q][j];
             const float pv = __shfl_sync(GLASS_FULL_MASK, pvsel, pl);
+            const float rc = pv != 0.f ? 1.0f / pv : 0.f;
+            if (lane == 0) { pp[j] = pphys; prc[j] = rc; }
             if (pv == 0.f) {
                 if (info == 0) info = j + 1;
-                prc[j] = 0.f;
                 continue;
             }
-            const float rc = 1.0f / pv;
-            prc[j] = rc;
             float m[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) {
@@ -200,27 +213,30 @@ __device__ __forceinline__ int getrf(float (&a)[LU<NMAX>::R][NMAX], int (&pos)[L
             }
         }
     }
+    __syncwarp();
     return info;
 }
 
 // One right-hand side held by physical row (x[q] = b of row lane+32q, the
 // row's ORIGINAL index): on return x[q] is the solution component at
-// logical position pos[q].
+// logical position pos[q].  sm: the scratch written by getrf.
 template <int NMAX>
 __device__ __forceinline__ void getrs(const float (&a)[LU<NMAX>::R][NMAX], const int (&pos)[LU<NMAX>::R],
-                                      const int (&pp)[NMAX], const float (&prc)[NMAX], float (&x)[LU<NMAX>::R],
-                                      int n) {
+                                      const int *sm, float (&x)[LU<NMAX>::R], int n) {
     constexpr int R = LU<NMAX>::R;
     const int lane = threadIdx.x & 31;
+    const int *pp = sm;
+    const float *prc = reinterpret_cast<const float *>(sm + NMAX);
 #pragma unroll
     for (int j = 0; j < NMAX; ++j) {
         if (j < n) {
-            const int pq = pp[j] >> 5;
+            const int pj = pp[j];
+            const int pq = pj >> 5;
             float sel = x[0];
 #pragma unroll
             for (int q = 1; q < R; ++q)
                 if (pq == q) sel = x[q];
-            const float yj = __shfl_sync(GLASS_FULL_MASK, sel, pp[j] & 31);
+            const float yj = __shfl_sync(GLASS_FULL_MASK, sel, pj & 31);
 #pragma unroll
             for (int q = 0; q < R; ++q)
                 if (pos[q] > j && lane + 32 * q < n) x[q] = fmaf(-a[q][j], yj, x[q]);
@@ -229,16 +245,17 @@ __device__ __forceinline__ void getrs(const float (&a)[LU<NMAX>::R][NMAX], const
 #pragma unroll
     for (int j = NMAX - 1; j >= 0; --j) {
         if (j < n) {
-            const int pq = pp[j] >> 5;
+            const int pj = pp[j];
+            const int pq = pj >> 5;
             float sel = x[0];
 #pragma unroll
             for (int q = 1; q < R; ++q)
                 if (pq == q) sel = x[q];
-            const float xj = __shfl_sync(GLASS_FULL_MASK, sel, pp[j] & 31) * prc[j];
+            const float xj = __shfl_sync(GLASS_FULL_MASK, sel, pj & 31) * prc[j];
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int i = lane + 32 * q;
-                if (i == pp[j]) x[q] = xj;
+                if (i == pj) x[q] = xj;
                 else if (pos[q] < j && i < n) x[q] = fmaf(-a[q][j], xj, x[q]);
             }
         }
@@ -247,88 +264,4 @@ __device__ __forceinline__ void getrs(const float (&a)[LU<NMAX>::R][NMAX], const
 
 }  // namespace warp
 
-namespace block {
-
-// Team LU in shared memory (column-major, leading dimension lda).  Per
-// step: the team's first warp finds the pivot, then the exchange and the
-// column scaling, then the trailing update, each phase closed by the team
-// barrier.  sc: 4 words of team scratch in shared memory.
-template <int T>
-__device__ __forceinline__ int getrf(float *a, int lda, int n, int *piv_s, float *rinv_s, int rank, int bar,
-                                     float *sc) {
-    constexpr int TI = T >= 64 ? 64 : T;
-    constexpr int TK = T / TI;
-    const int ti = rank % TI, tk = rank / TI;
-    int info = 0;
-    for (int j = 0; j < n; ++j) {
-        if (rank < 32) {
-            unsigned long long key = 0;
-            for (int i = j + rank; i < n; i += 32) {
-                const unsigned long long k = warp::piv_key(fabsf(a[j * lda + i]), i, i);
-                key = k > key ? k : key;
-            }
-            key = warp::warp_max_u64(key);
-            if (rank == 0) {
-                const int p = (int)(key & 63u);
-                piv_s[j] = p;
-                sc[0] = a[j * lda + j];  // old a_jj (moves to row p)
-                sc[1] = a[j * lda + p];  // the pivot value
-            }
-        }
-        team_sync<T>(bar);
-        const int p = piv_s[j];
-        const float old_jj = sc[0], pv = sc[1];
-        const float rc = pv != 0.f ? 1.0f / pv : 0.f;
-        if (pv == 0.f && info == 0) info = j + 1;
-        // exchange rows j and p in every column but j; column j is rewritten
-        // with the scaled multipliers directly.
-        if (p != j)
-            for (int c = rank; c < n; c += T)
-                if (c != j) {
-                    const float t = a[c * lda + j];
-                    a[c * lda + j] = a[c * lda + p];
-                    a[c * lda + p] = t;
-                }
-        if (pv != 0.f)
-            for (int i = j + 1 + rank; i < n; i += T) {
-                const float v = (i == p) ? old_jj : a[j * lda + i];
-                a[j * lda + i] = v * rc;
-            }
-        if (rank == 0) { a[j * lda + j] = pv; rinv_s[j] = rc; }
-        team_sync<T>(bar);
-        if (pv != 0.f)
-            for (int k = j + 1 + tk; k < n; k += TK) {
-                const float ujk = a[k * lda + j];
-                for (int i = j + 1 + ti; i < n; i += TI) a[k * lda + i] = fmaf(-a[j * lda + i], ujk, a[k * lda + i]);
-            }
-        team_sync<T>(bar);
-    }
-    return info;
-}
-
-// One right-hand side x (shared): swaps, unit-lower forward, upper backward.
-template <int T>
-__device__ __forceinline__ void getrs(const float *a, int lda, const int *piv_s, const float *rinv_s, float *x, int n,
-                                      int rank, int bar) {
-    if (rank == 0)
-        for (int j = 0; j < n; ++j) {
-            const int p = piv_s[j];
-            if (p != j) { const float t = x[j]; x[j] = x[p]; x[p] = t; }
-        }
-    team_sync<T>(bar);
-    for (int i = 0; i < n; ++i) {
-        const float yi = x[i];
-        for (int r = i + 1 + rank; r < n; r += T) x[r] = fmaf(-a[i * lda + r], yi, x[r]);
-        team_sync<T>(bar);
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        const float xi = x[i] * rinv_s[i];
-        for (int r = rank; r < i; r += T) x[r] = fmaf(-a[i * lda + r], xi, x[r]);
-        team_sync<T>(bar);
-        if (rank == 0) x[i] = xi;
-    }
-    team_sync<T>(bar);
-}
-
-}  // namespace block
 }  // namespace glass

@@ -7,9 +7,12 @@
 // 16-byte streaming loads (column-major input) or reads the interleaved
 // layout directly; warp scope loads rows straight into registers (each
 // column of a problem is a contiguous, coalesced segment); block scope
-// stages each problem into its team's shared memory.
+// stages each problem into its team's shared memory.  Solves with many
+// right-hand sides (trsm at warp and block scope, potrs at block scope)
+// give each thread whole columns of X with L broadcast from shared memory.
 #pragma once
 #include "dev_chol.cuh"
+#include "dev_rows.cuh"
 
 namespace glass {
 namespace {
@@ -19,14 +22,10 @@ enum CholOp { C_POTRF = 0, C_POTRS = 1, C_TRSM = 2, C_POSV = 3 };
 constexpr bool has_factor(int op) { return op == C_POTRF || op == C_POSV; }
 constexpr bool has_rhs(int op) { return op != C_POTRF; }
 
-// r = b - A x in FP64 for one problem, A symmetric with its lower triangle
-// read from `a` (column-major, leading dimension lda, ELEMENT accessor).
-// Used by the refinement step: the factorization and first solve are FP32.
-
 // ------------------------------------------------------------ thread scope
-template <int OP, int NMAX, bool EXACT>
+template <int OP, int NMAX, bool EXACT, bool REFINE>
 __global__ void __launch_bounds__(256) k_chol_thread(int n_rt, int nrhs, Mat A, Mat B, int *info,
-                                                     int batch, int fp64diag, int refine) {
+                                                     int batch, int fp64diag) {
     extern __shared__ float smem[];
     using TR = Tri<NMAX>;
     const int n = EXACT ? NMAX : n_rt;
@@ -70,7 +69,7 @@ __global__ void __launch_bounds__(256) k_chol_thread(int n_rt, int nrhs, Mat A, 
                     x[i] = (i < n) ? (staged ? pb[c * n + i] : B.get(b, i, c)) : 0.f;
                 thread::forward<NMAX, EXACT>(a, dinv, x, n);
                 if (OP != C_TRSM) thread::backward_t<NMAX, EXACT>(a, dinv, x, n);
-                if (OP == C_POSV && refine) {
+                if (REFINE) {
                     // r = b - A x0 in FP64 (A and b are still pristine in the
                     // staging buffers / in global memory).
                     float r[NMAX];
@@ -124,11 +123,17 @@ __global__ void __launch_bounds__(256) k_chol_thread(int n_rt, int nrhs, Mat A, 
 }
 
 // -------------------------------------------------------------- warp scope
-template <int OP, int NMAX>
-__global__ void __launch_bounds__(256) k_chol_warp(int n, int nrhs, Mat A, Mat B, int *info, int batch,
-                                                   int fp64diag, int refine) {
+// Row-distributed Cholesky / solve: lane i holds row i (and i+32).  The
+// refinement step is a separate instantiation (REFINE) so the plain kernel
+// does not carry its registers.  Dynamic shared memory: one NMAX-float
+// column buffer per warp.
+template <int OP, int NMAX, bool REFINE>
+__global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_chol_warp(int n, int nrhs, Mat A, Mat B, int *info, int batch,
+                                                   int fp64diag) {
     constexpr int R = warp::Rows<NMAX>::R;
+    extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31;
+    float *col = smem + (threadIdx.x >> 5) * NMAX;
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= batch) return;  // whole warp
     float a[R][NMAX];
@@ -138,10 +143,10 @@ __global__ void __launch_bounds__(256) k_chol_warp(int n, int nrhs, Mat A, Mat B
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int i = lane + 32 * q;
-            a[q][k] = (k < n && i < n && k <= i) ? A.get(b, i, k) : 0.f;
+            a[q][k] = (k < n && i < n && k <= i) ? A.cget(b, i, k) : 0.f;
         }
     if (has_factor(OP)) {
-        const int inf = warp::potrf<NMAX>(a, rd, n, fp64diag != 0);
+        const int inf = warp::potrf<NMAX>(a, rd, n, fp64diag != 0, col);
         if (lane == 0) info[b] = inf;
     } else {
 #pragma unroll
@@ -160,18 +165,18 @@ __global__ void __launch_bounds__(256) k_chol_warp(int n, int nrhs, Mat A, Mat B
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int i = lane + 32 * q;
-                x[q] = (i < n) ? B.get(b, i, c) : 0.f;
+                x[q] = (i < n) ? B.cget(b, i, c) : 0.f;
             }
             warp::forward<NMAX>(a, rd, x, n);
             if (OP != C_TRSM) warp::backward_t<NMAX>(a, rd, x, n);
-            if (OP == C_POSV && refine) {
+            if (REFINE) {
                 // r_i = b_i - sum_k a_ik x_k in FP64; A is re-read from
                 // global memory (not yet overwritten: L is stored last).
                 double acc[R];
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     const int i = lane + 32 * q;
-                    acc[q] = (i < n) ? (double)B.get(b, i, c) : 0.0;
+                    acc[q] = (i < n) ? (double)B.cget(b, i, c) : 0.0;
                 }
                 for (int k = 0; k < n; ++k) {
                     float xk = 0.f;
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(256) k_chol_warp(int n, int nrhs, Mat A, Mat B
                     for (int q = 0; q < R; ++q) {
                         const int i = lane + 32 * q;
                         if (i < n) {
-                            const float aik = (k <= i) ? A.get(b, i, k) : A.get(b, k, i);
+                            const float aik = (k <= i) ? A.cget(b, i, k) : A.cget(b, k, i);
                             acc[q] = fma(-(double)aik, (double)xk, acc[q]);
                         }
                     }
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(256) k_chol_warp(int n, int nrhs, Mat A, Mat B
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int i = lane + 32 * q;
-                if (i < n) B.set(b, i, c, x[q]);
+                if (i < n) B.cset(b, i, c, x[q]);
             }
         }
     }
@@ -210,132 +215,168 @@ __global__ void __launch_bounds__(256) k_chol_warp(int n, int nrhs, Mat A, Mat B
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int i = lane + 32 * q;
-                if (k < n && i < n && k <= i) A.set(b, i, k, a[q][k]);
+                if (k < n && i < n && k <= i) A.cset(b, i, k, a[q][k]);
             }
     }
 }
 
-// Warp-scope TRSM with many right-hand sides: L (and 1/l_ii) staged in the
-// warp's shared memory, lane c solving column c (and c+32, ...).
-template <int NMAX>
-__global__ void __launch_bounds__(256) k_trsm_warp(int n, int nrhs, Mat L, Mat B, int batch) {
-    extern __shared__ float smem[];
-    const int lane = threadIdx.x & 31;
-    const int w = threadIdx.x >> 5;
-    const int b = blockIdx.x * (blockDim.x >> 5) + w;
-    if (b >= batch) return;
-    float *Ls = smem + w * (NMAX * NMAX + NMAX);
+// Solves with many right-hand sides (trsm; potrs when BOTH): a team of T
+// threads per problem, L (lower triangle) and B staged in shared memory
+// with coalesced loads, each thread solving whole columns of X in
+// registers with L read as 16-byte broadcasts.  Per problem in shared
+// memory: L (NMAX x NMAX, 16-byte aligned), 1/l_ii, B (ld = n | 1).
+template <int NMAX, int T, bool BOTH>
+__global__ void __launch_bounds__(256) k_solve_cols(int n, int nrhs, Mat L, Mat B, int batch) {
+    extern __shared__ __align__(16) float smem[];
+    const int team = threadIdx.x / T, rank = threadIdx.x % T;
+    const int P = blockDim.x / T;
+    const int b = blockIdx.x * P + team;
+    const int bar = 1 + team;
+    const int ldb = n | 1;
+    const int per = NMAX * NMAX + NMAX + ((nrhs * ldb + 3) & ~3);
+    float *Ls = smem + team * per;
     float *dv = Ls + NMAX * NMAX;
-    for (int e = lane; e < n * n; e += 32) {
+    float *Bs = dv + NMAX;
+    if (b >= batch) return;
+    for (int e = rank; e < n * n; e += T) {
         const int j = e / n, i = e - j * n;
-        Ls[j * NMAX + i] = (i >= j) ? L.get(b, i, j) : 0.f;
+        if (i >= j) Ls[j * NMAX + i] = L.cget(b, i, j);
     }
-    __syncwarp();
-    for (int i = lane; i < n; i += 32) dv[i] = 1.0f / Ls[i * NMAX + i];
-    __syncwarp();
-    for (int c0 = 0; c0 < nrhs; c0 += 32) {
-        const int c = c0 + lane;
-        if (c < nrhs) {
-            float x[NMAX];
+    if (B.packed()) {
+        const float *g = B.p + (long long)b * B.s;
+        for (int e = rank; e < n * nrhs; e += T) {
+            const int c = e / n, i = e - c * n;
+            Bs[c * ldb + i] = __ldcs(g + e);
+        }
+    } else {
+        for (int e = rank; e < n * nrhs; e += T) {
+            const int c = e / n, i = e - c * n;
+            Bs[c * ldb + i] = B.cget(b, i, c);
+        }
+    }
+    team_sync<T>(bar);
+    for (int i = rank; i < n; i += T) dv[i] = 1.0f / Ls[i * NMAX + i];
+    team_sync<T>(bar);
+    for (int c = rank; c < nrhs; c += T) {
+        float x[NMAX];
+        float *xc = Bs + c * ldb;
 #pragma unroll
-            for (int i = 0; i < NMAX; ++i) x[i] = (i < n) ? B.get(b, i, c) : 0.f;
-            warp::forward_cols<NMAX>(Ls, NMAX, dv, x, n);
+        for (int i = 0; i < NMAX; ++i) x[i] = (i < n) ? xc[i] : 0.f;
+        warp::forward_cols<NMAX>(Ls, dv, x, n);
+        if (BOTH) warp::backward_t_cols<NMAX>(Ls, dv, x, n);
 #pragma unroll
-            for (int i = 0; i < NMAX; ++i)
-                if (i < n) B.set(b, i, c, x[i]);
+        for (int i = 0; i < NMAX; ++i)
+            if (i < n) xc[i] = x[i];
+    }
+    team_sync<T>(bar);
+    if (B.packed()) {
+        float *g = B.p + (long long)b * B.s;
+        for (int e = rank; e < n * nrhs; e += T) {
+            const int c = e / n, i = e - c * n;
+            __stcs(g + e, Bs[c * ldb + i]);
+        }
+    } else {
+        for (int e = rank; e < n * nrhs; e += T) {
+            const int c = e / n, i = e - c * n;
+            B.cset(b, i, c, Bs[c * ldb + i]);
         }
     }
 }
 
 // ------------------------------------------------------------- block scope
-template <int OP, int T>
-__global__ void __launch_bounds__(1024) k_chol_block(int n, int nrhs, Mat A, Mat B, int *info, int batch,
-                                                    int fp64diag, int refine) {
-    extern __shared__ float smem[];
-    const int team = threadIdx.x / T, rank = threadIdx.x % T;
-    const int P = blockDim.x / T;
-    const int b = blockIdx.x * P + team;
-    const int bar = 1 + team;
-    const int lda = n | 1;
-    const int per = n * lda + n + (has_rhs(OP) ? n * nrhs : 0) + ((OP == C_POSV && refine) ? 2 * n : 0);
-    float *a = smem + team * per;
-    float *dinv = a + n * lda;
-    float *x = dinv + n;
-    float *rr = x + (has_rhs(OP) ? n * nrhs : 0);
+// Row team (dev_rows.cuh): 64 threads per problem, thread i owns row i,
+// right-hand sides handled RS = 4 at a time.  The refinement residual
+// r = b - A x0 is formed in FP64 from A re-read in global memory (L is
+// written back last) and the solved x broadcast through shared memory.
+constexpr int kRS = 4;
+
+template <int NMAX>
+constexpr int rows_team_floats() {
+    return ((rows::Scratch<NMAX, kRS>::floats + NMAX * kRS + 3) / 4) * 4;
+}
+
+template <int OP, int NMAX, bool REFINE>
+__global__ void __launch_bounds__(256, 1) k_chol_rows(int n, int nrhs, Mat A, Mat B, int *info, int batch,
+                                                   int fp64diag) {
+    extern __shared__ __align__(16) float smem[];
+    const int team = threadIdx.x / rows::T, i = threadIdx.x % rows::T;
+    const int b = blockIdx.x * (blockDim.x / rows::T) + team;
+    const int bid = 1 + team;
+    float *base = smem + team * rows_team_floats<NMAX>();
+    rows::Scratch<NMAX, kRS> s(base);
+    float *xall = base + rows::Scratch<NMAX, kRS>::floats;  // [NMAX][kRS]
     if (b >= batch) return;  // the whole team leaves together
-    for (int e = rank; e < n * n; e += T) {
-        const int j = e / n, i = e - j * n;
-        if (i >= j) a[j * lda + i] = A.get(b, i, j);
-    }
-    if (has_rhs(OP))
-        for (int e = rank; e < n * nrhs; e += T) {
-            const int c = e / n, i = e - c * n;
-            x[c * n + i] = B.get(b, i, c);
-        }
-    team_sync<T>(bar);
-    if (has_factor(OP)) {
-        const int inf = block::potrf<T>(a, lda, n, rank, bar, fp64diag != 0, dinv);
-        if (rank == 0) info[b] = inf;
-    } else {
-        block::diag_inverse<T>(a, lda, n, rank, bar, dinv);
-    }
+    float a[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) a[k] = (k < n && i < n && k <= i) ? A.cget(b, i, k) : 0.f;
+    const int inf = rows::potrf<NMAX, kRS>(a, n, i, fp64diag != 0, s, bid);
+    if (i == 0) info[b] = inf;
     if (has_rhs(OP)) {
-        for (int c = 0; c < nrhs; ++c) {
-            float *xc = x + c * n;
-            block::forward<T>(a, lda, dinv, xc, n, rank, bar);
-            if (OP != C_TRSM) block::backward_t<T>(a, lda, dinv, xc, n, rank, bar);
-            if (OP == C_POSV && refine) {
-                for (int i = rank; i < n; i += T) {
-                    double acc = (double)B.get(b, i, c);
-                    for (int k = 0; k < n; ++k) {
-                        const float aik = (k <= i) ? A.get(b, i, k) : A.get(b, k, i);
-                        acc = fma(-(double)aik, (double)xc[k], acc);
-                    }
-                    rr[i] = (float)acc;
+        for (int c0 = 0; c0 < nrhs; c0 += kRS) {
+            float x[kRS];
+#pragma unroll
+            for (int c = 0; c < kRS; ++c) x[c] = (i < n && c0 + c < nrhs) ? B.cget(b, i, c0 + c) : 0.f;
+            rows::forward<NMAX, kRS>(a, x, n, i, s, bid);
+            rows::backward_t<NMAX, kRS>(a, x, n, i, s, bid);
+            if (REFINE) {
+                if (i < n)
+#pragma unroll
+                    for (int c = 0; c < kRS; ++c) xall[i * kRS + c] = x[c];
+                rows::bar(bid);
+                float r[kRS];
+#pragma unroll
+                for (int c = 0; c < kRS; ++c) {
+                    double acc = (i < n && c0 + c < nrhs) ? (double)B.cget(b, i, c0 + c) : 0.0;
+                    if (i < n)
+                        for (int k = 0; k < n; ++k) {
+                            const float aik = (k <= i) ? A.cget(b, i, k) : A.cget(b, k, i);
+                            acc = fma(-(double)aik, (double)xall[k * kRS + c], acc);
+                        }
+                    r[c] = (float)acc;
                 }
-                team_sync<T>(bar);
-                block::forward<T>(a, lda, dinv, rr, n, rank, bar);
-                block::backward_t<T>(a, lda, dinv, rr, n, rank, bar);
-                for (int i = rank; i < n; i += T) xc[i] += rr[i];
-                team_sync<T>(bar);
+                rows::forward<NMAX, kRS>(a, r, n, i, s, bid);
+                rows::backward_t<NMAX, kRS>(a, r, n, i, s, bid);
+#pragma unroll
+                for (int c = 0; c < kRS; ++c) x[c] += r[c];
+                rows::bar(bid);  // xall reads done before a later pass rewrites it
             }
-        }
-        for (int e = rank; e < n * nrhs; e += T) {
-            const int c = e / n, i = e - c * n;
-            B.set(b, i, c, x[c * n + i]);
+            if (i < n)
+#pragma unroll
+                for (int c = 0; c < kRS; ++c)
+                    if (c0 + c < nrhs) B.cset(b, i, c0 + c, x[c]);
         }
     }
-    if (has_factor(OP))
-        for (int e = rank; e < n * n; e += T) {
-            const int j = e / n, i = e - j * n;
-            if (i >= j) A.set(b, i, j, a[j * lda + i]);
-        }
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k)
+        if (k < n && i < n && k <= i) A.cset(b, i, k, a[k]);
 }
 
 // ---------------------------------------------------------------- dispatch
 template <typename K>
 cudaError_t launch_k(K kern, int grid, int threads, size_t smem, cudaStream_t st, int n, int nrhs,
-                     const Mat &A, const Mat &B, int *info, int batch, int fp64diag, int refine) {
+                     const Mat &A, const Mat &B, int *info, int batch, int fp64diag) {
     {
         cudaError_t e = prepare(kern, smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, threads, smem, st>>>(n, nrhs, A, B, info, batch, fp64diag, refine);
+    kern<<<grid, threads, smem, st>>>(n, nrhs, A, B, info, batch, fp64diag);
     return cudaPeekAtLastError();
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
 
+inline int nmax_bucket(int n) { return n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64; }
+
 // Thread-scope instantiations: exact orders of the placement sweep and
 // buckets (runtime order <= NMAX) for the rest.
-template <int OP>
+template <int OP, bool RF>
 cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, int pack,
-                            int fp64diag, int refine, cudaStream_t st) {
+                            int fp64diag, cudaStream_t st) {
     const int G = 32 * pack;
     const bool staged = A.layout == GLASS_LAYOUT_COLMAJOR;
     const size_t smem = staged ? (size_t)G * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4 : 0;
     const int grid = ceil_div(batch, G);
-#define GL_T(N, EX) launch_k(k_chol_thread<OP, N, EX>, grid, G, smem, st, n, nrhs, A, B, info, batch, fp64diag, refine)
+#define GL_T(N, EX) launch_k(k_chol_thread<OP, N, EX, RF>, grid, G, smem, st, n, nrhs, A, B, info, batch, fp64diag)
     switch (n) {
         case 3: return GL_T(3, true);
         case 6: return GL_T(6, true);
@@ -348,50 +389,86 @@ cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *in
     if (n <= 4) return GL_T(4, false);
     if (n <= 8) return GL_T(8, false);
     if (n <= 12) return GL_T(12, false);
-    if (n <= 16) return GL_T(16, false);
+    return GL_T(16, false);
 #undef GL_T
-    return cudaErrorInvalidValue;
 }
 
-template <int OP>
-cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, int pack,
-                          int fp64diag, int refine, cudaStream_t st) {
-    const int threads = 32 * pack;
-    const int grid = ceil_div(batch, pack);
-    if (OP == C_TRSM) {
-#define GL_TW(N) do { auto kern = k_trsm_warp<N>; size_t sm = (size_t)pack * (N * N + N) * 4;                 \
-        { cudaError_t e = prepare(kern, sm); if (e != cudaSuccess) return e; }                                 \
-        kern<<<grid, threads, sm, st>>>(n, nrhs, A, B, batch); return cudaPeekAtLastError(); } while (0)
-        if (n <= 8) GL_TW(8);
-        if (n <= 16) GL_TW(16);
-        if (n <= 32) GL_TW(32);
-        GL_TW(64);
-#undef GL_TW
+// Shared memory of the column-per-thread solve kernel, per problem (bytes).
+inline size_t solve_cols_per(int n, int nrhs) {
+    const int N = nmax_bucket(n);
+    return (size_t)(N * N + N + (((size_t)nrhs * (n | 1) + 3) & ~(size_t)3)) * 4;
+}
+
+template <int NMAX, int T, bool BOTH>
+cudaError_t launch_solve_cols(int n, int nrhs, const Mat &L, const Mat &B, int batch, int pack, cudaStream_t st) {
+    auto kern = k_solve_cols<NMAX, T, BOTH>;
+    const size_t sm = solve_cols_per(n, nrhs) * pack;
+    cudaError_t e = prepare(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<ceil_div(batch, pack), T * pack, sm, st>>>(n, nrhs, L, B, batch);
+    return cudaPeekAtLastError();
+}
+
+template <int T, bool BOTH>
+cudaError_t solve_cols_dispatch(int n, int nrhs, const Mat &L, const Mat &B, int batch, int pack, cudaStream_t st) {
+    switch (nmax_bucket(n)) {
+        case 8: return launch_solve_cols<8, T, BOTH>(n, nrhs, L, B, batch, pack, st);
+        case 16: return launch_solve_cols<16, T, BOTH>(n, nrhs, L, B, batch, pack, st);
+        case 32: return launch_solve_cols<32, T, BOTH>(n, nrhs, L, B, batch, pack, st);
+        default: return launch_solve_cols<64, T, BOTH>(n, nrhs, L, B, batch, pack, st);
     }
-#define GL_W(N) launch_k(k_chol_warp<OP, N>, grid, threads, 0, st, n, nrhs, A, B, info, batch, fp64diag, refine)
-    if (n <= 8) return GL_W(8);
-    if (n <= 16) return GL_W(16);
-    if (n <= 32) return GL_W(32);
-    return GL_W(64);
+}
+
+template <int OP, bool RF>
+cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, int pack,
+                          int fp64diag, cudaStream_t st) {
+    if constexpr (OP == C_TRSM) {
+        return solve_cols_dispatch<32, false>(n, nrhs, A, B, batch, pack, st);
+    } else {
+        const int threads = 32 * pack;
+        const int grid = ceil_div(batch, pack);
+        const int N = nmax_bucket(n);
+        const size_t sm = (size_t)pack * N * 4;
+#define GL_W(NN) launch_k(k_chol_warp<OP, NN, RF>, grid, threads, sm, st, n, nrhs, A, B, info, batch, fp64diag)
+        switch (N) {
+            case 8: return GL_W(8);
+            case 16: return GL_W(16);
+            case 32: return GL_W(32);
+            default: return GL_W(64);
+        }
 #undef GL_W
+    }
 }
 
-template <int OP>
-size_t block_smem(int n, int nrhs, int pack, int refine) {
-    const int lda = n | 1;
-    const size_t per = (size_t)n * lda + n + (has_rhs(OP) ? (size_t)n * nrhs : 0) + ((OP == C_POSV && refine) ? 2 * n : 0);
-    return per * pack * 4;
+inline size_t rows_team_bytes(int n) {
+    switch (nmax_bucket(n)) {
+        case 8: return rows_team_floats<8>() * 4;
+        case 16: return rows_team_floats<16>() * 4;
+        case 32: return rows_team_floats<32>() * 4;
+        default: return rows_team_floats<64>() * 4;
+    }
 }
 
-template <int OP>
+template <int OP, bool RF>
 cudaError_t block_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, int pack,
-                           int fp64diag, int refine, cudaStream_t st) {
-    const int T = block_team(n);
-    const size_t smem = block_smem<OP>(n, nrhs, pack, refine);
-    const int grid = ceil_div(batch, pack);
-    if (T == 64) return launch_k(k_chol_block<OP, 64>, grid, 64 * pack, smem, st, n, nrhs, A, B, info, batch, fp64diag, refine);
-    if (T == 128) return launch_k(k_chol_block<OP, 128>, grid, 128 * pack, smem, st, n, nrhs, A, B, info, batch, fp64diag, refine);
-    return launch_k(k_chol_block<OP, 256>, grid, 256 * pack, smem, st, n, nrhs, A, B, info, batch, fp64diag, refine);
+                           int fp64diag, cudaStream_t st) {
+    if constexpr (OP == C_TRSM) {
+        return solve_cols_dispatch<64, false>(n, nrhs, A, B, batch, pack, st);
+    } else if constexpr (OP == C_POTRS) {
+        return solve_cols_dispatch<64, true>(n, nrhs, A, B, batch, pack, st);
+    } else {
+        const size_t smem = rows_team_bytes(n) * pack;
+        const int grid = ceil_div(batch, pack);
+        const int th = rows::T * pack;
+#define GL_R(NN) launch_k(k_chol_rows<OP, NN, RF>, grid, th, smem, st, n, nrhs, A, B, info, batch, fp64diag)
+        switch (nmax_bucket(n)) {
+            case 8: return GL_R(8);
+            case 16: return GL_R(16);
+            case 32: return GL_R(32);
+            default: return GL_R(64);
+        }
+#undef GL_R
+    }
 }
 
 template <int OP>
@@ -399,13 +476,12 @@ size_t smem_of(int n, int nrhs, Placement pl, int refine) {
     switch (pl.scope) {
         case SCOPE_THREAD:
             return (size_t)32 * pl.pack * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4;
-        case SCOPE_WARP: {
-            if (OP != C_TRSM) return 0;
-            const int N = n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64;
-            return (size_t)pl.pack * (N * N + N) * 4;
-        }
+        case SCOPE_WARP:
+            if (OP == C_TRSM) return solve_cols_per(n, nrhs) * pl.pack;
+            return (size_t)pl.pack * nmax_bucket(n) * 4;
         default:
-            return block_smem<OP>(n, nrhs, pl.pack, refine);
+            if (OP == C_TRSM || OP == C_POTRS) return solve_cols_per(n, nrhs) * pl.pack;
+            return rows_team_bytes(n) * pl.pack;
     }
 }
 
@@ -414,7 +490,7 @@ bool feasible_of(int n, int nrhs, Placement pl, int refine) {
     if (n < 1 || n > 64) return false;
     if (pl.pack != 1 && pl.pack != 2 && pl.pack != 4 && pl.pack != 8) return false;
     if (pl.scope == SCOPE_THREAD && n > 16) return false;
-    if (pl.scope == SCOPE_BLOCK && block_team(n) * pl.pack > 1024) return false;
+    if (pl.scope == SCOPE_BLOCK && 64 * pl.pack > 256) return false;
     return smem_of<OP>(n, nrhs, pl, refine) <= kMaxSmem;
 }
 
@@ -422,10 +498,17 @@ template <int OP>
 cudaError_t run(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, Placement pl, int fp64diag,
                 int refine, cudaStream_t st) {
     if (!feasible_of<OP>(n, nrhs, pl, refine)) return cudaErrorInvalidConfiguration;
+    if constexpr (OP == C_POSV) {
+        if (refine) switch (pl.scope) {
+            case SCOPE_THREAD: return thread_dispatch<OP, true>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
+            case SCOPE_WARP: return warp_dispatch<OP, true>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
+            default: return block_dispatch<OP, true>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
+        }
+    }
     switch (pl.scope) {
-        case SCOPE_THREAD: return thread_dispatch<OP>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, refine, st);
-        case SCOPE_WARP: return warp_dispatch<OP>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, refine, st);
-        default: return block_dispatch<OP>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, refine, st);
+        case SCOPE_THREAD: return thread_dispatch<OP, false>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
+        case SCOPE_WARP: return warp_dispatch<OP, false>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
+        default: return block_dispatch<OP, false>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
     }
 }
 

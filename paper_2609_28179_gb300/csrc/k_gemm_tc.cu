@@ -1,6 +1,249 @@
+// k_gemm_tc.cu -- batched tensor-core GEMM C = A B for n in {16, 32, 64}
+// with FP32 accumulation: BF16 operands, TF32 operands, or 3xTF32 split
+// products (a = a_hi + a_lo with a_hi = tf32(a), a_lo = tf32(a - a_hi);
+// C += a_lo b_hi + a_hi b_lo + a_hi b_hi), the precision path the paper
+// lists as future work (Sec. V).
+//
+// Work split: n/16 warps per product, warp w owns rows 16w .. 16w+15 of C
+// and every 8-column block, so one A fragment serves n/8 MMAs.  A CTA holds
+// 4 warps (4/(n/16) products).  Operands are staged into shared memory with
+// coalesced 16-byte streaming loads, in padded layouts whose leading
+// dimensions make every fragment load bank-conflict free; C goes back
+// through shared memory for coalesced 16-byte stores.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
+
 namespace glass {
-cudaError_t launch_gemm_tc(int, int, const void *, const void *, float *, int, cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
 }
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int N>
+struct TcShape {
+    static constexpr int WP = N / 16;        // warps per product
+    static constexpr int PPC = 4 / WP;       // products per CTA
+    static constexpr int NB = N / 8;         // 8-column blocks
+    static constexpr int LDC = N + 4;        // C staging (floats)
+};
+
+// ------------------------------------------------------------------ TF32
+// As: A column-major, lda = N + 8 floats; Bs: B column-major, ldb = N + 4.
+template <int N, bool SPLIT>
+__global__ void __launch_bounds__(128) k_gemm_tf32(const float *__restrict__ A, const float *__restrict__ B,
+                                                   float *__restrict__ C, int batch) {
+    using S = TcShape<N>;
+    constexpr int LDA = N + 8, LDB = N + 4;
+    constexpr int PER = N * LDA + N * LDB;
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lp = warp / S::WP, wq = warp % S::WP;  // product in CTA, warp within product
+    const int b0 = blockIdx.x * S::PPC;
+    // stage all products of the CTA (float4, coalesced)
+    for (int p = 0; p < S::PPC; ++p) {
+        const int b = b0 + p;
+        if (b >= batch) break;
+        float *As = smem + p * PER, *Bs = As + N * LDA;
+        const float4 *ga = reinterpret_cast<const float4 *>(A + (long long)b * N * N);
+        const float4 *gb = reinterpret_cast<const float4 *>(B + (long long)b * N * N);
+        for (int v = threadIdx.x; v < N * N / 4; v += blockDim.x) {
+            const int col = (4 * v) / N, row = (4 * v) % N;
+            *reinterpret_cast<float4 *>(As + col * LDA + row) = __ldcs(ga + v);
+            *reinterpret_cast<float4 *>(Bs + col * LDB + row) = __ldcs(gb + v);
+        }
+    }
+    __syncthreads();
+    const int b = b0 + lp;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = 16 * wq;
+    float acc[S::NB][4];
+#pragma unroll
+    for (int j = 0; j < S::NB; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const float *As = smem + lp * PER, *Bs = As + N * LDA;
+    if (b < batch) {
+#pragma unroll 2
+        for (int k0 = 0; k0 < N; k0 += 8) {
+            float af[4];
+            af[0] = As[(k0 + t) * LDA + m0 + g];
+            af[1] = As[(k0 + t) * LDA + m0 + g + 8];
+            af[2] = As[(k0 + t + 4) * LDA + m0 + g];
+            af[3] = As[(k0 + t + 4) * LDA + m0 + g + 8];
+            unsigned ah[4], al[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ah[u] = tf32_rna(af[u]);
+                if (SPLIT) al[u] = tf32_rna(af[u] - __uint_as_float(ah[u]));
+            }
+#pragma unroll
+            for (int j = 0; j < S::NB; ++j) {
+                const float b0v = Bs[(8 * j + g) * LDB + k0 + t], b1v = Bs[(8 * j + g) * LDB + k0 + t + 4];
+                unsigned bh[2] = {tf32_rna(b0v), tf32_rna(b1v)};
+                if (SPLIT) {
+                    unsigned bl[2] = {tf32_rna(b0v - __uint_as_float(bh[0])), tf32_rna(b1v - __uint_as_float(bh[1]))};
+                    mma_tf32(acc[j], al, bh);
+                    mma_tf32(acc[j], ah, bl);
+                }
+                mma_tf32(acc[j], ah, bh);
+            }
+        }
+    }
+    __syncthreads();
+    // C fragments -> shared (column-major, ld LDC) -> global
+    float *Cs = smem + lp * (N * S::LDC);
+    if (b < batch) {
+#pragma unroll
+        for (int j = 0; j < S::NB; ++j) {
+            const int c0 = 8 * j + 2 * t;
+            Cs[c0 * S::LDC + m0 + g] = acc[j][0];
+            Cs[(c0 + 1) * S::LDC + m0 + g] = acc[j][1];
+            Cs[c0 * S::LDC + m0 + g + 8] = acc[j][2];
+            Cs[(c0 + 1) * S::LDC + m0 + g + 8] = acc[j][3];
+        }
+    }
+    __syncthreads();
+    for (int p = 0; p < S::PPC; ++p) {
+        const int bb = b0 + p;
+        if (bb >= batch) break;
+        const float *cs = smem + p * (N * S::LDC);
+        float4 *gc = reinterpret_cast<float4 *>(C + (long long)bb * N * N);
+        for (int v = threadIdx.x; v < N * N / 4; v += blockDim.x) {
+            const int col = (4 * v) / N, row = (4 * v) % N;
+            __stcs(gc + v, *reinterpret_cast<const float4 *>(cs + col * S::LDC + row));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ BF16
+// As: A row-major (transposed on staging), lda = N + 8 halves; Bs: B
+// column-major, ldb = N + 8 halves.  A fragment pairs run along k.
+template <int N>
+__global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16 *__restrict__ A,
+                                                   const __nv_bfloat16 *__restrict__ B, float *__restrict__ C,
+                                                   int batch) {
+    using S = TcShape<N>;
+    constexpr int LD = N + 8;
+    constexpr int PERH = 2 * N * LD;  // halves per product
+    static_assert(PERH / 2 >= N * S::LDC, "C staging must fit in the operand staging");
+    extern __shared__ __align__(16) unsigned short hsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lp = warp / S::WP, wq = warp % S::WP;
+    const int b0 = blockIdx.x * S::PPC;
+    for (int p = 0; p < S::PPC; ++p) {
+        const int b = b0 + p;
+        if (b >= batch) break;
+        unsigned short *As = hsm + p * PERH, *Bs = As + N * LD;
+        const uint4 *ga = reinterpret_cast<const uint4 *>(A + (long long)b * N * N);
+        const uint4 *gb = reinterpret_cast<const uint4 *>(B + (long long)b * N * N);
+        for (int v = threadIdx.x; v < N * N / 8; v += blockDim.x) {
+            const int col = (8 * v) / N, row = (8 * v) % N;
+            const uint4 xa = __ldcs(ga + v);
+            const uint4 xb = __ldcs(gb + v);
+            *reinterpret_cast<uint4 *>(Bs + col * LD + row) = xb;
+            const unsigned short *h = reinterpret_cast<const unsigned short *>(&xa);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) As[(row + u) * LD + col] = h[u];
+        }
+    }
+    __syncthreads();
+    const int b = b0 + lp;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = 16 * wq;
+    float acc[S::NB][4];
+#pragma unroll
+    for (int j = 0; j < S::NB; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const unsigned short *As = hsm + lp * PERH, *Bs = As + N * LD;
+    if (b < batch) {
+#pragma unroll
+        for (int k0 = 0; k0 < N; k0 += 16) {
+            unsigned a[4];
+            a[0] = *reinterpret_cast<const unsigned *>(As + (m0 + g) * LD + k0 + 2 * t);
+            a[1] = *reinterpret_cast<const unsigned *>(As + (m0 + g + 8) * LD + k0 + 2 * t);
+            a[2] = *reinterpret_cast<const unsigned *>(As + (m0 + g) * LD + k0 + 2 * t + 8);
+            a[3] = *reinterpret_cast<const unsigned *>(As + (m0 + g + 8) * LD + k0 + 2 * t + 8);
+#pragma unroll
+            for (int j = 0; j < S::NB; ++j) {
+                unsigned bq[2];
+                bq[0] = *reinterpret_cast<const unsigned *>(Bs + (8 * j + g) * LD + k0 + 2 * t);
+                bq[1] = *reinterpret_cast<const unsigned *>(Bs + (8 * j + g) * LD + k0 + 2 * t + 8);
+                mma_bf16(acc[j], a, bq);
+            }
+        }
+    }
+    __syncthreads();
+    float *Cs = reinterpret_cast<float *>(hsm) + lp * (PERH / 2);
+    if (b < batch) {
+#pragma unroll
+        for (int j = 0; j < S::NB; ++j) {
+            const int c0 = 8 * j + 2 * t;
+            Cs[c0 * S::LDC + m0 + g] = acc[j][0];
+            Cs[(c0 + 1) * S::LDC + m0 + g] = acc[j][1];
+            Cs[c0 * S::LDC + m0 + g + 8] = acc[j][2];
+            Cs[(c0 + 1) * S::LDC + m0 + g + 8] = acc[j][3];
+        }
+    }
+    __syncthreads();
+    for (int p = 0; p < S::PPC; ++p) {
+        const int bb = b0 + p;
+        if (bb >= batch) break;
+        const float *cs = reinterpret_cast<const float *>(hsm) + p * (PERH / 2);
+        float4 *gc = reinterpret_cast<float4 *>(C + (long long)bb * N * N);
+        for (int v = threadIdx.x; v < N * N / 4; v += blockDim.x) {
+            const int col = (4 * v) / N, row = (4 * v) % N;
+            __stcs(gc + v, *reinterpret_cast<const float4 *>(cs + col * S::LDC + row));
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float *C, int batch, cudaStream_t st) {
+    // 16-byte staging needs 16-byte aligned operands
+    if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) != 0)
+        return cudaErrorInvalidConfiguration;
+    const int ppc = 4 / (n / 16);
+    const int grid = ceil_div(batch, ppc);
+    cudaError_t e;
+    if (math == GLASS_MATH_BF16_TC) {
+        const size_t smem = (size_t)ppc * 2 * n * (n + 8) * 2;
+        const __nv_bfloat16 *a = static_cast<const __nv_bfloat16 *>(A), *b = static_cast<const __nv_bfloat16 *>(B);
+#define BF(NN) do { if ((e = prepare(k_gemm_bf16<NN>, smem)) != cudaSuccess) return e;                     \
+        k_gemm_bf16<NN><<<grid, 128, smem, st>>>(a, b, C, batch); return cudaPeekAtLastError(); } while (0)
+        if (n == 16) BF(16);
+        if (n == 32) BF(32);
+        BF(64);
+#undef BF
+    }
+    const size_t smem = (size_t)ppc * (n * (n + 8) + n * (n + 4)) * 4;
+    const float *a = static_cast<const float *>(A), *b = static_cast<const float *>(B);
+#define TF(NN, SP) do { if ((e = prepare(k_gemm_tf32<NN, SP>, smem)) != cudaSuccess) return e;           \
+        k_gemm_tf32<NN, SP><<<grid, 128, smem, st>>>(a, b, C, batch); return cudaPeekAtLastError(); } while (0)
+    if (math == GLASS_MATH_TF32_TC) {
+        if (n == 16) TF(16, false);
+        if (n == 32) TF(32, false);
+        TF(64, false);
+    }
+    if (n == 16) TF(16, true);
+    if (n == 32) TF(32, true);
+    TF(64, true);
+#undef TF
+}
+
 }  // namespace glass

@@ -1,9 +1,9 @@
 // k_lu.cu -- batched getrf + getrs (partial pivoting) at thread, warp and
-// block scope.  The batched wrappers follow k_chol.cu: thread scope stages
-// 32*pack problems through shared memory, warp scope loads rows straight
-// into registers, block scope keeps each problem in its team's shared
-// memory.
+// block scope.  Thread scope stages 32*pack problems through shared memory;
+// warp scope loads rows straight into registers (one or two per lane);
+// block scope is a 64-thread row team (dev_rows.cuh), one row per thread.
 #include "dev_lu.cuh"
+#include "dev_rows.cuh"
 
 namespace glass {
 namespace {
@@ -72,79 +72,80 @@ __global__ void __launch_bounds__(256) k_lu_thread(int n_rt, int nrhs, Mat A, in
 }
 
 template <int NMAX>
-__global__ void __launch_bounds__(256) k_lu_warp(int n, int nrhs, Mat A, int *ipiv, Mat B, int *info, int batch) {
+__global__ void __launch_bounds__(256, NMAX <= 32 ? 2 : 1) k_lu_warp(int n, int nrhs, Mat A, int *ipiv, Mat B,
+                                                                    int *info, int batch) {
     constexpr int R = warp::LU<NMAX>::R;
+    extern __shared__ int ismem[];
     const int lane = threadIdx.x & 31;
+    int *sm = ismem + (threadIdx.x >> 5) * 2 * NMAX;
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= batch) return;
     float a[R][NMAX];
     int pos[R];
-    int pp[NMAX];
-    float prc[NMAX];
 #pragma unroll
     for (int k = 0; k < NMAX; ++k)
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int i = lane + 32 * q;
-            a[q][k] = (k < n && i < n) ? A.get(b, i, k) : 0.f;
+            a[q][k] = (k < n && i < n) ? A.cget(b, i, k) : 0.f;
         }
-    const int inf = warp::getrf<NMAX>(a, pos, pp, prc, ipiv + (long long)b * n, n);
+    const int inf = warp::getrf<NMAX>(a, pos, sm, ipiv + (long long)b * n, n);
     if (lane == 0) info[b] = inf;
     for (int c = 0; c < nrhs; ++c) {
         float x[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int i = lane + 32 * q;
-            x[q] = (i < n) ? B.get(b, i, c) : 0.f;
+            x[q] = (i < n) ? B.cget(b, i, c) : 0.f;
         }
-        warp::getrs<NMAX>(a, pos, pp, prc, x, n);
+        warp::getrs<NMAX>(a, pos, sm, x, n);
 #pragma unroll
         for (int q = 0; q < R; ++q)
-            if (lane + 32 * q < n) B.set(b, pos[q], c, x[q]);
+            if (lane + 32 * q < n) B.cset(b, pos[q], c, x[q]);
     }
 #pragma unroll
     for (int k = 0; k < NMAX; ++k)
 #pragma unroll
         for (int q = 0; q < R; ++q)
-            if (k < n && lane + 32 * q < n) A.set(b, pos[q], k, a[q][k]);
+            if (k < n && lane + 32 * q < n) A.cset(b, pos[q], k, a[q][k]);
 }
 
-template <int T>
-__global__ void __launch_bounds__(1024) k_lu_block(int n, int nrhs, Mat A, int *ipiv, Mat B, int *info, int batch) {
-    extern __shared__ float smem[];
-    const int team = threadIdx.x / T, rank = threadIdx.x % T;
-    const int P = blockDim.x / T;
-    const int b = blockIdx.x * P + team;
-    const int bar = 1 + team;
-    const int lda = n | 1;
-    const int per = n * lda + 2 * n + n * nrhs + 4;
-    float *a = smem + team * per;
-    int *piv = reinterpret_cast<int *>(a + n * lda);
-    float *rinv = a + n * lda + n;
-    float *x = rinv + n;
-    float *sc = x + n * nrhs;
+constexpr int kRS = 4;
+
+template <int NMAX>
+constexpr int lu_team_floats() {
+    return ((rows::Scratch<NMAX, kRS>::floats + 3) / 4) * 4;
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(256) k_lu_rows(int n, int nrhs, Mat A, int *ipiv, Mat B, int *info, int batch) {
+    extern __shared__ __align__(16) float smem[];
+    const int team = threadIdx.x / rows::T, i = threadIdx.x % rows::T;
+    const int b = blockIdx.x * (blockDim.x / rows::T) + team;
+    const int bid = 1 + team;
+    rows::Scratch<NMAX, kRS> s(smem + team * lu_team_floats<NMAX>());
     if (b >= batch) return;
-    for (int e = rank; e < n * n; e += T) {
-        const int j = e / n, i = e - j * n;
-        a[j * lda + i] = A.get(b, i, j);
+    float a[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) a[k] = (k < n && i < n) ? A.cget(b, i, k) : 0.f;
+    int pos;
+    bool done;
+    const int inf = rows::getrf<NMAX, kRS>(a, pos, done, n, i, s, ipiv + (long long)b * n, bid);
+    if (i == 0) info[b] = inf;
+    for (int c0 = 0; c0 < nrhs; c0 += kRS) {
+        float x[kRS];
+#pragma unroll
+        for (int c = 0; c < kRS; ++c) x[c] = (i < n && c0 + c < nrhs) ? B.cget(b, i, c0 + c) : 0.f;
+        rows::getrs<NMAX, kRS>(a, pos, x, n, i, s, bid);
+        if (i < n)
+#pragma unroll
+            for (int c = 0; c < kRS; ++c)
+                if (c0 + c < nrhs) B.cset(b, pos, c0 + c, x[c]);
     }
-    for (int e = rank; e < n * nrhs; e += T) {
-        const int c = e / n, i = e - c * n;
-        x[c * n + i] = B.get(b, i, c);
-    }
-    team_sync<T>(bar);
-    const int inf = block::getrf<T>(a, lda, n, piv, rinv, rank, bar, sc);
-    if (rank == 0) info[b] = inf;
-    for (int j = rank; j < n; j += T) ipiv[(long long)b * n + j] = piv[j];
-    for (int c = 0; c < nrhs; ++c) block::getrs<T>(a, lda, piv, rinv, x + c * n, n, rank, bar);
-    for (int e = rank; e < n * nrhs; e += T) {
-        const int c = e / n, i = e - c * n;
-        B.set(b, i, c, x[c * n + i]);
-    }
-    for (int e = rank; e < n * n; e += T) {
-        const int j = e / n, i = e - j * n;
-        A.set(b, i, j, a[j * lda + i]);
-    }
+    if (i < n)
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k)
+            if (k < n) A.cset(b, pos, k, a[k]);
 }
 
 template <typename K>
@@ -163,8 +164,13 @@ constexpr size_t kMaxSmem = 227 * 1024;
 size_t smem_lu(int n, int nrhs, Placement pl) {
     switch (pl.scope) {
         case SCOPE_THREAD: return (size_t)32 * pl.pack * (odd_stride(n * n) + (nrhs > 0 ? odd_stride(n * nrhs) : 0)) * 4;
-        case SCOPE_WARP: return 0;
-        default: return (size_t)pl.pack * (n * (n | 1) + 2 * n + n * nrhs + 4) * 4;
+        case SCOPE_WARP: return (size_t)pl.pack * 2 * 64 * 4;
+        default: {
+            const int N = n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64;
+            const int f = N == 8 ? lu_team_floats<8>() : N == 16 ? lu_team_floats<16>()
+                        : N == 32 ? lu_team_floats<32>() : lu_team_floats<64>();
+            return (size_t)pl.pack * f * 4;
+        }
     }
 }
 
@@ -174,7 +180,7 @@ bool feasible_lu(int n, int nrhs, Placement pl) {
     if (n < 1 || n > 64 || nrhs < 0) return false;
     if (pl.pack != 1 && pl.pack != 2 && pl.pack != 4 && pl.pack != 8) return false;
     if (pl.scope == SCOPE_THREAD && n > 12) return false;
-    if (pl.scope == SCOPE_BLOCK && block_team(n) * pl.pack > 1024) return false;
+    if (pl.scope == SCOPE_BLOCK && rows::T * pl.pack > 256) return false;
     return smem_lu(n, nrhs, pl) <= kMaxSmem;
 }
 
@@ -203,15 +209,18 @@ cudaError_t launch_getrf_getrs(int n, int nrhs, Mat A, int *ipiv, Mat B, int *in
     const int grid = ceil_div(batch, pl.pack);
     if (pl.scope == SCOPE_WARP) {
         const int th = 32 * pl.pack;
-        if (n <= 8) return go(k_lu_warp<8>, grid, th, 0, st, n, nrhs, A, ipiv, B, info, batch);
-        if (n <= 16) return go(k_lu_warp<16>, grid, th, 0, st, n, nrhs, A, ipiv, B, info, batch);
-        if (n <= 32) return go(k_lu_warp<32>, grid, th, 0, st, n, nrhs, A, ipiv, B, info, batch);
-        return go(k_lu_warp<64>, grid, th, 0, st, n, nrhs, A, ipiv, B, info, batch);
+        const int N = n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64;
+        const size_t sw = (size_t)pl.pack * 2 * N * 4;
+        if (N == 8) return go(k_lu_warp<8>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
+        if (N == 16) return go(k_lu_warp<16>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
+        if (N == 32) return go(k_lu_warp<32>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
+        return go(k_lu_warp<64>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
     }
-    const int T = block_team(n);
-    if (T == 64) return go(k_lu_block<64>, grid, 64 * pl.pack, smem, st, n, nrhs, A, ipiv, B, info, batch);
-    if (T == 128) return go(k_lu_block<128>, grid, 128 * pl.pack, smem, st, n, nrhs, A, ipiv, B, info, batch);
-    return go(k_lu_block<256>, grid, 256 * pl.pack, smem, st, n, nrhs, A, ipiv, B, info, batch);
+    const int th = rows::T * pl.pack;
+    if (n <= 8) return go(k_lu_rows<8>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
+    if (n <= 16) return go(k_lu_rows<16>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
+    if (n <= 32) return go(k_lu_rows<32>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
+    return go(k_lu_rows<64>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
 }
 
 }  // namespace glass

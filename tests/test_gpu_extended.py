@@ -1,0 +1,245 @@
+"""Parity of the precision path (tensor-core GEMM, FP64-residual refinement),
+the mixed-size persistent posv, and the learned cost model's kernels against
+the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2609_28179_gb300 as g
+from paper_2609_28179_gb300 import workloads as W
+from tests.helpers import U32, backward_error, host, sync, to_dev, zeros_i32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2609_28179_gb300 import _build
+    _build.build()
+    g.lib()
+
+
+def mats(flat, batch, r, c):
+    return W.from_colmajor(flat, batch, r, c)
+
+
+def bf16_round(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def tf32_round(x):
+    """Round to nearest (ties away) at 10 mantissa bits, as cvt.rna.tf32.f32."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return u.view(np.float32)
+
+
+# ------------------------------------------------------------ tensor cores
+@pytest.mark.parametrize("n", [16, 32, 64])
+@pytest.mark.parametrize("math", [g.GLASS_MATH_BF16_TC, g.GLASS_MATH_TF32_TC, g.GLASS_MATH_3XTF32_TC])
+def test_tc_gemm_integer_bit_exact(n, math):
+    import torch
+    batch = 37
+    A = W.colmajor(W.int_matrix(n, n, batch, 2000 + n))
+    B = W.colmajor(W.int_matrix(n, n, batch, 2100 + n))
+    ref = oracle.gemm(n, n, n, A.astype(np.float64), B.astype(np.float64), batch)
+    if math == g.GLASS_MATH_BF16_TC:
+        dA = torch.from_numpy(A).to("cuda").to(torch.bfloat16)
+        dB = torch.from_numpy(B).to("cuda").to(torch.bfloat16)
+        o = g.make_opts(dtype=g.GLASS_BF16, math=math)
+    else:
+        dA, dB = to_dev(A), to_dev(B)
+        o = g.make_opts(math=math)
+    dC = to_dev(np.full(batch * n * n, np.nan, np.float32))
+    g.check(g.glass_batched_gemm(n, n, n, dA, n, n * n, dB, n, n * n, dC, n, n * n, batch, o))
+    sync()
+    assert np.array_equal(host(dC).astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("n", [16, 32, 64])
+def test_tc_gemm_gaussian_errors(n):
+    """BF16 and TF32 products match the FP64 product of the ROUNDED operands
+    to FP32 accumulation accuracy; 3xTF32 meets the FP32 bound on the
+    original operands (its error against FP64 is stated, 1e-4 bar)."""
+    import torch
+    batch = 301
+    A = W.gaussian(batch * n * n, 2200 + n)
+    B = W.gaussian(batch * n * n, 2300 + n)
+    absAB = np.abs(mats(A, batch, n, n)) @ np.abs(mats(B, batch, n, n))
+    for math in (g.GLASS_MATH_BF16_TC, g.GLASS_MATH_TF32_TC, g.GLASS_MATH_3XTF32_TC):
+        if math == g.GLASS_MATH_BF16_TC:
+            Ar, Br = bf16_round(A), bf16_round(B)
+            dA = torch.from_numpy(A).to("cuda").to(torch.bfloat16)
+            dB = torch.from_numpy(B).to("cuda").to(torch.bfloat16)
+            o = g.make_opts(dtype=g.GLASS_BF16, math=math)
+        else:
+            Ar, Br = (tf32_round(A), tf32_round(B)) if math == g.GLASS_MATH_TF32_TC else (A, B)
+            dA, dB = to_dev(A), to_dev(B)
+            o = g.make_opts(math=math)
+        ref = oracle.gemm(n, n, n, Ar.astype(np.float64), Br.astype(np.float64), batch)
+        dC = to_dev(np.zeros(batch * n * n, np.float32))
+        g.check(g.glass_batched_gemm(n, n, n, dA, n, n * n, dB, n, n * n, dC, n, n * n, batch, o))
+        sync()
+        C = mats(host(dC).astype(np.float64), batch, n, n)
+        err = np.abs(C - mats(ref, batch, n, n)) / (absAB + 1e-30)
+        # 3xTF32 drops the lo*lo term (<= 2^-22 relative) on top of FP32 accumulation
+        bound = 2 * n * U32 + (2.0 ** -20 if math == g.GLASS_MATH_3XTF32_TC else 0.0)
+        assert err.max() <= bound, (n, math, err.max(), bound)
+        rel = np.linalg.norm((C - mats(oracle.gemm(n, n, n, A.astype(np.float64), B.astype(np.float64), batch),
+                                        batch, n, n)).reshape(batch, -1), axis=1) / (
+            np.linalg.norm(mats(A, batch, n, n).reshape(batch, -1), axis=1) *
+            np.linalg.norm(mats(B, batch, n, n).reshape(batch, -1), axis=1))
+        if math == g.GLASS_MATH_3XTF32_TC:
+            assert rel.max() <= 1e-4
+
+
+# -------------------------------------------------------------- refinement
+@pytest.mark.parametrize("n", [8, 32, 64])
+@pytest.mark.parametrize("kappa", [1e1, 1e3])
+def test_refined_posv_improves_forward_error(n, kappa):
+    batch = 96
+    A = W.kappa_spd(n, batch, kappa, 2400 + n)
+    b = W.gaussian(batch * n, 2401 + n)
+    _, Xs, info_ref = oracle.posv(n, 1, A.astype(np.float64), b.astype(np.float64), batch)
+    Am = mats(A, batch, n, n).astype(np.float64)
+    scopes = [(1, 1), (2, 1)] + ([(0, 1)] if n <= 16 else [])
+    for scope, pack in scopes:
+        res = {}
+        for refine in (0, 1):
+            for fp64d in (0, 1):
+                dA, dB, info = to_dev(A), to_dev(b), zeros_i32(batch)
+                o = g.make_opts(scope=scope, pack=pack, refine_steps=refine, fp64_diag=fp64d)
+                g.check(g.glass_batched_posv(n, 1, dA, n, n * n, dB, n, n, info, batch, o))
+                sync()
+                assert (host(info)[:batch] == 0).all()
+                X = host(dB).astype(np.float64)
+                fwd = np.abs(X - Xs).reshape(batch, n).max(1) / np.abs(Xs).reshape(batch, n).max(1)
+                be = backward_error(Am, mats(X, batch, n, 1), mats(b, batch, n, 1).astype(np.float64))
+                res[(refine, fp64d)] = (fwd, be)
+                assert be.max() <= 1e-4, (n, kappa, scope, refine, be.max())
+        f0, f1 = res[(0, 0)][0], res[(1, 0)][0]
+        assert np.median(f1) <= np.median(f0), (n, kappa, scope, np.median(f0), np.median(f1))
+        assert res[(1, 0)][1].max() <= res[(0, 0)][1].max() * 1.5 + 1e-7
+
+
+# ----------------------------------------------------------- mixed sizes
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_varsize_posv_matches_oracle(nrhs):
+    import torch
+    batch = 777
+    sizes = W.varsize_sizes(batch, 2500, lo=1, hi=64)
+    A, B, offA, offB = W.varsize_pack(sizes, nrhs, 2501)
+    dn = torch.from_numpy(sizes).cuda()
+    doA = torch.from_numpy(offA).cuda()
+    doB = torch.from_numpy(offB).cuda()
+    dA, dB = to_dev(A), to_dev(B)
+    info = zeros_i32(batch)
+    wsb = g.glass_posv_varsize_workspace(batch)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    for wpc in (0, 1, 4, 8):
+        dA.copy_(torch.from_numpy(A))
+        dB.copy_(torch.from_numpy(B))
+        o = g.make_opts(scope=g.GLASS_SCOPE_WARP if wpc else g.GLASS_SCOPE_AUTO, pack=wpc)
+        g.check(g.glass_posv_varsize(batch, dn, doA, doB, nrhs, dA, dB, info, ws, wsb, o))
+        sync()
+        assert (host(info)[:batch] == 0).all()
+        LA, XA = host(dA).astype(np.float64), host(dB).astype(np.float64)
+        for i in range(0, batch, 7):
+            n = int(sizes[i])
+            L, X, inf = oracle.posv(n, nrhs, A[offA[i]:offA[i] + n * n].astype(np.float64),
+                                    B[offB[i]:offB[i] + n * nrhs].astype(np.float64), 1)
+            x = XA[offB[i]:offB[i] + n * nrhs]
+            assert np.abs(x - X).max() <= 1e-4 * np.abs(X).max(), (i, n, wpc)
+            l = np.tril(mats(LA[offA[i]:offA[i] + n * n], 1, n, n)[0])
+            assert np.abs(l - np.tril(mats(L, 1, n, n)[0])).max() <= 1e-4 * np.abs(L).max()
+
+
+def test_varsize_flags_bad_orders_and_failures_and_is_graph_capturable():
+    import torch
+    batch = 300
+    sizes = W.varsize_sizes(batch, 2600, lo=6, hi=64)
+    sizes[5] = 0
+    sizes[17] = 65
+    A, B, offA, offB = W.varsize_pack(np.clip(sizes, 1, 64), 1, 2601)
+    # instance 40 is not SPD at its column 2
+    n40 = int(sizes[40])
+    A40 = A[offA[40]:offA[40] + n40 * n40].reshape(n40, n40)
+    A40[2, 2] = -1.0
+    dn = torch.from_numpy(sizes).cuda()
+    doA, doB = torch.from_numpy(offA).cuda(), torch.from_numpy(offB).cuda()
+    dA, dB = to_dev(A), to_dev(B)
+    info = zeros_i32(batch)
+    wsb = g.glass_posv_varsize_workspace(batch)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    # record into a CUDA graph, replay twice on fresh inputs
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.graph(graph, stream=s):
+        st = g.glass_posv_varsize(batch, dn, doA, doB, 1, dA, dB, info, ws, wsb, None)
+    assert st == g.GLASS_OK
+    for _ in range(2):
+        dA.copy_(torch.from_numpy(A))
+        dB.copy_(torch.from_numpy(B))
+        info.fill_(99)
+        graph.replay()
+        sync()
+        inf = host(info)[:batch]
+        assert inf[5] == -1 and inf[17] == -1
+        assert 1 <= inf[40] <= 3
+        ok = np.ones(batch, bool)
+        ok[[5, 17, 40]] = False
+        assert (inf[ok] == 0).all()
+    assert g.glass_last_device_status() == g.GLASS_OK
+
+
+# ------------------------------------------------------------- cost model
+DIN, H, DOUT = 8, 64, 12
+NP = 5516
+
+
+def _mlp_data(rows, seed):
+    gg = W.rng(seed)
+    w = (gg.standard_normal(NP) * 0.2).astype(np.float32)
+    X = gg.standard_normal((rows, DIN)).astype(np.float32)
+    T = gg.standard_normal((rows, DOUT)).astype(np.float32)
+    M = (gg.random((rows, DOUT)) > 0.25).astype(np.float32)
+    return w, X, T, M
+
+
+@pytest.mark.parametrize("rows", [1, 63, 64, 257, 5000])
+def test_mlp_forward_and_gradient_vs_oracle(rows):
+    import torch
+    w, X, T, M = _mlp_data(rows, 2700 + rows)
+    dw, dX, dT, dM = to_dev(w), to_dev(X.reshape(-1)), to_dev(T.reshape(-1)), to_dev(M.reshape(-1))
+    dY = to_dev(np.zeros(rows * DOUT, np.float32))
+    g.check(g.glass_mlp_forward(DIN, dw, rows, dX, dY))
+    Yref = oracle.mlp_fwd(DIN, H, DOUT, w.astype(np.float64), X.astype(np.float64))
+    sync()
+    Y = host(dY).reshape(rows, DOUT)
+    assert np.abs(Y - Yref).max() <= 1e-4 * max(1.0, np.abs(Yref).max())
+    wsb = g.glass_mlp_workspace(rows)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    dg = to_dev(np.zeros(NP, np.float32))
+    dl = to_dev(np.zeros(1, np.float32))
+    g.check(g.glass_mlp_loss_grad(DIN, dw, rows, dX, dT, dM, dg, dl, ws, wsb))
+    loss_ref, grad_ref = oracle.mlp_loss_grad(DIN, H, DOUT, w.astype(np.float64), X.astype(np.float64),
+                                              T.astype(np.float64), M.astype(np.float64))
+    sync()
+    assert abs(float(host(dl)[0]) - loss_ref) <= 1e-4 * abs(loss_ref)
+    gr = host(dg).astype(np.float64)
+    assert np.linalg.norm(gr - grad_ref) <= 1e-4 * np.linalg.norm(grad_ref)
+
+
+def test_mlp_adam_matches_oracle_step():
+    w, _, _, _ = _mlp_data(1, 2800)
+    gr = W.gaussian(NP, 2801)
+    m0 = (W.gaussian(NP, 2802) * 0.1).astype(np.float32)
+    v0 = np.abs(W.gaussian(NP, 2803)).astype(np.float32) * 0.01
+    dw, dg, dm, dv = to_dev(w), to_dev(gr), to_dev(m0), to_dev(v0)
+    g.check(g.glass_mlp_adam(NP, dw, dg, dm, dv, 3, 1e-3))
+    wr, mr, vr = w.astype(np.float64), m0.astype(np.float64), v0.astype(np.float64)
+    oracle.adam_step(wr, gr.astype(np.float64), mr, vr, 3, lr=1e-3)
+    sync()
+    assert np.abs(host(dw) - wr).max() <= 1e-6
+    assert np.abs(host(dm) - mr).max() <= 1e-6 and np.abs(host(dv) - vr).max() <= 1e-6
