@@ -310,6 +310,236 @@ def traffic_for(kernel_key):
     return d.get("cells", {}).get(kernel_key)
 
 
+# ------------------------------------------------------------ other configs
+def _graph_time(fn, reps, iters=5, setup=None):
+    """Median ms of `reps` back-to-back calls of fn captured in one graph."""
+    import torch
+    if setup:
+        setup()
+    fn()  # warm (module load, attributes) outside capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.graph(graph, stream=s):
+        for _ in range(reps):
+            fn()
+    out = []
+    for _ in range(iters):
+        if setup:
+            setup()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b) / reps)
+    return statistics.median(out)
+
+
+def extra_plain_posv(peaks):
+    """Plain batched Cholesky factor+solve: 1024 SPD systems, n = 6, one RHS,
+    one thread per matrix (no tuning)."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300 import workloads as W
+    from paper_2609_28179_gb300.cells import bytes_flops
+    n, batch = 6, 1024
+    A = torch.from_numpy(W.spd(n, batch, 1000)).cuda()
+    b = torch.from_numpy(W.gaussian(n * batch, 1001)).cuda()
+    sets = 64
+    As = [A.clone() for _ in range(sets)]
+    bs = [b.clone() for _ in range(sets)]
+    info = torch.zeros(batch, dtype=torch.int32, device="cuda")
+    o = g.make_opts(scope=g.GLASS_SCOPE_THREAD, pack=1)
+    k = [0]
+
+    def fn():
+        i = k[0] % sets
+        k[0] += 1
+        g.glass_batched_posv(n, 1, As[i], n, n * n, bs[i], n, n, info, batch, o)
+
+    def setup():
+        for x, y in zip(As, bs):
+            x.copy_(A)
+            y.copy_(b)
+    ms = _graph_time(fn, sets, setup=setup)
+    by = bytes_flops("posv", n, 1)[0] * batch
+    return {"workload": "posv n=6 batch 1024 nrhs 1, one thread per matrix", "us": ms * 1e3,
+            "matrices_per_s": batch / (ms / 1e3), "gbs": by / (ms / 1e3) / 1e9,
+            "frac_hbm": by / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "note": "3.5 kB per launch: launch/latency bound, not bandwidth bound"}
+
+
+def extra_varsize(peaks, wpcs=(0, 2, 4, 8)):
+    """8192 SPD systems, n ~ U{6..64}, 4 RHS, one persistent launch (with its
+    binning kernel) per graph node, replayed."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300 import workloads as W
+    from paper_2609_28179_gb300.cells import bytes_flops
+    batch, nrhs = 8192, 4
+    sizes = W.varsize_sizes(batch, 1003)
+    A, B, offA, offB = W.varsize_pack(sizes, nrhs, 1004)
+    dn = torch.from_numpy(sizes).cuda()
+    doA, doB = torch.from_numpy(offA).cuda(), torch.from_numpy(offB).cuda()
+    A0, B0 = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    sets = 8
+    As = [A0.clone() for _ in range(sets)]
+    Bs = [B0.clone() for _ in range(sets)]
+    info = torch.zeros(batch, dtype=torch.int32, device="cuda")
+    wsb = g.glass_posv_varsize_workspace(batch)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    by = sum(bytes_flops("posv", int(n), nrhs)[0] for n in sizes)
+    out = {"workload": "8192 SPD systems, n ~ U{6..64}, 4 RHS, persistent posv in a CUDA graph",
+           "bytes_per_launch": by, "schedules": {}}
+
+    def setup():
+        for x, y in zip(As, Bs):
+            x.copy_(A0)
+            y.copy_(B0)
+    for wpc in wpcs:
+        o = g.make_opts(scope=g.GLASS_SCOPE_WARP if wpc else g.GLASS_SCOPE_AUTO, pack=wpc)
+        k = [0]
+
+        def fn():
+            i = k[0] % sets
+            k[0] += 1
+            g.glass_posv_varsize(batch, dn, doA, doB, nrhs, As[i], Bs[i], info, ws, wsb, o)
+        ms = _graph_time(fn, sets, setup=setup)
+        out["schedules"][f"warps_per_cta={wpc or 8}"] = {"us": ms * 1e3, "matrices_per_s": batch / (ms / 1e3),
+                                                         "gbs": by / (ms / 1e3) / 1e9,
+                                                         "frac_hbm": by / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    best = min(out["schedules"].items(), key=lambda kv: kv[1]["us"])
+    out["best"] = {"schedule": best[0], **best[1]}
+    return out
+
+
+def extra_tc_gemm(peaks, batch=65536):
+    """Tensor-core batched GEMM, n in {16, 32, 64}, batch 65536, inputs N(0,1)."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    out = {}
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1004)
+    for n in (16, 32, 64):
+        A = torch.randn(batch * n * n, generator=gen, device="cuda")
+        B = torch.randn(batch * n * n, generator=gen, device="cuda")
+        C = torch.empty_like(A)
+        Ab, Bb = A.to(torch.bfloat16), B.to(torch.bfloat16)
+        for name, math_, dt, a, b, bpe in (("bf16", g.GLASS_MATH_BF16_TC, g.GLASS_BF16, Ab, Bb, 2),
+                                           ("tf32", g.GLASS_MATH_TF32_TC, g.GLASS_F32, A, B, 4),
+                                           ("3xtf32", g.GLASS_MATH_3XTF32_TC, g.GLASS_F32, A, B, 4),
+                                           ("fp32_simt", g.GLASS_MATH_FP32, g.GLASS_F32, A, B, 4)):
+            o = g.make_opts(dtype=dt, math=math_)
+            fn = lambda: g.glass_batched_gemm(n, n, n, a, n, n * n, b, n, n * n, C, n, n * n, batch, o)
+            g.check(fn(), f"tc gemm {name}")
+            ms = _graph_time(fn, 4)
+            by = (2 * bpe + 4) * n * n * batch
+            fl = 2 * n ** 3 * batch
+            out[f"{name}_n{n}"] = {"us": ms * 1e3, "matrices_per_s": batch / (ms / 1e3),
+                                   "gbs": by / (ms / 1e3) / 1e9, "tflops": fl / (ms / 1e3) / 1e12,
+                                   "frac_hbm": by / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    return out
+
+
+def extra_refine(peaks, batch=16384):
+    """Refined SPD solve: n in {32, 64}, kappa swept 1e1..1e6, one FP64-residual
+    step; forward error of x0 and x1 against the FP64 solution (numpy/LAPACK)
+    of the same FP32-rounded systems on a sample, and time at full batch."""
+    import numpy as np
+    import torch
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300 import workloads as W
+    from paper_2609_28179_gb300.cells import bytes_flops
+    out = {}
+    sample = 128
+    for n in (32, 64):
+        for kappa in (1e1, 1e3, 1e6):
+            A = W.kappa_spd(n, sample, kappa, 1005)
+            b = W.gaussian(n * sample, 1006)
+            Am = W.from_colmajor(A, sample, n, n).astype(np.float64)
+            # FP64 reference solution of the FP32-rounded system (LAPACK via numpy)
+            Xs = np.linalg.solve(Am, b.reshape(sample, n, 1).astype(np.float64)).reshape(-1)
+            row = {}
+            for refine in (0, 1):
+                dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
+                info = torch.zeros(sample, dtype=torch.int32, device="cuda")
+                o = g.make_opts(scope=g.GLASS_SCOPE_WARP, pack=1, refine_steps=refine, fp64_diag=refine)
+                g.check(g.glass_batched_posv(n, 1, dA, n, n * n, dB, n, n, info, sample, o))
+                X = dB.cpu().numpy().astype(np.float64)
+                inf = info.cpu().numpy()
+                ok = inf == 0
+                fwd = (np.abs(X - Xs).reshape(sample, n).max(1) / np.abs(Xs).reshape(sample, n).max(1))[ok]
+                Xm = X.reshape(sample, n, 1)
+                bm = b.reshape(sample, n, 1).astype(np.float64)
+                R = bm - Am @ Xm
+                be = (np.abs(R).max((1, 2)) / (np.abs(Am).sum(2).max(1) * np.abs(Xm).max((1, 2)) +
+                                               np.abs(bm).max((1, 2))))[ok]
+                row[f"x{refine}"] = {"fwd_err_median": float(np.median(fwd)) if ok.any() else None,
+                                     "bwd_err_max": float(be.max()) if ok.any() else None,
+                                     "failed": int((~ok).sum())}
+            out[f"n{n}_kappa{kappa:.0e}"] = row
+    # time at full batch (kappa 1e3 inputs), refined and plain
+    for n in (32, 64):
+        A = torch.from_numpy(W.kappa_spd(n, 256, 1e3, 1007)).cuda().repeat(batch // 256)
+        b = torch.from_numpy(W.gaussian(n * batch, 1008)).cuda()
+        sets = 4
+        As = [A.clone() for _ in range(sets)]
+        bs = [b.clone() for _ in range(sets)]
+        info = torch.zeros(batch, dtype=torch.int32, device="cuda")
+
+        def setup():
+            for x, y in zip(As, bs):
+                x.copy_(A)
+                y.copy_(b)
+        for refine in (0, 1):
+            o = g.make_opts(refine_steps=refine, fp64_diag=refine)
+            k = [0]
+
+            def fn():
+                i = k[0] % sets
+                k[0] += 1
+                g.glass_batched_posv(n, 1, As[i], n, n * n, bs[i], n, n, info, batch, o)
+            ms = _graph_time(fn, sets, setup=setup)
+            by = bytes_flops("posv", n, 1)[0] * batch + (4 * n * batch if refine else 0)
+            out[f"time_n{n}_refine{refine}"] = {"us": ms * 1e3, "matrices_per_s": batch / (ms / 1e3),
+                                                "gbs": by / (ms / 1e3) / 1e9}
+    return out
+
+
+def extra_learned():
+    """Median / p90 regret of the learned placement model on held-out measured
+    points, against nearest-grid table lookup and the best fixed placement
+    (the model is trained here, on the GPU, from the committed measurements)."""
+    import paper_2609_28179_gb300.learned as Lm
+    tdir = os.path.join(ROOT, "paper_2609_28179_gb300", "tuning")
+    tr, ho = os.path.join(tdir, "sm103_random_train.jsonl"), os.path.join(tdir, "sm103_random_heldout.jsonl")
+    if not (os.path.exists(tr) and os.path.exists(ho)):
+        return {"unavailable": "no committed random-point measurements"}
+    train_pts, held = Lm.load_points(tr), Lm.load_points(ho)
+    t0 = time.perf_counter()
+    w, mu, sd, losses = Lm.train(train_pts, epochs=300)
+    res = Lm.evaluate(w, mu, sd, train_pts, held)
+    res["train_seconds"] = time.perf_counter() - t0
+    res["final_loss"] = losses[-1]
+    return res
+
+
+def run_extras(peaks, which):
+    out = {}
+    for name, fn in (("plain_posv_n6", lambda: extra_plain_posv(peaks)), ("mixed_size", lambda: extra_varsize(peaks)),
+                     ("tensor_core_gemm", lambda: extra_tc_gemm(peaks)), ("refined_posv", lambda: extra_refine(peaks)),
+                     ("learned_placement", extra_learned)):
+        if which != "all" and name not in which.split(","):
+            continue
+        try:
+            out[name] = fn()
+        except Exception as e:  # report, do not hide: the line says what failed
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -323,6 +553,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sample-div", type=int, default=64)
+    ap.add_argument("--extras", default="all", help="comma list of extra configs, 'all' or 'none'")
     args = ap.parse_args()
     from paper_2609_28179_gb300.cells import OPS, SWEEP_N
     args.ops = args.ops or OPS
@@ -429,6 +660,8 @@ def main():
                        "ms_per_step": t_e2e / args.steps}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline([c.host for c in cells], [(c.op, c.n) for c in cells], args.batch)
+    if rank == 0 and args.extras != "none":
+        line["extras"] = run_extras(peaks, args.extras)
     line["cells"] = rows
     if rank == 0:
         print(json.dumps(line))

@@ -32,7 +32,9 @@
  *    in info[b] (0 = success, j+1 = column j is the first failing column),
  *    LAPACK style.  Outputs of a failed problem are unspecified.
  *  - Triangular factors are lower ('L'); the strict upper triangle of a
- *    factored matrix is neither read nor written.
+ *    factored or triangular operand is never used and keeps its contents.
+ *  - Warp and block scopes accept the column-major layout only; the
+ *    interleaved layout is served at thread scope.
  *  - No C++ exception crosses this interface.
  */
 #ifndef GLASS_H
@@ -137,11 +139,11 @@ glass_status glass_batched_potrs(int n, int nrhs, const void *L, int lda, long l
 
 /* Batched SPD solve, fused factor + solve kept on chip (glass::posv of
  * Sec. III-A; POSV of Sec. IV-D).  A is overwritten by L (lower), B by X.
- * With opts->refine_steps == 1 a copy of A is kept on chip, the residual
- * r = b - A x0 is formed in FP64 and one correction dx = solve(L, r) is
- * added (x1 = x0 + dx); opts->fp64_diag computes the diagonal square roots
- * and reciprocals in FP64.  Refinement requires nrhs == 1 is NOT required:
- * every right-hand side is refined. */
+ * With opts->refine_steps == 1 the residual r = b - A x0 is formed in FP64
+ * from the original A (re-read before L is written back) and one correction
+ * dx = solve(L, r) is added, x1 = x0 + dx, for every right-hand side;
+ * opts->fp64_diag computes the diagonal square roots and reciprocals in
+ * FP64.  nrhs == 0 factors only. */
 glass_status glass_batched_posv(int n, int nrhs, void *A, int lda, long long sA,
                                 void *B, int ldb, long long sB, int *info,
                                 int batch, const glass_opts *opts, glass_stream_t stream);

@@ -188,9 +188,12 @@ Placement resolve(int op, int n, int k, int batch, int use_learned) {
 }
 
 // Placement of a call: explicit (validated) or resolved from the table.
+// The interleaved layout is served at thread scope only.
 glass_status placement_of(int op, int n, int k, int batch, const glass_opts &o, Placement &pl) {
+    const bool inter = o.layout == GLASS_LAYOUT_INTERLEAVED32;
     if (o.placement.scope == GLASS_SCOPE_AUTO) {
         pl = resolve(op, n, k, batch, o.use_learned);
+        if (inter && pl.scope != SCOPE_THREAD) pl = Placement{SCOPE_THREAD, 1};
         if (o.placement.pack != 0) {
             if (!valid_pack(o.placement.pack)) return GLASS_ERR_INVALID_VALUE;
             pl.pack = o.placement.pack;
@@ -202,7 +205,8 @@ glass_status placement_of(int op, int n, int k, int batch, const glass_opts &o, 
         pl.pack = o.placement.pack == 0 ? 1 : o.placement.pack;
         if (!valid_pack(pl.pack)) return GLASS_ERR_INVALID_VALUE;
     }
-    if (!feasible(op, n, k, pl)) return GLASS_ERR_INVALID_VALUE;
+    if (inter && pl.scope != SCOPE_THREAD) return GLASS_ERR_UNSUPPORTED;
+    if (!feasible(op, n, k, pl)) return inter ? GLASS_ERR_UNSUPPORTED : GLASS_ERR_INVALID_VALUE;
     return GLASS_OK;
 }
 
@@ -254,7 +258,7 @@ glass_status glass_batched_gemm(int m, int n, int k, const void *A, int lda, lon
         return GLASS_ERR_INVALID_VALUE;
     Placement pl;
     const int nn = m > n ? (m > k ? m : k) : (n > k ? n : k);
-    if (o.placement.scope == GLASS_SCOPE_AUTO) {
+    if (o.placement.scope == GLASS_SCOPE_AUTO && o.layout == GLASS_LAYOUT_COLMAJOR) {
         pl = resolve(GLASS_OP_GEMM, nn, nn, batch, o.use_learned);
         if (o.placement.pack != 0) pl.pack = o.placement.pack;
         if (!feasible_gemm(m, n, k, pl)) {
@@ -264,6 +268,7 @@ glass_status glass_batched_gemm(int m, int n, int k, const void *A, int lda, lon
     } else {
         GLASS_TRY(placement_of(GLASS_OP_GEMM, nn, nn, batch, o, pl));
     }
+    if (o.layout == GLASS_LAYOUT_INTERLEAVED32 && pl.scope != SCOPE_THREAD) return GLASS_ERR_UNSUPPORTED;
     if (!feasible_gemm(m, n, k, pl)) return GLASS_ERR_INVALID_VALUE;
     return from_cuda(launch_gemm(m, n, k, make_mat(A, lda, sA, m, k, o.layout), make_mat(B, ldb, sB, k, n, o.layout),
                                  make_mat(C, ldc, sC, m, n, o.layout), batch, pl, st));

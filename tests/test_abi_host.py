@@ -111,3 +111,12 @@ def test_learned_model_rejects_bad_weights(L):
     import numpy as np
     assert g.glass_set_learned_model(np.zeros(10), np.zeros(8), np.ones(8)) == g.GLASS_ERR_INVALID_VALUE
     assert g.glass_set_learned_model(np.zeros(5516), np.zeros(8), np.zeros(8)) == g.GLASS_ERR_INVALID_VALUE
+
+
+def test_interleaved_layout_is_thread_scope_only(L):
+    o = g.make_opts(layout=g.GLASS_LAYOUT_INTERLEAVED32, scope=g.GLASS_SCOPE_WARP, pack=1)
+    assert g.glass_batched_posv(6, 1, BAD, 6, 36, BAD, 6, 6, BAD, 4, o, 0) == g.GLASS_ERR_UNSUPPORTED
+    o = g.make_opts(layout=g.GLASS_LAYOUT_INTERLEAVED32, scope=g.GLASS_SCOPE_BLOCK, pack=1)
+    assert g.glass_batched_getrf_getrs(6, 1, BAD, 6, 36, BAD, BAD, 6, 6, BAD, 4, o, 0) == g.GLASS_ERR_UNSUPPORTED
+    o = g.make_opts(layout=g.GLASS_LAYOUT_INTERLEAVED32)   # auto: no thread-scope kernel above n = 16
+    assert g.glass_batched_posv(40, 1, BAD, 40, 1600, BAD, 40, 40, BAD, 4, o, 0) == g.GLASS_ERR_UNSUPPORTED
