@@ -223,6 +223,22 @@ glass_status glass_posv_varsize(int batch, const int *n_dev, const long long *of
                                 int *info, void *ws, size_t ws_bytes,
                                 const glass_opts *opts, glass_stream_t stream);
 
+/* The same mixed-size solve for callers that cannot allocate device memory
+ * (a real-time loop that forbids allocation once running, or a program whose
+ * device memory belongs to another allocator): the scratch lives in a fixed
+ * array inside the library, one per device, sized for batch <= 65536
+ * (about 260 KB, held by every GPU that loads the library until exit).
+ * The paper has no counterpart of this entry point.  Arguments are those of
+ * glass_posv_varsize without ws / ws_bytes; batch > 65536 returns
+ * GLASS_ERR_UNSUPPORTED and launches nothing; nothing is allocated.  The
+ * first call on a device looks up the array's device address, so make it
+ * before any stream capture.  Every call on a device shares the array: calls
+ * that overlap on the GPU race.  Each call rebuilds all the scratch it reads,
+ * so earlier contents never leak into a result. */
+glass_status glass_posv_varsize_noalloc(int batch, const int *n_dev, const long long *offA_dev,
+                                        const long long *offB_dev, int nrhs, void *A, void *B,
+                                        int *info, const glass_opts *opts, glass_stream_t stream);
+
 /* ------------------------------------------------------------ placement */
 
 /* The placement the library would use for (op, n, k, batch, dtype): the

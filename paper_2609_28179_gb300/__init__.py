@@ -80,6 +80,7 @@ _SIGS = {
     "glass_from_interleaved32": (_i, [_i, _i, _P, _P, _i, _P]),
     "glass_posv_varsize_workspace": (_sz, [_i]),
     "glass_posv_varsize": (_i, [_i, _P, _P, _P, _i, _P, _P, _P, _P, _sz, _OPTS, _P]),
+    "glass_posv_varsize_noalloc": (_i, [_i, _P, _P, _P, _i, _P, _P, _P, _OPTS, _P]),
     "glass_get_placement": (_i, [_i, _i, _i, _i, _i, _i, ctypes.POINTER(glass_placement)]),
     "glass_placement_feasible": (_i, [_i, _i, _i, glass_placement]),
     "glass_set_learned_model": (_i, [_P, _i, _P, _P]),
@@ -205,6 +206,13 @@ def glass_posv_varsize(batch, n_dev, offA_dev, offB_dev, nrhs, A, B, info, ws, w
                        stream=None):
     return lib().glass_posv_varsize(batch, _ptr(n_dev), _ptr(offA_dev), _ptr(offB_dev), nrhs, _ptr(A),
                                     _ptr(B), _ptr(info), _ptr(ws), ws_bytes, _opts(opts), _stream(stream))
+
+
+def glass_posv_varsize_noalloc(batch, n_dev, offA_dev, offB_dev, nrhs, A, B, info, opts=None, stream=None):
+    """Mixed-size solve with the library's built-in scratch (batch <= 65536),
+    for callers that cannot allocate device memory."""
+    return lib().glass_posv_varsize_noalloc(batch, _ptr(n_dev), _ptr(offA_dev), _ptr(offB_dev), nrhs, _ptr(A),
+                                            _ptr(B), _ptr(info), _opts(opts), _stream(stream))
 
 
 def glass_get_placement(op, n, k, batch, dtype=GLASS_F32, use_learned=0):
