@@ -71,6 +71,36 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Returns p unchanged but opaque to the optimiser, so that addresses formed
+// from it are not merged with earlier identical ones (an unrolled load loop
+// and store loop over the same n addresses would otherwise keep all n
+// pointers live across the whole computation).
+template <typename T>
+__device__ __forceinline__ T *opaque(T *p) {
+    asm volatile("" : "+l"(p));
+    return p;
+}
+
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only): every
+// thread can keep many copies in flight without holding registers.  Both
+// addresses must be 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// Shared-memory pitch (floats) of a column of n values read with 16-byte
+// loads, one column per thread: a multiple of 4 whose number of float4s is
+// odd, so 8 consecutive threads hit 8 distinct 16-byte bank groups.
+__host__ __device__ __forceinline__ int col_pitch(int n) {
+    int p = (n + 3) & ~3;
+    if (((p >> 2) & 1) == 0) p += 4;
+    return p;
+}
+
 // Odd per-problem stride in shared memory: problem t's element e sits at
 // t*S + e, so 32 threads reading the same e hit 32 distinct banks.
 __host__ __device__ __forceinline__ int odd_stride(int per) { return per | 1; }
@@ -99,6 +129,7 @@ __device__ __forceinline__ void stage_in(float *sm, int S, const Mat &M, int b0,
         if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
             const int nv = total >> 2;
             const float4 *g4 = reinterpret_cast<const float4 *>(g);
+#pragma unroll 4
             for (int v = threadIdx.x; v < nv; v += blockDim.x) {
                 float4 x = __ldcs(g4 + v);
                 int p, q;

@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(256) k_chol_thread(int n_rt, int nrhs, Mat A, 
         }
         if (has_rhs(OP)) {
             float *pb = sb + t * SB;
+            float *wb = opaque(pb);
             for (int c = 0; c < nrhs; ++c) {
                 float x[NMAX];
 #pragma unroll
@@ -98,13 +99,13 @@ __global__ void __launch_bounds__(256) k_chol_thread(int n_rt, int nrhs, Mat A, 
 #pragma unroll
                 for (int i = 0; i < NMAX; ++i)
                     if (i < n) {
-                        if (staged) pb[c * n + i] = x[i];
+                        if (staged) wb[c * n + i] = x[i];
                         else B.set(b, i, c, x[i]);
                     }
             }
         }
         if (has_factor(OP)) {
-            float *wa = sa + t * SA;
+            float *wa = opaque(sa + t * SA);
 #pragma unroll
             for (int j = 0; j < NMAX; ++j)
 #pragma unroll
@@ -210,45 +211,57 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
         }
     }
     if (has_factor(OP)) {
+        float *wa = opaque(A.p + (long long)b * A.s);
 #pragma unroll
         for (int k = 0; k < NMAX; ++k)
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int i = lane + 32 * q;
-                if (k < n && i < n && k <= i) A.cset(b, i, k, a[q][k]);
+                if (k < n && i < n && k <= i) wa[(long long)k * A.ld + i] = a[q][k];
             }
     }
 }
 
 // Solves with many right-hand sides (trsm; potrs when BOTH): a team of T
-// threads per problem, L (lower triangle) and B staged in shared memory
-// with coalesced loads, each thread solving whole columns of X in
-// registers with L read as 16-byte broadcasts.  Per problem in shared
-// memory: L (NMAX x NMAX, 16-byte aligned), 1/l_ii, B (ld = n | 1).
+// threads per problem, L (lower triangle) and B staged in shared memory,
+// each thread solving whole columns of X in registers with L read as
+// 16-byte broadcasts.  Packed, 16-byte aligned operands of order n % 4 == 0
+// are staged with cp.async 16-byte copies (only the chunks of L that hold
+// lower-triangle entries); anything else with plain loads.  Per problem in
+// shared memory: L (NMAX x NMAX), 1/l_ii, B (pitch col_pitch(n)).
 template <int NMAX, int T, bool BOTH>
-__global__ void __launch_bounds__(256) k_solve_cols(int n, int nrhs, Mat L, Mat B, int batch) {
+__global__ void __launch_bounds__(256, 1) k_solve_cols(int n, int nrhs, Mat L, Mat B, int batch) {
     extern __shared__ __align__(16) float smem[];
     const int team = threadIdx.x / T, rank = threadIdx.x % T;
     const int P = blockDim.x / T;
     const int b = blockIdx.x * P + team;
     const int bar = 1 + team;
-    const int ldb = n | 1;
-    const int per = NMAX * NMAX + NMAX + ((nrhs * ldb + 3) & ~3);
+    const int ldb = col_pitch(n);
+    const int per = NMAX * NMAX + NMAX + nrhs * ldb;
     float *Ls = smem + team * per;
     float *dv = Ls + NMAX * NMAX;
     float *Bs = dv + NMAX;
     if (b >= batch) return;
-    for (int e = rank; e < n * n; e += T) {
-        const int j = e / n, i = e - j * n;
-        if (i >= j) Ls[j * NMAX + i] = L.cget(b, i, j);
-    }
-    if (B.packed()) {
-        const float *g = B.p + (long long)b * B.s;
-        for (int e = rank; e < n * nrhs; e += T) {
-            const int c = e / n, i = e - c * n;
-            Bs[c * ldb + i] = __ldcs(g + e);
+    const float *gl = L.p + (long long)b * L.s;
+    const float *gb = B.p + (long long)b * B.s;
+    const bool vec = (n & 3) == 0 && L.ld == n && B.ld == n &&
+                     ((reinterpret_cast<uintptr_t>(gl) | reinterpret_cast<uintptr_t>(gb)) & 15) == 0;
+    if (vec) {
+        const int q4 = n >> 2;  // 16-byte chunks per column
+        for (int e = rank; e < n * q4; e += T) {
+            const int j = e / q4, q = e - j * q4;
+            if (4 * q + 3 >= j) cp_async16(Ls + j * NMAX + 4 * q, gl + j * n + 4 * q);
         }
+        for (int e = rank; e < nrhs * q4; e += T) {
+            const int c = e / q4, q = e - c * q4;
+            cp_async16(Bs + c * ldb + 4 * q, gb + c * n + 4 * q);
+        }
+        cp_async_wait_all();
     } else {
+        for (int e = rank; e < n * n; e += T) {
+            const int j = e / n, i = e - j * n;
+            if (i >= j) Ls[j * NMAX + i] = L.cget(b, i, j);
+        }
         for (int e = rank; e < n * nrhs; e += T) {
             const int c = e / n, i = e - c * n;
             Bs[c * ldb + i] = B.cget(b, i, c);
@@ -264,16 +277,18 @@ __global__ void __launch_bounds__(256) k_solve_cols(int n, int nrhs, Mat L, Mat 
         for (int i = 0; i < NMAX; ++i) x[i] = (i < n) ? xc[i] : 0.f;
         warp::forward_cols<NMAX>(Ls, dv, x, n);
         if (BOTH) warp::backward_t_cols<NMAX>(Ls, dv, x, n);
+        float *wc = opaque(xc);
 #pragma unroll
         for (int i = 0; i < NMAX; ++i)
-            if (i < n) xc[i] = x[i];
+            if (i < n) wc[i] = x[i];
     }
     team_sync<T>(bar);
-    if (B.packed()) {
-        float *g = B.p + (long long)b * B.s;
-        for (int e = rank; e < n * nrhs; e += T) {
-            const int c = e / n, i = e - c * n;
-            __stcs(g + e, Bs[c * ldb + i]);
+    float *wg = B.p + (long long)b * B.s;
+    if (vec) {
+        const int q4 = n >> 2;
+        for (int e = rank; e < nrhs * q4; e += T) {
+            const int c = e / q4, q = e - c * q4;
+            __stcs(reinterpret_cast<float4 *>(wg + c * n + 4 * q), *reinterpret_cast<const float4 *>(Bs + c * ldb + 4 * q));
         }
     } else {
         for (int e = rank; e < n * nrhs; e += T) {
@@ -340,15 +355,18 @@ __global__ void __launch_bounds__(256, 1) k_chol_rows(int n, int nrhs, Mat A, Ma
                 for (int c = 0; c < kRS; ++c) x[c] += r[c];
                 rows::bar(bid);  // xall reads done before a later pass rewrites it
             }
-            if (i < n)
+            if (i < n) {
+                float *wb = opaque(B.p + (long long)b * B.s);
 #pragma unroll
                 for (int c = 0; c < kRS; ++c)
-                    if (c0 + c < nrhs) B.cset(b, i, c0 + c, x[c]);
+                    if (c0 + c < nrhs) wb[(long long)(c0 + c) * B.ld + i] = x[c];
+            }
         }
     }
+    float *wa = opaque(A.p + (long long)b * A.s);
 #pragma unroll
     for (int k = 0; k < NMAX; ++k)
-        if (k < n && i < n && k <= i) A.cset(b, i, k, a[k]);
+        if (k < n && i < n && k <= i) wa[(long long)k * A.ld + i] = a[k];
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -396,7 +414,7 @@ cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *in
 // Shared memory of the column-per-thread solve kernel, per problem (bytes).
 inline size_t solve_cols_per(int n, int nrhs) {
     const int N = nmax_bucket(n);
-    return (size_t)(N * N + N + (((size_t)nrhs * (n | 1) + 3) & ~(size_t)3)) * 4;
+    return (size_t)(N * N + N + (size_t)nrhs * col_pitch(n)) * 4;
 }
 
 template <int NMAX, int T, bool BOTH>

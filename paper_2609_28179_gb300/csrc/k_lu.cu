@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(256) k_lu_thread(int n_rt, int nrhs, Mat A, in
         for (int j = 0; j < NMAX; ++j)
             if (j < n) ipiv[(long long)b * n + j] = piv[j];
         float *pb = sb + t * SB;
+        float *wb = opaque(pb);
         for (int c = 0; c < nrhs; ++c) {
             float x[NMAX];
 #pragma unroll
@@ -51,16 +52,17 @@ __global__ void __launch_bounds__(256) k_lu_thread(int n_rt, int nrhs, Mat A, in
 #pragma unroll
             for (int i = 0; i < NMAX; ++i)
                 if (i < n) {
-                    if (staged) pb[c * n + i] = x[i];
+                    if (staged) wb[c * n + i] = x[i];
                     else B.set(b, i, c, x[i]);
                 }
         }
+        float *wa = opaque(pa);
 #pragma unroll
         for (int j = 0; j < NMAX; ++j)
 #pragma unroll
             for (int i = 0; i < NMAX; ++i)
                 if (i < n && j < n) {
-                    if (staged) pa[j * n + i] = a[i][j];
+                    if (staged) wa[j * n + i] = a[i][j];
                     else A.set(b, i, j, a[i][j]);
                 }
     }
@@ -103,11 +105,12 @@ __global__ void __launch_bounds__(256, NMAX <= 32 ? 2 : 1) k_lu_warp(int n, int 
         for (int q = 0; q < R; ++q)
             if (lane + 32 * q < n) B.cset(b, pos[q], c, x[q]);
     }
+    float *wa = opaque(A.p + (long long)b * A.s);
 #pragma unroll
     for (int k = 0; k < NMAX; ++k)
 #pragma unroll
         for (int q = 0; q < R; ++q)
-            if (k < n && lane + 32 * q < n) A.cset(b, pos[q], k, a[q][k]);
+            if (k < n && lane + 32 * q < n) wa[(long long)k * A.ld + pos[q]] = a[q][k];
 }
 
 constexpr int kRS = 4;

@@ -90,12 +90,13 @@ __device__ __forceinline__ int warp_posv_one(float *A, float *B, int n, int nrhs
             if (i < n) __stcs(B + c * n + i, x[q]);
         }
     }
+    float *wa = opaque(A);
 #pragma unroll
     for (int k = 0; k < NMAX; ++k)
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int i = lane + 32 * q;
-            if (k < n && i < n && k <= i) __stcs(A + k * n + i, a[q][k]);
+            if (k < n && i < n && k <= i) __stcs(wa + k * n + i, a[q][k]);
         }
     return info;
 }
