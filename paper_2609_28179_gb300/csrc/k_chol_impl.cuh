@@ -13,6 +13,7 @@
 #pragma once
 #include "dev_chol.cuh"
 #include "dev_rows.cuh"
+#include "dev_chol_tc.cuh"
 
 namespace glass {
 namespace {
@@ -132,9 +133,11 @@ template <int OP, int NMAX, bool REFINE>
 __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_chol_warp(int n, int nrhs, Mat A, Mat B, int *info, int batch,
                                                    int fp64diag) {
     constexpr int R = warp::Rows<NMAX>::R;
+    constexpr int AP = NMAX + 1;  // odd pitch of the refinement copy of A
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31;
-    float *col = smem + (threadIdx.x >> 5) * NMAX;
+    float *col = smem + (threadIdx.x >> 5) * (NMAX + (REFINE ? NMAX * AP : 0));
+    float *As = col + NMAX;  // REFINE only: original A, element (i,k) at k*AP + i
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= batch) return;  // whole warp
     float a[R][NMAX];
@@ -145,6 +148,7 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
         for (int q = 0; q < R; ++q) {
             const int i = lane + 32 * q;
             a[q][k] = (k < n && i < n && k <= i) ? A.cget(b, i, k) : 0.f;
+            if (REFINE && k < n && i < n && k <= i) As[k * AP + i] = a[q][k];
         }
     if (has_factor(OP)) {
         const int inf = warp::potrf<NMAX>(a, rd, n, fp64diag != 0, col);
@@ -171,33 +175,38 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
             warp::forward<NMAX>(a, rd, x, n);
             if (OP != C_TRSM) warp::backward_t<NMAX>(a, rd, x, n);
             if (REFINE) {
-                // r_i = b_i - sum_k a_ik x_k in FP64; A is re-read from
-                // global memory (not yet overwritten: L is stored last).
-                double acc[R];
+                // r_i = b_i - sum_k a_ik x_k in FP64 from the original A kept
+                // in shared memory (lower triangle, odd pitch: conflict free).
+                // four independent partial sums per row hide the FP64 latency
+                double acc[R][4];
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     const int i = lane + 32 * q;
-                    acc[q] = (i < n) ? (double)B.cget(b, i, c) : 0.0;
+                    acc[q][0] = (i < n) ? (double)B.cget(b, i, c) : 0.0;
+                    acc[q][1] = acc[q][2] = acc[q][3] = 0.0;
                 }
-                for (int k = 0; k < n; ++k) {
-                    float xk = 0.f;
+#pragma unroll 4
+                for (int k = 0; k < NMAX; ++k) {
+                    if (k < n) {
+                        float xk = 0.f;
 #pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        const float v = __shfl_sync(GLASS_FULL_MASK, x[q], k & 31);
-                        if ((k >> 5) == q) xk = v;
-                    }
+                        for (int q = 0; q < R; ++q) {
+                            const float v = __shfl_sync(GLASS_FULL_MASK, x[q], k & 31);
+                            if ((k >> 5) == q) xk = v;
+                        }
 #pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        const int i = lane + 32 * q;
-                        if (i < n) {
-                            const float aik = (k <= i) ? A.cget(b, i, k) : A.cget(b, k, i);
-                            acc[q] = fma(-(double)aik, (double)xk, acc[q]);
+                        for (int q = 0; q < R; ++q) {
+                            const int i = lane + 32 * q;
+                            if (i < n) {
+                                const float aik = (k <= i) ? As[k * AP + i] : As[i * AP + k];
+                                acc[q][k & 3] = fma(-(double)aik, (double)xk, acc[q][k & 3]);
+                            }
                         }
                     }
                 }
                 float r[R];
 #pragma unroll
-                for (int q = 0; q < R; ++q) r[q] = (float)acc[q];
+                for (int q = 0; q < R; ++q) r[q] = (float)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]));
                 warp::forward<NMAX>(a, rd, r, n);
                 warp::backward_t<NMAX>(a, rd, r, n);
 #pragma unroll
@@ -220,6 +229,56 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
                 if (k < n && i < n && k <= i) wa[(long long)k * A.ld + i] = a[q][k];
             }
     }
+}
+
+// Warp scope, orders 17..64, no refinement: blocked Cholesky with
+// tensor-core trailing updates (dev_chol_tc.cuh) on the problem held in the
+// warp's shared memory; the solves run against L in shared memory.
+template <int OP, int NMAX>
+__global__ void __launch_bounds__(256, 1) k_chol_tc(int n, int nrhs, Mat A, Mat B, int *info, int batch, int fp64diag) {
+    constexpr int LD = tcwarp::Shape<NMAX>::LD;
+    constexpr int R = tcwarp::Shape<NMAX>::R;
+    extern __shared__ __align__(16) float smem[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *As = smem + w * (NMAX * LD + NMAX);
+    float *dv = As + NMAX * LD;
+    const int b = blockIdx.x * (blockDim.x >> 5) + w;
+    if (b >= batch) return;  // whole warp
+    const float *ga = A.p + (long long)b * A.s;
+#pragma unroll 8
+    for (int k = 0; k < NMAX; ++k)
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = lane + 32 * q;
+            As[k * LD + i] = (k < n && i < n && i >= k) ? ga[(long long)k * A.ld + i] : 0.f;
+        }
+    __syncwarp();
+    const int inf = tcwarp::potrf<NMAX>(As, n, dv, fp64diag != 0);
+    if (lane == 0) info[b] = inf;
+    if (has_rhs(OP)) {
+        for (int c = 0; c < nrhs; ++c) {
+            float x[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = lane + 32 * q;
+                x[q] = (i < n) ? B.cget(b, i, c) : 0.f;
+            }
+            tcwarp::potrs<NMAX>(As, dv, x, n);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = lane + 32 * q;
+                if (i < n) B.cset(b, i, c, x[q]);
+            }
+        }
+    }
+    float *wa = opaque(A.p + (long long)b * A.s);
+#pragma unroll 8
+    for (int k = 0; k < NMAX; ++k)
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = lane + 32 * q;
+            if (k < n && i < n && i >= k) wa[(long long)k * A.ld + i] = As[k * LD + i];
+        }
 }
 
 // Solves with many right-hand sides (trsm; potrs when BOTH): a team of T
@@ -271,16 +330,24 @@ __global__ void __launch_bounds__(256, 1) k_solve_cols(int n, int nrhs, Mat L, M
     for (int i = rank; i < n; i += T) dv[i] = 1.0f / Ls[i * NMAX + i];
     team_sync<T>(bar);
     for (int c = rank; c < nrhs; c += T) {
+        // the column is read and written as 16-byte vectors: with the
+        // col_pitch stride, 8 consecutive threads touch 8 distinct bank groups
         float x[NMAX];
-        float *xc = Bs + c * ldb;
+        const float4 *xc4 = reinterpret_cast<const float4 *>(Bs + c * ldb);
 #pragma unroll
-        for (int i = 0; i < NMAX; ++i) x[i] = (i < n) ? xc[i] : 0.f;
-        warp::forward_cols<NMAX>(Ls, dv, x, n);
-        if (BOTH) warp::backward_t_cols<NMAX>(Ls, dv, x, n);
-        float *wc = opaque(xc);
+        for (int i4 = 0; i4 < NMAX / 4; ++i4) {
+            const float4 v = 4 * i4 < n ? xc4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[4 * i4] = v.x; x[4 * i4 + 1] = v.y; x[4 * i4 + 2] = v.z; x[4 * i4 + 3] = v.w;
+        }
 #pragma unroll
         for (int i = 0; i < NMAX; ++i)
-            if (i < n) wc[i] = x[i];
+            if (i >= n) x[i] = 0.f;
+        warp::forward_cols<NMAX>(Ls, dv, x, n);
+        if (BOTH) warp::backward_t_cols<NMAX>(Ls, dv, x, n);
+        float4 *wc4 = reinterpret_cast<float4 *>(opaque(Bs + c * ldb));
+#pragma unroll
+        for (int i4 = 0; i4 < NMAX / 4; ++i4)
+            if (4 * i4 < n) wc4[i4] = make_float4(x[4 * i4], x[4 * i4 + 1], x[4 * i4 + 2], x[4 * i4 + 3]);
     }
     team_sync<T>(bar);
     float *wg = B.p + (long long)b * B.s;
@@ -303,14 +370,14 @@ __global__ void __launch_bounds__(256, 1) k_solve_cols(int n, int nrhs, Mat L, M
 // right-hand sides handled RS = 4 at a time.  The refinement residual
 // r = b - A x0 is formed in FP64 from A re-read in global memory (L is
 // written back last) and the solved x broadcast through shared memory.
-constexpr int kRS = 4;
+constexpr int kRSmax = 4;
 
 template <int NMAX>
 constexpr int rows_team_floats() {
-    return ((rows::Scratch<NMAX, kRS>::floats + NMAX * kRS + 3) / 4) * 4;
+    return ((rows::Scratch<NMAX, kRSmax>::floats + NMAX * kRSmax + 3) / 4) * 4;
 }
 
-template <int OP, int NMAX, bool REFINE>
+template <int OP, int NMAX, bool REFINE, int kRS>
 __global__ void __launch_bounds__(256, 1) k_chol_rows(int n, int nrhs, Mat A, Mat B, int *info, int batch,
                                                    int fp64diag) {
     extern __shared__ __align__(16) float smem[];
@@ -319,7 +386,7 @@ __global__ void __launch_bounds__(256, 1) k_chol_rows(int n, int nrhs, Mat A, Ma
     const int bid = 1 + team;
     float *base = smem + team * rows_team_floats<NMAX>();
     rows::Scratch<NMAX, kRS> s(base);
-    float *xall = base + rows::Scratch<NMAX, kRS>::floats;  // [NMAX][kRS]
+    float *xall = base + rows::Scratch<NMAX, kRSmax>::floats;  // [NMAX][kRS]
     if (b >= batch) return;  // the whole team leaves together
     float a[NMAX];
 #pragma unroll
@@ -411,6 +478,12 @@ cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *in
 #undef GL_T
 }
 
+// Shared memory of the blocked tensor-core Cholesky, per warp (bytes).
+inline size_t tc_smem(int n) {
+    const int N = n <= 32 ? 32 : 64;
+    return (size_t)(N * (N + 8) + N) * 4;
+}
+
 // Shared memory of the column-per-thread solve kernel, per problem (bytes).
 inline size_t solve_cols_per(int n, int nrhs) {
     const int N = nmax_bucket(n);
@@ -443,10 +516,20 @@ cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info
     if constexpr (OP == C_TRSM) {
         return solve_cols_dispatch<32, false>(n, nrhs, A, B, batch, pack, st);
     } else {
+        if constexpr (has_factor(OP) && !RF) {
+            if (n > 16) {
+                const int grid = ceil_div(batch, pack);
+                if (n <= 32)
+                    return launch_k(k_chol_tc<OP, 32>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info,
+                                    batch, fp64diag);
+                return launch_k(k_chol_tc<OP, 64>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info, batch,
+                                fp64diag);
+            }
+        }
         const int threads = 32 * pack;
         const int grid = ceil_div(batch, pack);
         const int N = nmax_bucket(n);
-        const size_t sm = (size_t)pack * N * 4;
+        const size_t sm = (size_t)pack * (N + (RF ? N * (N + 1) : 0)) * 4;
 #define GL_W(NN) launch_k(k_chol_warp<OP, NN, RF>, grid, threads, sm, st, n, nrhs, A, B, info, batch, fp64diag)
         switch (N) {
             case 8: return GL_W(8);
@@ -478,7 +561,8 @@ cudaError_t block_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *inf
         const size_t smem = rows_team_bytes(n) * pack;
         const int grid = ceil_div(batch, pack);
         const int th = rows::T * pack;
-#define GL_R(NN) launch_k(k_chol_rows<OP, NN, RF>, grid, th, smem, st, n, nrhs, A, B, info, batch, fp64diag)
+#define GL_R(NN) (nrhs <= 1 ? launch_k(k_chol_rows<OP, NN, RF, 1>, grid, th, smem, st, n, nrhs, A, B, info, batch, fp64diag) \
+                         : launch_k(k_chol_rows<OP, NN, RF, 4>, grid, th, smem, st, n, nrhs, A, B, info, batch, fp64diag))
         switch (nmax_bucket(n)) {
             case 8: return GL_R(8);
             case 16: return GL_R(16);
@@ -494,9 +578,12 @@ size_t smem_of(int n, int nrhs, Placement pl, int refine) {
     switch (pl.scope) {
         case SCOPE_THREAD:
             return (size_t)32 * pl.pack * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4;
-        case SCOPE_WARP:
+        case SCOPE_WARP: {
             if (OP == C_TRSM) return solve_cols_per(n, nrhs) * pl.pack;
-            return (size_t)pl.pack * nmax_bucket(n) * 4;
+            if (has_factor(OP) && !refine && n > 16) return tc_smem(n) * pl.pack;
+            const int N = nmax_bucket(n);
+            return (size_t)pl.pack * (N + (refine ? N * (N + 1) : 0)) * 4;
+        }
         default:
             if (OP == C_TRSM || OP == C_POTRS) return solve_cols_per(n, nrhs) * pl.pack;
             return rows_team_bytes(n) * pl.pack;

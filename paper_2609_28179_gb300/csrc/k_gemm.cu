@@ -164,6 +164,75 @@ __global__ void __launch_bounds__(256) k_gemm_team(int m, int n, int k, Mat A, M
     }
 }
 
+// Block scope, n a multiple of 4, packed 16-byte aligned operands: A and B
+// staged column-major (pitch NMAX + 4) with cp.async 16-byte copies; the
+// inner loop takes four k at a time so each B fragment is one 16-byte read
+// of a column of B.  Lanes are laid out row-group fastest: the 8 lanes of
+// a quarter-warp share their B columns (broadcast) and read 8 consecutive
+// 16-byte A fragments (no bank conflict).  C goes back through shared
+// memory for coalesced 16-byte stores.
+template <int NMAX, int T>
+__global__ void __launch_bounds__(T) k_gemm_async(int n, Mat A, Mat B, Mat C, int batch) {
+    constexpr int TM = 4, TN = 4;
+    constexpr int RG = NMAX / TM, CG = NMAX / TN;
+    static_assert(RG * CG == T, "tile does not cover the product");
+    constexpr int LD = NMAX + 4;
+    extern __shared__ __align__(16) float smem[];
+    float *As = smem, *Bs = smem + NMAX * LD;
+    const int b = blockIdx.x;
+    const int rank = threadIdx.x;
+    const int q4 = n >> 2;
+    const float *ga = A.p + (long long)b * A.s, *gb = B.p + (long long)b * B.s;
+    for (int e = rank; e < n * q4; e += T) {
+        const int c = e / q4, q = e - c * q4;
+        cp_async16(As + c * LD + 4 * q, ga + c * n + 4 * q);
+        cp_async16(Bs + c * LD + 4 * q, gb + c * n + 4 * q);
+    }
+    // zero padding when n < NMAX
+    for (int e = rank; e < NMAX * NMAX; e += T) {
+        const int c = e / NMAX, r = e - c * NMAX;
+        if (r >= n || c >= n) { As[c * LD + r] = 0.f; Bs[c * LD + r] = 0.f; }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int rg = rank % RG, cg = rank / RG;
+    const int i0 = rg * TM, j0 = cg * TN;
+    float acc[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = 0.f;
+#pragma unroll 2
+    for (int l = 0; l < NMAX; l += 4) {
+        float bq[TN][4];
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const float4 v = *reinterpret_cast<const float4 *>(Bs + (j0 + c) * LD + l);
+            bq[c][0] = v.x; bq[c][1] = v.y; bq[c][2] = v.z; bq[c][3] = v.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 a = *reinterpret_cast<const float4 *>(As + (l + u) * LD + i0);
+            const float af[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int r = 0; r < TM; ++r)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) acc[r][c] = fmaf(af[r], bq[c][u], acc[r][c]);
+        }
+    }
+    __syncthreads();
+    float *Cs = As;
+#pragma unroll
+    for (int c = 0; c < TN; ++c)
+        *reinterpret_cast<float4 *>(Cs + (j0 + c) * LD + i0) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+    __syncthreads();
+    float *gc = C.p + (long long)b * C.s;
+    for (int e = rank; e < n * q4; e += T) {
+        const int c = e / q4, q = e - c * q4;
+        __stcs(reinterpret_cast<float4 *>(gc + c * n + 4 * q), *reinterpret_cast<const float4 *>(Cs + c * LD + 4 * q));
+    }
+}
+
 template <typename K>
 cudaError_t go(K kern, int grid, int threads, size_t smem, cudaStream_t st, int m, int n, int k, const Mat &A,
                const Mat &B, const Mat &C, int batch) {
@@ -225,6 +294,22 @@ cudaError_t launch_gemm(int m, int n, int k, Mat A, Mat B, Mat C, int batch, Pla
         if (N <= 4 && m <= 4 && n <= 4 && k <= 4)
             return go(k_gemm_thread<4, false>, grid, G, sm, st, m, n, k, A, B, C, batch);
         return go(k_gemm_thread<8, false>, grid, G, sm, st, m, n, k, A, B, C, batch);
+    }
+    const bool async_ok = pl.scope == SCOPE_BLOCK && pl.pack == 1 && m == n && n == k && (n & 3) == 0 && N >= 32 &&
+                          A.packed() && B.packed() && C.packed() &&
+                          ((reinterpret_cast<uintptr_t>(A.p) | reinterpret_cast<uintptr_t>(B.p) |
+                            reinterpret_cast<uintptr_t>(C.p)) & 15) == 0;
+    if (async_ok) {
+        const size_t sm = (size_t)2 * N * (N + 4) * 4;
+        cudaError_t e;
+        if (N == 32) {
+            if ((e = prepare(k_gemm_async<32, 64>, sm)) != cudaSuccess) return e;
+            k_gemm_async<32, 64><<<batch, 64, sm, st>>>(n, A, B, C, batch);
+        } else {
+            if ((e = prepare(k_gemm_async<64, 256>, sm)) != cudaSuccess) return e;
+            k_gemm_async<64, 256><<<batch, 256, sm, st>>>(n, A, B, C, batch);
+        }
+        return cudaPeekAtLastError();
     }
     const int T = team_of(pl.scope, N);
     const int grid = ceil_div(batch, pl.pack);

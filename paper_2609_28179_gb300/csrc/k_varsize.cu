@@ -4,13 +4,16 @@
 //
 // 1. k_varsize_bin (one CTA): histogram of the orders, a descending scan
 //    (largest orders first: longest-processing-time order, so the tail of
-//    the launch is made of the cheapest instances), and the scatter of the
-//    instance indices into `order`.  Instances with an order outside
-//    [1, 64] get info = -1 and are left out.  The ticket is reset here.
-// 2. k_varsize_posv (persistent, grid = resident CTAs): every warp takes the
-//    next ticket with one atomic, solves instance order[ticket] with the
-//    warp primitive of the bucket its order falls in, and repeats.  No CTA
-//    ever waits on another.
+//    each launch is made of its cheapest instances), the scatter of the
+//    instance indices into `order`, and the ranges of the four order
+//    buckets (33..64, 17..32, 9..16, 1..8).  Instances with an order outside
+//    [1, 64] get info = -1 and are left out.  The tickets are reset here.
+// 2. k_varsize_posv<NMAX> (persistent, one launch per bucket, largest
+//    first, grid = resident CTAs of that instantiation): every warp takes
+//    the next ticket of its bucket with one atomic, solves instance
+//    order[start + ticket] with the warp primitive specialised for the
+//    bucket, and repeats.  One instantiation per bucket keeps each launch at
+//    the register count of its own order.  No CTA ever waits on another.
 //
 // Everything the launch needs lives in the caller's workspace, so the pair
 // of kernels can be recorded in a CUDA graph and replayed.
@@ -20,13 +23,18 @@ namespace glass {
 namespace {
 
 struct VarWs {
-    int ticket;
+    int ticket[4];   // per bucket
+    int bstart[4];   // bucket ranges in order[]
+    int bcount[4];
     int valid;
-    int pad[62];
+    int pad[51];
     int count[65];
     int start[65];
     // followed by int order[batch]
 };
+
+// Bucket of an order: 0 -> 33..64, 1 -> 17..32, 2 -> 9..16, 3 -> 1..8.
+__host__ __device__ __forceinline__ int bucket_of(int n) { return n > 32 ? 0 : n > 16 ? 1 : n > 8 ? 2 : 3; }
 
 __global__ void __launch_bounds__(1024) k_varsize_bin(int batch, const int *__restrict__ n_dev, int *__restrict__ info,
                                                       VarWs *ws) {
@@ -50,7 +58,15 @@ __global__ void __launch_bounds__(1024) k_varsize_bin(int batch, const int *__re
             s += cnt[n];
         }
         ws->valid = s;
-        ws->ticket = 0;
+        for (int q = 0; q < 4; ++q) {
+            const int hi = q == 0 ? 64 : q == 1 ? 32 : q == 2 ? 16 : 8;
+            const int lo = q == 0 ? 33 : q == 1 ? 17 : q == 2 ? 9 : 1;
+            int c = 0;
+            for (int n = lo; n <= hi; ++n) c += cnt[n];
+            ws->bstart[q] = cur[hi];
+            ws->bcount[q] = c;
+            ws->ticket[q] = 0;
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < batch; i += blockDim.x) {
@@ -101,30 +117,60 @@ __device__ __forceinline__ int warp_posv_one(float *A, float *B, int n, int nrhs
     return info;
 }
 
+template <int NMAX>
 __global__ void __launch_bounds__(256) k_varsize_posv(const int *__restrict__ n_dev, const long long *__restrict__ offA,
                                                       const long long *__restrict__ offB, int nrhs, float *A, float *B,
-                                                      int *__restrict__ info, VarWs *ws) {
+                                                      int *__restrict__ info, VarWs *ws, int bucket) {
     extern __shared__ __align__(16) float vsm[];
     const int lane = threadIdx.x & 31;
-    float *col = vsm + (threadIdx.x >> 5) * 64;
+    float *col = vsm + (threadIdx.x >> 5) * NMAX;
     const int *order = reinterpret_cast<const int *>(ws + 1);
-    const int valid = ws->valid;
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(&ws->ticket, 1);
-        t = __shfl_sync(GLASS_FULL_MASK, t, 0);
-        if (t >= valid) break;
-        const int i = order[t];
-        const int n = n_dev[i];
-        float *a = A + offA[i];
-        float *b = B + offB[i];
-        int inf;
-        if (n <= 8) inf = warp_posv_one<8>(a, b, n, nrhs, col);
-        else if (n <= 16) inf = warp_posv_one<16>(a, b, n, nrhs, col);
-        else if (n <= 32) inf = warp_posv_one<32>(a, b, n, nrhs, col);
-        else inf = warp_posv_one<64>(a, b, n, nrhs, col);
+    const int start = ws->bstart[bucket], count = ws->bcount[bucket];
+    // software pipeline: lane 0 takes the next ticket and fetches that
+    // instance's metadata before the current instance is solved; the warp
+    // reads them (shuffles) only afterwards, so their latency overlaps it
+    int t = 0;
+    if (lane == 0) t = atomicAdd(&ws->ticket[bucket], 1);
+    t = __shfl_sync(GLASS_FULL_MASK, t, 0);
+    int i = t < count ? order[start + t] : 0;
+    int n = t < count ? n_dev[i] : 0;
+    long long oa = t < count ? offA[i] : 0, ob = t < count ? offB[i] : 0;
+    while (t < count) {
+        int t2 = count, i2 = 0, n2 = 0;
+        long long oa2 = 0, ob2 = 0;
+        if (lane == 0) {
+            t2 = atomicAdd(&ws->ticket[bucket], 1);
+            if (t2 < count) {
+                i2 = order[start + t2];
+                n2 = n_dev[i2];
+                oa2 = offA[i2];
+                ob2 = offB[i2];
+            }
+        }
+        const int inf = warp_posv_one<NMAX>(A + oa, B + ob, n, nrhs, col);
         if (lane == 0) info[i] = inf;
+        t = __shfl_sync(GLASS_FULL_MASK, t2, 0);
+        i = __shfl_sync(GLASS_FULL_MASK, i2, 0);
+        n = __shfl_sync(GLASS_FULL_MASK, n2, 0);
+        oa = __shfl_sync(GLASS_FULL_MASK, oa2, 0);
+        ob = __shfl_sync(GLASS_FULL_MASK, ob2, 0);
     }
+}
+
+template <int NMAX>
+cudaError_t launch_bucket(int batch, const int *n_dev, const long long *offA, const long long *offB, int nrhs, float *A,
+                          float *B, int *info, VarWs *w, int warps_per_cta, int bucket, int sms, cudaStream_t st) {
+    const int threads = 32 * warps_per_cta;
+    const size_t sm = (size_t)warps_per_cta * NMAX * 4;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_varsize_posv<NMAX>, threads, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const long long want = (long long)sms * per_sm;
+    const long long need = ((long long)batch + warps_per_cta - 1) / warps_per_cta;
+    const int grid = (int)(want < need ? want : need);
+    k_varsize_posv<NMAX><<<grid, threads, sm, st>>>(n_dev, offA, offB, nrhs, A, B, info, w, bucket);
+    return cudaPeekAtLastError();
 }
 
 }  // namespace
@@ -142,19 +188,16 @@ cudaError_t launch_posv_varsize(int batch, const int *n_dev, const long long *of
     k_varsize_bin<<<1, 1024, 0, st>>>(batch, n_dev, info, w);
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int threads = 32 * warps_per_cta;
-    const size_t sm = (size_t)warps_per_cta * 64 * 4;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_varsize_posv, threads, sm)) != cudaSuccess)
+    if ((e = launch_bucket<64>(batch, n_dev, offA, offB, nrhs, A, B, info, w, warps_per_cta, 0, sms, st)) != cudaSuccess)
         return e;
-    if (per_sm < 1) per_sm = 1;
-    const long long want = (long long)sms * per_sm;
-    const long long need = ((long long)batch + warps_per_cta - 1) / warps_per_cta;
-    const int grid = (int)(want < need ? want : need);
-    k_varsize_posv<<<grid, threads, sm, st>>>(n_dev, offA, offB, nrhs, A, B, info, w);
-    return cudaPeekAtLastError();
+    if ((e = launch_bucket<32>(batch, n_dev, offA, offB, nrhs, A, B, info, w, warps_per_cta, 1, sms, st)) != cudaSuccess)
+        return e;
+    if ((e = launch_bucket<16>(batch, n_dev, offA, offB, nrhs, A, B, info, w, warps_per_cta, 2, sms, st)) != cudaSuccess)
+        return e;
+    return launch_bucket<8>(batch, n_dev, offA, offB, nrhs, A, B, info, w, warps_per_cta, 3, sms, st);
 }
 
 }  // namespace glass
