@@ -81,6 +81,14 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         os.replace(tmp, LIB)
         with open(stamp, "w") as f:
             f.write(want)
+    # drop objects of earlier source versions
+    keep = set(objs)
+    for stale in glob.glob(os.path.join(BUILD, "*.o")):
+        if stale not in keep:
+            try:
+                os.remove(stale)
+            except OSError:
+                pass
     if verbose:
         for s, log in sorted(logs.items()):
             sys.stderr.write(f"== {os.path.basename(s)}\n{log}")

@@ -19,6 +19,8 @@ Usage (on the GPU):
   python -m paper_2609_28179_gb300.tune sweep   [--out FILE]   # placement grid
   python -m paper_2609_28179_gb300.tune random  --count N --seed S --out FILE
   python -m paper_2609_28179_gb300.tune codegen [--inp FILE]   # -> csrc/placement_table.h
+  python -m paper_2609_28179_gb300.tune launch  --cells op:n:batch[:scope:pack] ...
+      (one launch of each cell, for profilers; default placement = the table's)
 """
 from __future__ import annotations
 
@@ -215,9 +217,28 @@ static const unsigned char kTable[{len(OPS)}][{len(SWEEP_N)}][{len(SWEEP_B)}] = 
     return out
 
 
+def launch_cells(specs):
+    """One launch of each cell 'op:n:batch[:scope:pack]' (device inputs)."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300.cells import Cell
+    g.lib()
+    for spec in specs:
+        parts = spec.split(":")
+        op, n, batch = parts[0], int(parts[1]), int(parts[2])
+        scope, pack = (int(parts[3]), int(parts[4])) if len(parts) == 5 else (g.GLASS_SCOPE_AUTO, 0)
+        cell = Cell(op, n, batch, sets=1, device_inputs=True)
+        g.check(cell.launch(0, scope, pack), spec)
+        torch.cuda.synchronize()
+        del cell
+        torch.cuda.empty_cache()
+        print("launched", spec, flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["sweep", "random", "codegen"])
+    ap.add_argument("cmd", choices=["sweep", "random", "codegen", "launch"])
+    ap.add_argument("--cells", nargs="+", default=[])
     ap.add_argument("--out", default=None)
     ap.add_argument("--inp", default=GRID_FILE)
     ap.add_argument("--count", type=int, default=5000)
@@ -228,6 +249,8 @@ def main():
         sweep(args.out or GRID_FILE, ops=args.ops)
     elif args.cmd == "random":
         random_points(args.out or os.path.join(TUNING, f"sm103_random_{args.seed}.jsonl"), args.count, args.seed)
+    elif args.cmd == "launch":
+        launch_cells(args.cells)
     else:
         print(codegen(args.inp))
 
