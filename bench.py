@@ -288,6 +288,23 @@ def config_of(args, sample_note=None):
     return c
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The job's time is the slowest replica's (replicas share no data; the
+    only collective is this reduction, outside the timed region)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(problems_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Whole-job matrices/s: every rank's problems over the slowest rank's time."""
+    return problems_per_rank * world * steps / (ms_max / 1e3)
+
+
 def kernel_hash():
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2609_28179_gb300", "csrc")
@@ -604,19 +621,12 @@ def main():
     if not args.no_e2e:
         t_e2e, h2d, d2h = e2e_steps(cells, args.steps, args.warmup)
 
-    def maxr(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    t_tuned, t_plain = maxr(t_tuned), maxr(t_plain)
+    t_tuned, t_plain = max_over_ranks(t_tuned, world), max_over_ranks(t_plain, world)
     if t_e2e is not None:
-        t_e2e = maxr(t_e2e)
+        t_e2e = max_over_ranks(t_e2e, world)
     problems = len(cells) * args.batch * world
     ms_step = t_tuned / args.steps
-    value = problems * args.steps / (t_tuned / 1e3)
+    value = replica_value(len(cells) * args.batch, world, args.steps, t_tuned)
 
     peaks = load_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count

@@ -1,5 +1,5 @@
 // dev_chol_tc.cuh -- warp-scope blocked Cholesky with tensor-core trailing
-// updates, for orders 17..64.
+// updates, for orders 33..64 (below that the register form is faster).
 //
 // One warp owns one problem held in its shared memory, column-major with
 // pitch LD = NMAX + 8 (LD = 8 mod 32: every TF32 fragment load of the MMA

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
     }
 }
 
-// Warp scope, orders 17..64, no refinement: blocked Cholesky with
+// Warp scope, orders 33..64, no refinement: blocked Cholesky with
 // tensor-core trailing updates (dev_chol_tc.cuh) on the problem held in the
 // warp's shared memory; the solves run against L in shared memory.
 template <int OP, int NMAX>
@@ -517,11 +517,8 @@ cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info
         return solve_cols_dispatch<32, false>(n, nrhs, A, B, batch, pack, st);
     } else {
         if constexpr (has_factor(OP) && !RF) {
-            if (n > 16) {
+            if (n > 32) {
                 const int grid = ceil_div(batch, pack);
-                if (n <= 32)
-                    return launch_k(k_chol_tc<OP, 32>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info,
-                                    batch, fp64diag);
                 return launch_k(k_chol_tc<OP, 64>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info, batch,
                                 fp64diag);
             }
@@ -580,7 +577,7 @@ size_t smem_of(int n, int nrhs, Placement pl, int refine) {
             return (size_t)32 * pl.pack * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4;
         case SCOPE_WARP: {
             if (OP == C_TRSM) return solve_cols_per(n, nrhs) * pl.pack;
-            if (has_factor(OP) && !refine && n > 16) return tc_smem(n) * pl.pack;
+            if (has_factor(OP) && !refine && n > 32) return tc_smem(n) * pl.pack;
             const int N = nmax_bucket(n);
             return (size_t)pl.pack * (N + (refine ? N * (N + 1) : 0)) * 4;
         }

@@ -1,0 +1,50 @@
+"""Multi-GPU runs are replicas (independent problems, no data-path
+collective): the job time is the slowest rank's, reduced once with a max
+outside the timed region.  Checked here with two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t = bench.max_over_ranks(10.0 + 5.0 * rank, world, device="cpu")   # ms of this rank
+    v = bench.replica_value(1000, world, 4, t)
+    q.put((rank, t, v))
+    dist.destroy_process_group()
+
+
+@pytest.mark.timeout(120)
+def test_max_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=100) for _ in range(2))
+    for p in procs:
+        p.join(timeout=30)
+        assert p.exitcode == 0
+    assert [t for _, t, _ in out] == [15.0, 15.0]            # slowest rank's time on every rank
+    assert out[0][2] == pytest.approx(1000 * 2 * 4 / 0.015)  # all ranks' problems / that time
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+    assert bench.replica_value(10, 1, 2, 1.0) == pytest.approx(20000.0)
