@@ -63,6 +63,10 @@ def _load():
             "oracle_getrs_f64": (None, [_int, _int, _D, _int, _ll, _I, _D, _int, _ll, _int]),
             "oracle_getrf_getrs_f64": (None, [_int, _int, _D, _int, _ll, _I, _D, _int, _ll,
                                               _I, _int]),
+            "oracle_gemm_ex_f64": (None, [_int, _int, _int, _int, _int, ctypes.c_double, _D, _int, _ll, _D, _int,
+                                          _ll, ctypes.c_double, _D, _int, _ll, _int]),
+            "oracle_riccati_gain_f64": (None, [_int, _int, _D, _ll, _D, _ll, _D, _ll, _D, _ll, _D, _ll, _I,
+                                               _int]),
             "oracle_rot3_compose_f64": (None, [_int, _D, _ll, _D, _ll, _int]),
             "oracle_se3_apply_f64": (None, [_int, _D, _ll, _int, _D, _ll, _D, _ll, _int]),
             "oracle_mlp_nparams": (_ll, [_int, _int, _int]),
@@ -205,6 +209,30 @@ def getrf_getrs(n, nrhs, A, B, batch, lda=None, sA=None, ldb=None, sB=None):
     _load().oracle_getrf_getrs_f64(n, nrhs, _dp(LU), lda, sA, _ip(ipiv), _dp(X), ldb, sB,
                                    _ip(info), batch)
     return LU, ipiv[:batch * n], X, info[:batch]
+
+
+def gemm_ex(ta, tb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch):
+    """C = alpha op(A) op(B) + beta C (returns the new C; C may be None when beta == 0)."""
+    A, B = _f64(A), _f64(B)
+    C = np.zeros(max(1, sC * batch), dtype=np.float64) if C is None else _f64(C)
+    _load().oracle_gemm_ex_f64(int(bool(ta)), int(bool(tb)), m, n, k, float(alpha), _dp(A), lda, sA, _dp(B), ldb,
+                               sB, float(beta), _dp(C), ldc, sC, batch)
+    return C
+
+
+def riccati_gain(nx, nu, A, B, P, R, batch, sA=None, sB=None, sP=None, sR=None, sK=None):
+    """K = (R + B^T P B)^{-1} B^T P A per problem; returns (K, info)."""
+    sA = nx * nx if sA is None else sA
+    sB = nx * nu if sB is None else sB
+    sP = nx * nx if sP is None else sP
+    sR = nu * nu if sR is None else sR
+    sK = nu * nx if sK is None else sK
+    A, B, P, R = _f64(A), _f64(B), _f64(P), _f64(R)
+    K = np.zeros(max(1, sK * batch), dtype=np.float64)
+    info = np.zeros(max(1, batch), dtype=np.int32)
+    _load().oracle_riccati_gain_f64(nx, nu, _dp(A), sA, _dp(B), sB, _dp(P), sP, _dp(R), sR, _dp(K), sK, _ip(info),
+                                    batch)
+    return K, info[:batch]
 
 
 def rot3_compose(chain, Rs, batch, sRs=None, sR=9):

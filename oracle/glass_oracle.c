@@ -299,6 +299,92 @@ void oracle_getrf_getrs_f64(int n, int nrhs, double *A, int lda, long long sA,
 }
 
 /* ------------------------------------------------------------------------ */
+/* GEMM with operand transposes and scaling (Sec. III-B "BLAS L1-L3"; the     */
+/* BLAS xGEMM definition):  C = alpha op(A) op(B) + beta C, op(X) = X or X^T, */
+/* C m x n, op(A) m x k, op(B) k x n.  With beta == 0, C is not read.         */
+/* ------------------------------------------------------------------------ */
+void oracle_gemm_ex_f64(int ta, int tb, int m, int n, int k, double alpha,
+                        const double *A, int lda, long long sA,
+                        const double *B, int ldb, long long sB, double beta,
+                        double *C, int ldc, long long sC, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *a = A + (long long)b * sA;
+        const double *bb = B + (long long)b * sB;
+        double *c = C + (long long)b * sC;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < k; ++l) {
+                    const double x = ta ? a[i * lda + l] : a[l * lda + i];
+                    const double y = tb ? bb[l * ldb + j] : bb[j * ldb + l];
+                    s += x * y;
+                }
+                c[j * ldc + i] = beta == 0.0 ? alpha * s : alpha * s + beta * c[j * ldc + i];
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* LQR feedback gain (Sec. III-B fused operations; Sec. IV-E):               */
+/*   K = (R + B^T P B)^{-1} B^T P A                                          */
+/* A nx x nx, B nx x nu, P nx x nx, R nu x nu, K nu x nx, each packed        */
+/* column-major (leading dimension = rows) with its own batch stride.  The    */
+/* steps follow the formula: PB = P B; S = R + B^T PB; PA = P A;              */
+/* M = B^T PA; S = L L^T (POTRF, info); K = L^{-T} L^{-1} M (POTRS over the   */
+/* nx columns of M).  K is unspecified where info != 0.                       */
+/* ------------------------------------------------------------------------ */
+void oracle_riccati_gain_f64(int nx, int nu, const double *A, long long sA,
+                             const double *B, long long sB, const double *P, long long sP,
+                             const double *R, long long sR, double *K, long long sK,
+                             int *info, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *a = A + (long long)b * sA, *bm = B + (long long)b * sB;
+        const double *p = P + (long long)b * sP, *r = R + (long long)b * sR;
+        double *kk = K + (long long)b * sK;
+        double *pb = (double *)malloc(sizeof(double) * (size_t)nx * nu);
+        double *pa = (double *)malloc(sizeof(double) * (size_t)nx * nx);
+        double *sm = (double *)malloc(sizeof(double) * (size_t)nu * nu);
+        for (int i = 0; i < nx; ++i)          /* PB = P B */
+            for (int j = 0; j < nu; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < nx; ++l) s += p[l * nx + i] * bm[j * nx + l];
+                pb[j * nx + i] = s;
+            }
+        for (int i = 0; i < nu; ++i)          /* S = R + B^T PB */
+            for (int j = 0; j < nu; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < nx; ++l) s += bm[i * nx + l] * pb[j * nx + l];
+                sm[j * nu + i] = r[j * nu + i] + s;
+            }
+        for (int i = 0; i < nx; ++i)          /* PA = P A */
+            for (int j = 0; j < nx; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < nx; ++l) s += p[l * nx + i] * a[j * nx + l];
+                pa[j * nx + i] = s;
+            }
+        for (int i = 0; i < nu; ++i)          /* M = B^T PA, into K */
+            for (int j = 0; j < nx; ++j) {
+                double s = 0.0;
+                for (int l = 0; l < nx; ++l) s += bm[i * nx + l] * pa[j * nx + l];
+                kk[j * nu + i] = s;
+            }
+        info[b] = potrf_one(nu, sm, nu);      /* S = L L^T */
+        if (info[b] == 0)
+            for (int c = 0; c < nx; ++c) {    /* K = S^{-1} M, column by column */
+                forward_lower(nu, sm, nu, kk + (long long)c * nu, 0);
+                backward_lower_transposed(nu, sm, nu, kk + (long long)c * nu);
+            }
+        free(pb);
+        free(pa);
+        free(sm);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Rotation composition (Sec. III-B: SO(3) maps).  A chain of `chain` 3x3    */
 /* column-major rotations R_0..R_{c-1} per problem, stored back to back      */
 /* (9 values each), composes to R = R_0 R_1 ... R_{c-1}: R_{c-1} acts first. */

@@ -478,3 +478,109 @@ def test_adam_first_step_closed_form_and_training_decreases():
         oracle.adam_step(wv, gr, mm, vv, t, lr=1e-2)
     l1, _ = oracle.mlp_loss_grad(DIN, H, DOUT, wv, X, T, M)
     assert l1 < 0.5 * l0
+
+
+# ------------------------------------------------------- gemm with op()
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_gemm_ex_matches_numpy_with_transposes_and_scaling(ta, tb):
+    rng = np.random.default_rng(40 + 2 * ta + tb)
+    m, n, k, batch = 5, 7, 4, 6
+    A = rng.standard_normal((batch, k, m) if ta else (batch, m, k))
+    B = rng.standard_normal((batch, n, k) if tb else (batch, k, n))
+    C = rng.standard_normal((batch, m, n))
+    lda, ldb, ldc = A.shape[1] + 2, B.shape[1] + 1, m + 3
+
+    def pad(X, ld):
+        out = np.zeros((X.shape[0], X.shape[2], ld))
+        out[:, :, :X.shape[1]] = X.transpose(0, 2, 1)
+        return out.reshape(-1), ld * X.shape[2]
+    a, sA = pad(A, lda)
+    b, sB = pad(B, ldb)
+    c, sC = pad(C, ldc)
+    got = oracle.gemm_ex(ta, tb, m, n, k, 1.5, a, lda, sA, b, ldb, sB, -0.5, c, ldc, sC, batch)
+    opA = A.transpose(0, 2, 1) if ta else A
+    opB = B.transpose(0, 2, 1) if tb else B
+    want = 1.5 * opA @ opB - 0.5 * C
+    got = got.reshape(batch, n, ldc).transpose(0, 2, 1)[:, :m]
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    # beta == 0 never reads C (NaN there stays out of the result)
+    nanc = np.full_like(c, np.nan)
+    got0 = oracle.gemm_ex(ta, tb, m, n, k, 2.0, a, lda, sA, b, ldb, sB, 0.0, nanc, ldc, sC, batch)
+    got0 = got0.reshape(batch, n, ldc).transpose(0, 2, 1)[:, :m]
+    assert np.abs(got0 - 2.0 * opA @ opB).max() <= 1e-12 * np.abs(opA @ opB).max()
+
+
+def test_gemm_ex_integer_exact():
+    rng = np.random.default_rng(44)
+    m = n = k = 9
+    A = rng.integers(-4, 5, size=(3, m, k)).astype(np.float64)
+    B = rng.integers(-4, 5, size=(3, k, n)).astype(np.float64)
+    got = oracle.gemm_ex(1, 0, m, n, k, 1.0, _cm(A.transpose(0, 2, 1)), k, m * k, _cm(B), k, k * n, 0.0, None, m,
+                         m * n, 3)
+    assert np.array_equal(_mats(got, 3, m, n), A @ B)
+
+
+# ------------------------------------------------------- LQR gain
+def _riccati_case(nx, nu, batch, seed):
+    rng = np.random.default_rng(seed)
+    A = np.eye(nx) + 0.1 * rng.standard_normal((batch, nx, nx))
+    B = rng.standard_normal((batch, nx, nu))
+    Mp = rng.standard_normal((batch, nx, nx))
+    P = Mp @ Mp.transpose(0, 2, 1) + nx * np.eye(nx)
+    Mr = rng.standard_normal((batch, nu, nu))
+    R = Mr @ Mr.transpose(0, 2, 1) + nu * np.eye(nu)
+    return A, B, P, R
+
+
+@pytest.mark.parametrize("nx,nu", [(1, 1), (4, 1), (6, 3), (12, 4), (14, 7)])
+def test_riccati_gain_matches_linear_solve(nx, nu):
+    batch = 7
+    A, B, P, R = _riccati_case(nx, nu, batch, 50 + nx)
+    K, info = oracle.riccati_gain(nx, nu, _cm(A), _cm(B), _cm(P), _cm(R), batch)
+    Bt = B.transpose(0, 2, 1)
+    want = np.linalg.solve(R + Bt @ P @ B, Bt @ P @ A)
+    assert (info == 0).all()
+    assert np.abs(_mats(K, batch, nu, nx) - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_riccati_gain_scalar_closed_form():
+    a, b, p, r = 1.25, -0.75, 3.0, 0.5
+    K, info = oracle.riccati_gain(1, 1, [a], [b], [p], [r], 1)
+    assert info[0] == 0 and K[0] == pytest.approx(b * p * a / (r + b * b * p), rel=1e-15)
+
+
+def test_riccati_gain_dyadic_exact():
+    # B = P = I, R = 3 I (nu = nx): S = 4 I, L = 2 I, K = A / 4 exactly
+    nx, batch = 5, 4
+    A = np.random.default_rng(51).integers(-8, 9, size=(batch, nx, nx)).astype(np.float64)
+    I = np.broadcast_to(np.eye(nx), (batch, nx, nx))
+    K, info = oracle.riccati_gain(nx, nx, _cm(A), _cm(I), _cm(I), _cm(3 * I), batch)
+    assert (info == 0).all() and np.array_equal(_mats(K, batch, nx, nx), A / 4)
+
+
+def test_riccati_gain_satisfies_the_discrete_riccati_equation():
+    # P from SciPy's DARE solver; the oracle's K must close the Riccati
+    # recursion P = Q + A^T P A - A^T P B K (a transposed operand fails it)
+    rng = np.random.default_rng(52)
+    nx, nu = 6, 2
+    A = np.eye(nx) + 0.2 * rng.standard_normal((nx, nx))
+    B = rng.standard_normal((nx, nu))
+    Q = np.eye(nx)
+    R = np.array([[2.0, 0.3], [0.3, 1.0]])
+    P = sla.solve_discrete_are(A, B, Q, R)
+    K, info = oracle.riccati_gain(nx, nu, _cm(A[None]), _cm(B[None]), _cm(P[None]), _cm(R[None]), 1)
+    K = _mats(K, 1, nu, nx)[0]
+    assert info[0] == 0
+    resid = Q + A.T @ P @ A - A.T @ P @ B @ K - P
+    assert np.abs(resid).max() <= 1e-9 * np.abs(P).max()
+
+
+def test_riccati_gain_reports_indefinite_s():
+    # B = 0 leaves S = R; an R whose second pivot is negative gives info = 2
+    nx, nu = 3, 2
+    A = np.eye(nx)[None]
+    B = np.zeros((1, nx, nu))
+    P = np.eye(nx)[None]
+    R = np.array([[[1.0, 2.0], [2.0, 1.0]]])
+    _, info = oracle.riccati_gain(nx, nu, _cm(A), _cm(B), _cm(P), _cm(R), 1)
+    assert info[0] == 2
