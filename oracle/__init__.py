@@ -67,6 +67,15 @@ def _load():
                                           _ll, ctypes.c_double, _D, _int, _ll, _int]),
             "oracle_riccati_gain_f64": (None, [_int, _int, _D, _ll, _D, _ll, _D, _ll, _D, _ll, _D, _ll, _I,
                                                _int]),
+            "oracle_quat_retract_f64": (None, [_D, _D, _D, _int]),
+            "oracle_quat_error_f64": (None, [_D, _D, _D, _int]),
+            "oracle_se3_retract_f64": (None, [_D, _D, _D, _int]),
+            "oracle_motion_cross_f64": (None, [_D, _D, _D, _int]),
+            "oracle_eig3_f64": (None, [_D, _D, _D, _int]),
+            "oracle_svd3_f64": (None, [_D, _D, _D, _D, _int]),
+            "oracle_closest_rotation_f64": (None, [_D, _D, _int]),
+            "oracle_argmax_f64": (None, [_int, _D, _ll, _I, _int]),
+            "oracle_softmax_f64": (None, [_int, _D, _ll, _D, _ll, _int]),
             "oracle_rot3_compose_f64": (None, [_int, _D, _ll, _D, _ll, _int]),
             "oracle_se3_apply_f64": (None, [_int, _D, _ll, _int, _D, _ll, _D, _ll, _int]),
             "oracle_mlp_nparams": (_ll, [_int, _int, _int]),
@@ -233,6 +242,73 @@ def riccati_gain(nx, nu, A, B, P, R, batch, sA=None, sB=None, sP=None, sR=None, 
     _load().oracle_riccati_gain_f64(nx, nu, _dp(A), sA, _dp(B), sB, _dp(P), sP, _dp(R), sR, _dp(K), sK, _ip(info),
                                     batch)
     return K, info[:batch]
+
+
+# ------------------------------------------------ robotics operations
+def _out(n):
+    return np.zeros(max(1, n), dtype=np.float64)
+
+
+def quat_retract(q, d, batch):
+    """q * Exp(d), q = (w, x, y, z) [batch][4], d [batch][3] -> [batch][4]."""
+    o = _out(4 * batch)
+    _load().oracle_quat_retract_f64(_dp(_f64(q)), _dp(_f64(d)), _dp(o), batch)
+    return o
+
+
+def quat_error(q1, q2, batch):
+    """Log(conj(q1) * q2) -> [batch][3]."""
+    o = _out(3 * batch)
+    _load().oracle_quat_error_f64(_dp(_f64(q1)), _dp(_f64(q2)), _dp(o), batch)
+    return o
+
+
+def se3_retract(T, xi, batch):
+    """T Exp(xi), T 4x4 column-major [batch][16], xi = (rho, phi) [batch][6]."""
+    o = _out(16 * batch)
+    _load().oracle_se3_retract_f64(_dp(_f64(T)), _dp(_f64(xi)), _dp(o), batch)
+    return o
+
+
+def motion_cross(v, m, batch):
+    """v x m for motion vectors (linear, angular) [batch][6]."""
+    o = _out(6 * batch)
+    _load().oracle_motion_cross_f64(_dp(_f64(v)), _dp(_f64(m)), _dp(o), batch)
+    return o
+
+
+def eig3(A, batch):
+    """(w [batch][3] ascending, V [batch][9] column-major eigenvectors)."""
+    w, V = _out(3 * batch), _out(9 * batch)
+    _load().oracle_eig3_f64(_dp(_f64(A)), _dp(w), _dp(V), batch)
+    return w, V
+
+
+def svd3(M, batch):
+    """(U [batch][9], s [batch][3] descending, V [batch][9])."""
+    U, sv, V = _out(9 * batch), _out(3 * batch), _out(9 * batch)
+    _load().oracle_svd3_f64(_dp(_f64(M)), _dp(U), _dp(sv), _dp(V), batch)
+    return U, sv, V
+
+
+def closest_rotation(M, batch):
+    o = _out(9 * batch)
+    _load().oracle_closest_rotation_f64(_dp(_f64(M)), _dp(o), batch)
+    return o
+
+
+def argmax(n, x, batch, sx=None):
+    sx = n if sx is None else sx
+    idx = np.zeros(max(1, batch), dtype=np.int32)
+    _load().oracle_argmax_f64(n, _dp(_f64(x)), sx, _ip(idx), batch)
+    return idx[:batch]
+
+
+def softmax(n, x, batch, sx=None):
+    sx = n if sx is None else sx
+    y = _out(n * batch)
+    _load().oracle_softmax_f64(n, _dp(_f64(x)), sx, _dp(y), n, batch)
+    return y
 
 
 def rot3_compose(chain, Rs, batch, sRs=None, sR=9):

@@ -606,3 +606,302 @@ void oracle_adam_step_f64(long long np, double *w, const double *g, double *m,
         w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
     }
 }
+
+/* ======================================================================== */
+/* Robotics operations of the placement table of Sec. IV-E (Table II).      */
+/* The paper fixes a convention per operation but does not print them; the  */
+/* readings used here (and by the device library, by contract):             */
+/*   quaternion q = (w, x, y, z), Hamilton product, unit norm;               */
+/*   rotation vector d: angle |d| about d / |d|; Exp(d) = (cos |d|/2,         */
+/*     sin(|d|/2) d / |d|); Log is its inverse on the w >= 0 hemisphere;     */
+/*   quat_retract(q, d) = q * Exp(d)            (right perturbation);       */
+/*   quat_error(q1, q2) = Log(conj(q1) * q2)    (so q2 = retract(q1, err));  */
+/*   twist xi = (rho, phi): linear part first, angular second;              */
+/*   se3_retract(T, xi) = T Exp(xi), T a 4x4 column-major homogeneous        */
+/*     matrix, Exp(xi) = [Exp_SO3(phi), V(phi) rho; 0 1];                     */
+/*   motion vectors (linear, angular); motion_cross(v, m) = v x m =          */
+/*     (w x m_lin + v_lin x m_ang, w x m_ang) with w = v_ang;                */
+/*   eig3: symmetric 3x3, eigenvalues ascending, eigenvector columns with    */
+/*     their largest-magnitude component positive;                          */
+/*   svd3: M = U diag(s) V^T, s descending and >= 0;                          */
+/*   closest_rotation(M) = argmin_{R in SO(3)} |R - M|_F                      */
+/*     = U diag(1, 1, det(U V^T)) V^T;                                      */
+/*   argmax: first index of the largest value; softmax: exp(x - max) / sum.  */
+/* ======================================================================== */
+static void qmul(const double *a, const double *b, double *o)
+{
+    o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+static void qexp(const double *d, double *q)
+{
+    const double th = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double s = th > 0.0 ? sin(0.5 * th) / th : 0.5;
+    q[0] = cos(0.5 * th);
+    q[1] = s * d[0];
+    q[2] = s * d[1];
+    q[3] = s * d[2];
+}
+
+static void qlog(const double *qin, double *d)
+{
+    double q[4] = {qin[0], qin[1], qin[2], qin[3]};
+    if (q[0] < 0.0)
+        for (int i = 0; i < 4; ++i) q[i] = -q[i];
+    const double nv = sqrt(q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const double f = nv > 0.0 ? 2.0 * atan2(nv, q[0]) / nv : 2.0 / q[0];
+    for (int i = 0; i < 3; ++i) d[i] = f * q[i + 1];
+}
+
+void oracle_quat_retract_f64(const double *q, const double *d, double *out, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        double e[4];
+        qexp(d + 3LL * b, e);
+        qmul(q + 4LL * b, e, out + 4LL * b);
+    }
+}
+
+void oracle_quat_error_f64(const double *q1, const double *q2, double *out, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *a = q1 + 4LL * b;
+        const double c[4] = {a[0], -a[1], -a[2], -a[3]};
+        double r[4];
+        qmul(c, q2 + 4LL * b, r);
+        qlog(r, out + 3LL * b);
+    }
+}
+
+/* [p]x, column-major */
+static void skew(const double *p, double *S)
+{
+    S[0] = 0.0;   S[3] = -p[2]; S[6] = p[1];
+    S[1] = p[2];  S[4] = 0.0;   S[7] = -p[0];
+    S[2] = -p[1]; S[5] = p[0];  S[8] = 0.0;
+}
+
+/* Exp of a twist: R = I + a S + b S^2, V = I + b S + c S^2, S = [phi]x,
+ * a = sin t / t, b = (1 - cos t) / t^2 = 2 sin^2(t/2) / t^2,
+ * c = (t - sin t) / t^3 (its Taylor series below t = 1e-2). */
+static void se3_exp(const double *xi, double *T)
+{
+    const double *rho = xi, *phi = xi + 3;
+    const double t2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2], t = sqrt(t2);
+    double a, bb, c;
+    if (t > 0.0) {
+        const double sh = sin(0.5 * t);
+        a = sin(t) / t;
+        bb = 2.0 * sh * sh / t2;
+    } else {
+        a = 1.0;
+        bb = 0.5;
+    }
+    if (t < 1e-2)
+        c = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0 - t2 * t2 * t2 / 362880.0;
+    else
+        c = (t - sin(t)) / (t2 * t);
+    double S[9], S2[9], R[9], V[9];
+    skew(phi, S);
+    mat3_mul(S, S, S2);
+    for (int k = 0; k < 9; ++k) {
+        const double id = (k % 4 == 0) ? 1.0 : 0.0;
+        R[k] = id + a * S[k] + bb * S2[k];
+        V[k] = id + bb * S[k] + c * S2[k];
+    }
+    for (int k = 0; k < 16; ++k) T[k] = 0.0;
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) T[j * 4 + i] = R[j * 3 + i];
+    for (int i = 0; i < 3; ++i) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += V[l * 3 + i] * rho[l];
+        T[12 + i] = s;
+    }
+    T[15] = 1.0;
+}
+
+void oracle_se3_retract_f64(const double *T, const double *xi, double *out, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        double E[16];
+        se3_exp(xi + 6LL * b, E);
+        const double *t = T + 16LL * b;
+        double *o = out + 16LL * b;
+        for (int j = 0; j < 4; ++j)
+            for (int i = 0; i < 4; ++i) {
+                double s = 0.0;
+                for (int l = 0; l < 4; ++l) s += (i == 3 ? (l == 3 ? 1.0 : 0.0) : t[l * 4 + i]) * E[j * 4 + l];
+                o[j * 4 + i] = s;
+            }
+    }
+}
+
+static void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void oracle_motion_cross_f64(const double *v, const double *m, double *out, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *vl = v + 6LL * b, *w = vl + 3, *ml = m + 6LL * b, *mw = ml + 3;
+        double *o = out + 6LL * b, c1[3], c2[3];
+        cross3(w, ml, c1);
+        cross3(vl, mw, c2);
+        for (int i = 0; i < 3; ++i) o[i] = c1[i] + c2[i];
+        cross3(w, mw, o + 3);
+    }
+}
+
+/* Cyclic Jacobi eigenvalue iteration on a symmetric 3x3 (col-major A),
+ * to convergence in FP64; w ascending, V columns the eigenvectors. */
+static void eig3_one(const double *Ain, double *w, double *Vout)
+{
+    double A[9], V[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    for (int k = 0; k < 9; ++k) A[k] = Ain[k];
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        const double off = A[3] * A[3] + A[6] * A[6] + A[7] * A[7];
+        if (off == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                const double apq = A[q * 3 + p];
+                if (apq == 0.0) continue;
+                const double app = A[p * 3 + p], aqq = A[q * 3 + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                /* A <- J^T A J with J the rotation in the (p, q) plane */
+                for (int k = 0; k < 3; ++k) {
+                    const double akp = A[p * 3 + k], akq = A[q * 3 + k];
+                    A[p * 3 + k] = c * akp - s * akq;
+                    A[q * 3 + k] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double apk = A[k * 3 + p], aqk = A[k * 3 + q];
+                    A[k * 3 + p] = c * apk - s * aqk;
+                    A[k * 3 + q] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double vkp = V[p * 3 + k], vkq = V[q * 3 + k];
+                    V[p * 3 + k] = c * vkp - s * vkq;
+                    V[q * 3 + k] = s * vkp + c * vkq;
+                }
+            }
+    }
+    int idx[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (A[idx[j] * 4] < A[idx[i] * 4]) { const int tmp = idx[i]; idx[i] = idx[j]; idx[j] = tmp; }
+    for (int c = 0; c < 3; ++c) {
+        w[c] = A[idx[c] * 4];
+        int big = 0;
+        for (int i = 1; i < 3; ++i)
+            if (fabs(V[idx[c] * 3 + i]) > fabs(V[idx[c] * 3 + big])) big = i;
+        const double sg = V[idx[c] * 3 + big] < 0.0 ? -1.0 : 1.0;
+        for (int i = 0; i < 3; ++i) Vout[c * 3 + i] = sg * V[idx[c] * 3 + i];
+    }
+}
+
+void oracle_eig3_f64(const double *A, double *w, double *V, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) eig3_one(A + 9LL * b, w + 3LL * b, V + 9LL * b);
+}
+
+/* SVD of a 3x3 through the eigen-decomposition of M^T M: V its
+ * eigenvectors (descending), s = sqrt of the eigenvalues, U = M V / s with
+ * the last column completed as u1 x u2 when s3 is zero. */
+static void svd3_one(const double *M, double *U, double *s, double *V)
+{
+    double MtM[9], w[3], E[9];
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+            double acc = 0.0;
+            for (int l = 0; l < 3; ++l) acc += M[i * 3 + l] * M[j * 3 + l];
+            MtM[j * 3 + i] = acc;
+        }
+    eig3_one(MtM, w, E);
+    for (int c = 0; c < 3; ++c) {
+        const int e = 2 - c;  /* descending */
+        s[c] = sqrt(w[e] > 0.0 ? w[e] : 0.0);
+        for (int i = 0; i < 3; ++i) V[c * 3 + i] = E[e * 3 + i];
+    }
+    for (int c = 0; c < 3; ++c) {
+        double u[3];
+        for (int i = 0; i < 3; ++i) {
+            double acc = 0.0;
+            for (int l = 0; l < 3; ++l) acc += M[l * 3 + i] * V[c * 3 + l];
+            u[i] = acc;
+        }
+        for (int i = 0; i < 3; ++i) U[c * 3 + i] = s[c] > 0.0 ? u[i] / s[c] : 0.0;
+    }
+    if (!(s[2] > 0.0)) cross3(U, U + 3, U + 6);
+}
+
+void oracle_svd3_f64(const double *M, double *U, double *s, double *V, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) svd3_one(M + 9LL * b, U + 9LL * b, s + 3LL * b, V + 9LL * b);
+}
+
+void oracle_closest_rotation_f64(const double *M, double *R, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        double U[9], s[3], V[9], UVt[9];
+        svd3_one(M + 9LL * b, U, s, V);
+        for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 3; ++i) {
+                double acc = 0.0;
+                for (int l = 0; l < 3; ++l) acc += U[l * 3 + i] * V[l * 3 + j];
+                UVt[j * 3 + i] = acc;
+            }
+        const double det = UVt[0] * (UVt[4] * UVt[8] - UVt[7] * UVt[5]) -
+                           UVt[3] * (UVt[1] * UVt[8] - UVt[7] * UVt[2]) +
+                           UVt[6] * (UVt[1] * UVt[5] - UVt[4] * UVt[2]);
+        const double d[3] = {1.0, 1.0, det < 0.0 ? -1.0 : 1.0};
+        double *r = R + 9LL * b;
+        for (int j = 0; j < 3; ++j)
+            for (int i = 0; i < 3; ++i) {
+                double acc = 0.0;
+                for (int l = 0; l < 3; ++l) acc += U[l * 3 + i] * d[l] * V[l * 3 + j];
+                r[j * 3 + i] = acc;
+            }
+    }
+}
+
+void oracle_argmax_f64(int n, const double *x, long long sx, int *idx, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *v = x + (long long)b * sx;
+        int best = 0;
+        for (int i = 1; i < n; ++i)
+            if (v[i] > v[best]) best = i;
+        idx[b] = best;
+    }
+}
+
+void oracle_softmax_f64(int n, const double *x, long long sx, double *y, long long sy, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *v = x + (long long)b * sx;
+        double *o = y + (long long)b * sy;
+        double mx = v[0];
+        for (int i = 1; i < n; ++i)
+            if (v[i] > mx) mx = v[i];
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) { o[i] = exp(v[i] - mx); s += o[i]; }
+        for (int i = 0; i < n; ++i) o[i] /= s;
+    }
+}

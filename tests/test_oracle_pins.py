@@ -584,3 +584,131 @@ def test_riccati_gain_reports_indefinite_s():
     R = np.array([[[1.0, 2.0], [2.0, 1.0]]])
     _, info = oracle.riccati_gain(nx, nu, _cm(A), _cm(B), _cm(P), _cm(R), 1)
     assert info[0] == 2
+
+
+# ------------------------------------------------- robotics operations
+def _unit_quats(batch, seed):
+    q = np.random.default_rng(seed).standard_normal((batch, 4))
+    return q / np.linalg.norm(q, axis=1, keepdims=True)
+
+
+def _wxyz_to_scipy(q):
+    from scipy.spatial.transform import Rotation
+    return Rotation.from_quat(np.concatenate([q[:, 1:], q[:, :1]], axis=1))
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-3, 1e-9, 0.0])
+def test_quat_retract_against_scipy_rotations(scale):
+    from scipy.spatial.transform import Rotation
+    batch = 40
+    q = _unit_quats(batch, 100)
+    d = scale * np.random.default_rng(101).standard_normal((batch, 3))
+    out = oracle.quat_retract(q.reshape(-1), d.reshape(-1), batch).reshape(batch, 4)
+    want = (_wxyz_to_scipy(q) * Rotation.from_rotvec(d)).as_matrix()
+    assert np.abs(_wxyz_to_scipy(out).as_matrix() - want).max() <= 1e-13
+    assert np.abs(np.linalg.norm(out, axis=1) - 1.0).max() <= 1e-14
+    if scale == 0.0:
+        assert np.array_equal(out, q)
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-6, 0.0])
+def test_quat_error_inverts_retract_and_matches_scipy(scale):
+    batch = 40
+    q1 = _unit_quats(batch, 102)
+    d = scale * np.random.default_rng(103).uniform(-1, 1, (batch, 3))   # |d| < pi: Log is unique
+    q2 = oracle.quat_retract(q1.reshape(-1), d.reshape(-1), batch).reshape(batch, 4)
+    q2[::2] *= -1.0                                                     # the double cover
+    err = oracle.quat_error(q1.reshape(-1), q2.reshape(-1), batch).reshape(batch, 3)
+    assert np.abs(err - d).max() <= 1e-12 * scale + 1e-15          # roundoff of the unit products
+    rel = (_wxyz_to_scipy(q1).inv() * _wxyz_to_scipy(q2)).as_rotvec()
+    assert np.abs(err - rel).max() <= 1e-12
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-3, 1e-8, 0.0])
+def test_se3_retract_against_matrix_exponential(scale):
+    batch = 20
+    rng = np.random.default_rng(104)
+    T = np.zeros((batch, 4, 4))
+    T[:, :3, :3] = _wxyz_to_scipy(_unit_quats(batch, 105)).as_matrix()
+    T[:, :3, 3] = rng.standard_normal((batch, 3))
+    T[:, 3, 3] = 1.0
+    xi = scale * rng.standard_normal((batch, 6))
+    out = oracle.se3_retract(_cm(T), xi.reshape(-1), batch)
+    for b in range(batch):
+        rho, phi = xi[b, :3], xi[b, 3:]
+        Xi = np.zeros((4, 4))
+        Xi[:3, :3] = [[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]]
+        Xi[:3, 3] = rho
+        want = T[b] @ sla.expm(Xi)
+        got = _mats(out[b * 16:(b + 1) * 16], 1, 4, 4)[0]
+        assert np.abs(got - want).max() <= 1e-13, (b, scale)
+
+
+def test_motion_cross_against_the_6x6_cross_matrix():
+    batch = 30
+    rng = np.random.default_rng(106)
+    v, m = rng.standard_normal((batch, 6)), rng.standard_normal((batch, 6))
+    out = oracle.motion_cross(v.reshape(-1), m.reshape(-1), batch).reshape(batch, 6)
+
+    def sk(p):
+        return np.array([[0, -p[2], p[1]], [p[2], 0, -p[0]], [-p[1], p[0], 0]])
+    for b in range(batch):
+        vl, w = v[b, :3], v[b, 3:]
+        X = np.zeros((6, 6))          # motion cross matrix for (linear, angular) ordering
+        X[:3, :3] = sk(w)
+        X[:3, 3:] = sk(vl)
+        X[3:, 3:] = sk(w)
+        assert np.abs(out[b] - X @ m[b]).max() <= 1e-14
+    vv = oracle.motion_cross(v.reshape(-1), v.reshape(-1), batch)
+    assert np.abs(vv).max() <= 1e-14                         # v x v = 0
+
+
+def test_eig3_against_numpy_eigh():
+    batch = 60
+    rng = np.random.default_rng(107)
+    A = rng.standard_normal((batch, 3, 3))
+    A = A + A.transpose(0, 2, 1)
+    A[0] = np.diag([3.0, -1.0, 2.0])                          # already diagonal
+    A[1] = 2.0 * np.eye(3)                                    # triple eigenvalue
+    w, V = oracle.eig3(_cm(A), batch)
+    w, V = w.reshape(batch, 3), _mats(V, batch, 3, 3)
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() <= 1e-13
+    assert np.abs(A @ V - V * w[:, None, :]).max() <= 1e-13
+    assert np.abs(V.transpose(0, 2, 1) @ V - np.eye(3)).max() <= 1e-13
+    big = np.argmax(np.abs(V), axis=1)
+    assert (np.take_along_axis(V, big[:, None, :], axis=1) > 0).all()
+
+
+def test_svd3_against_numpy_and_closest_rotation_against_polar():
+    batch = 60
+    rng = np.random.default_rng(108)
+    M = rng.standard_normal((batch, 3, 3))
+    M[0] = np.diag([1.0, 2.0, 0.0])                            # rank deficient
+    U, s, V = oracle.svd3(_cm(M), batch)
+    U, s, V = _mats(U, batch, 3, 3), s.reshape(batch, 3), _mats(V, batch, 3, 3)
+    assert np.abs(s - np.linalg.svd(M, compute_uv=False)).max() <= 1e-12
+    assert np.abs(U * s[:, None, :] @ V.transpose(0, 2, 1) - M).max() <= 1e-12
+    assert np.abs(U.transpose(0, 2, 1) @ U - np.eye(3)).max() <= 1e-12
+    R = _mats(oracle.closest_rotation(_cm(M), batch), batch, 3, 3)
+    assert np.abs(R.transpose(0, 2, 1) @ R - np.eye(3)).max() <= 1e-12
+    assert np.abs(np.linalg.det(R) - 1.0).max() <= 1e-12
+    pos = np.linalg.det(M) > 0
+    for b in np.nonzero(pos)[0]:
+        Up, _ = sla.polar(M[b])                                # orthogonal polar factor = closest rotation
+        assert np.abs(R[b] - Up).max() <= 1e-11
+    # the closest rotation to a rotation is itself
+    Q = _wxyz_to_scipy(_unit_quats(5, 109)).as_matrix()
+    assert np.abs(_mats(oracle.closest_rotation(_cm(Q), 5), 5, 3, 3) - Q).max() <= 1e-13
+
+
+def test_argmax_and_softmax_against_numpy():
+    from scipy.special import softmax as sp_softmax
+    batch, n = 50, 16
+    x = np.random.default_rng(110).standard_normal((batch, n))
+    x[3, [2, 9]] = 7.0                                          # tie: the first index wins
+    assert np.array_equal(oracle.argmax(n, x.reshape(-1), batch), np.argmax(x, axis=1))
+    assert oracle.argmax(n, x.reshape(-1), batch)[3] == 2
+    y = oracle.softmax(n, x.reshape(-1), batch).reshape(batch, n)
+    assert np.abs(y - sp_softmax(x, axis=1)).max() <= 1e-15
+    big = oracle.softmax(n, (x + 1000.0).reshape(-1), batch).reshape(batch, n)  # shift invariance, no overflow
+    assert np.abs(big - y).max() <= 1e-12                       # x + 1000 rounds at ~1e-13
