@@ -14,7 +14,9 @@ Reported (one JSON line):
               D2H of every result inside the timed region);
   roofline    of the dominant kernel (largest share of the step), from CUDA
               events around its launches;
-  cpu_baseline  the FP64 C oracle on a bounded sample, all host cores;
+  cpu_baseline  the FP64 C oracle on a bounded sample, all host cores (and
+              the same sample on one core);
+  peaks       measured FP32/FP64/tensor pipe peaks (glass_peak_probe);
   plain       the plain step and the tuned/plain speedup.
 `--impl reference` times the oracle (the reference arm of this task) on the
 same workload, one bounded sample per step.
@@ -240,9 +242,21 @@ def cpu_baseline(hosts, ops_sizes, batch, budget_s=12.0):
         full_time += dt / s * batch
         samples.append(f"{op}{n}:{s}")
     value = len(ops_sizes) * batch / full_time
-    return {"value": value, "unit": "matrices/s", "cores": oracle.max_threads(), "kind": "oracle",
+    cores = oracle.max_threads()
+    # the same samples on one core
+    one_time = 0.0
+    oracle.set_threads(1)
+    try:
+        for (op, n), host, tag in zip(ops_sizes, hosts, samples):
+            s = int(tag.split(":")[1])
+            dt, s = oracle_cell_time(op, n, host, batch, s)
+            one_time += dt / s * batch
+    finally:
+        oracle.set_threads(cores)
+    return {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
+            "value_1core": len(ops_sizes) * batch / one_time,
             "sample": f"per cell an adaptive prefix of the {batch} problems ({', '.join(samples)}), "
-                      f"scaled to the full batch"}
+                      f"scaled to the full batch; value_1core: the same samples on one core"}
 
 
 # ------------------------------------------------------------- reference
@@ -543,11 +557,155 @@ def extra_learned():
     return res
 
 
+def measure_peaks():
+    """Measured pipe peaks (TFLOP/s) from the library's throughput probes:
+    FP32 FFMA, FP64 DFMA, TF32 m16n8k8 and BF16 m16n8k16 mma.sync; each
+    launch sized to about 2 ms, the best of 5 launches."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, threads = sms * 8, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    out = {}
+
+    def once(kind, iters):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        st, fl = g.glass_peak_probe(kind, iters, blocks, threads, sink)
+        b.record()
+        torch.cuda.synchronize()
+        g.check(st, "peak probe")
+        return a.elapsed_time(b), fl
+    for kind, name in ((0, "fp32_ffma"), (1, "fp64_dfma"), (2, "tf32_mma_m16n8k8"), (3, "bf16_mma_m16n8k16")):
+        iters = 16
+        for _ in range(4):
+            ms, _ = once(kind, iters)
+            if ms >= 1.0:
+                break
+            iters = int(min(1 << 22, max(iters * 2, iters * 2.0 / max(ms, 1e-3))))
+        best = min(once(kind, iters) for _ in range(5))
+        out[name] = {"tflops": best[1] / (best[0] / 1e3) / 1e12, "ms": best[0], "iters": iters,
+                     "grid": f"{blocks}x{threads}"}
+    return out
+
+
+def extra_latency(ops=None, sizes=(6, 64), batches=(1, 1024, 16384)):
+    """Per-call latency: one launch on a cold L2 (a 512 MB buffer written
+    between calls), timed with events; the median of 5."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300.cells import OPS, Cell
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for op in ops or OPS:
+        for n in sizes:
+            for batch in batches:
+                cell = Cell(op, n, batch, sets=1, device_inputs=True, seed=2000 + n)
+                g.check(cell.launch(0), f"latency {op} {n}")
+                ts = []
+                for _ in range(5):
+                    cell.restore()
+                    flush.fill_(1)
+                    torch.cuda.synchronize()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    cell.launch(0)
+                    b.record()
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b) * 1e3)
+                out[f"{op}:n{n}:b{batch}"] = round(statistics.median(ts), 2)
+                del cell
+        torch.cuda.empty_cache()
+    return {"unit": "us per call (cold L2, single launch, table placement)", "cells": out}
+
+
+def extra_batch_scaling(peaks, ops=("gemm", "posv", "getrf_getrs"), sizes=(16, 64),
+                        batches=(16384, 65536, 262144, 1048576)):
+    """Where the HBM roofline becomes reachable: the matrix operations at
+    batches up to 2^20 (table placement; inputs restored between launches,
+    untimed)."""
+    import torch
+    from paper_2609_28179_gb300.cells import Cell
+    out = {}
+    for op in ops:
+        for n in sizes:
+            for batch in batches:
+                cell = Cell(op, n, batch, sets=1, device_inputs=True, seed=3000 + n)
+                ms = _graph_time(lambda: cell.launch(0), 1, iters=5, setup=cell.restore)
+                out[f"{op}:n{n}:b{batch}"] = {"us": round(ms * 1e3, 2), "matrices_per_s": batch / (ms / 1e3),
+                                              "gbs": cell.bytes / (ms / 1e3) / 1e9,
+                                              "frac_hbm": cell.bytes / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+                del cell
+                torch.cuda.empty_cache()
+    return out
+
+
+def extra_riccati(peaks, batches=(64, 16384)):
+    """LQR feedback gain K = (R + B^T P B)^{-1} B^T P A at the workload's
+    (nx, nu) pairs: the fused kernel at every feasible placement against the
+    composition of primitive calls, and what the table resolves."""
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300 import workloads as W
+    from paper_2609_28179_gb300.tune import COMPOSED, RiccatiCell
+    out = {}
+    for nx, nu in W.RICCATI_SIZES:
+        for batch in batches:
+            cell = RiccatiCell(nx, nu, batch)
+            times = {}
+            for scope, pack in cell.placements():
+                g.check(cell.launch(scope, pack), "riccati")
+                times[f"{g.SCOPE_NAMES[scope]}x{pack}"] = _graph_time(lambda: cell.launch(scope, pack), 8) * 1e3
+            auto_us = _graph_time(lambda: cell.launch(), 8) * 1e3
+            fused = {k: v for k, v in times.items() if not k.startswith("composed")}
+            bf = min(fused, key=fused.get)
+            out[f"{nx}x{nu}:b{batch}"] = {
+                "fused_best": bf, "fused_us": round(fused[bf], 2), "composed_us": round(times["composedx1"], 2),
+                "composed_over_fused": times["composedx1"] / fused[bf], "auto_us": round(auto_us, 2),
+                "auto_placement": "{}x{}".format(*(lambda s: (g.SCOPE_NAMES[s[1][0]], s[1][1]))(
+                    g.glass_riccati_placement(nx, nu, batch, True))),
+                "matrices_per_s_auto": batch / (auto_us / 1e6),
+                "gbs_auto": cell.bytes / (auto_us / 1e6) / 1e9}
+            del cell
+    return out
+
+
+def extra_robo(peaks, batches=(4096, 1 << 20)):
+    """Robotics operations of the placement table (quaternion/SE(3)
+    retractions and error, motion cross product, eig3, svd3, closest
+    rotation, argmax and softmax at n = 16): ns per problem at the best
+    placement of each scope, as the paper tabulates them, and the table's."""
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300.tune import ROBO_N, RoboCell
+    out = {}
+    for op, name in enumerate(g.ROBO_OPS):
+        for batch in batches:
+            cell = RoboCell(op, batch)
+            per_scope = {}
+            for scope in (0, 1, 2):
+                best = None
+                for pack in (1, 2, 4, 8):
+                    if not g.glass_robo_feasible(op, ROBO_N, scope, pack):
+                        continue
+                    g.check(cell.launch(scope, pack), name)
+                    us = _graph_time(lambda: cell.launch(scope, pack), 16) * 1e3
+                    if best is None or us < best[0]:
+                        best = (us, pack)
+                per_scope[g.SCOPE_NAMES[scope]] = {"ns_per_problem": best[0] * 1e3 / batch, "pack": best[1]}
+            us = _graph_time(lambda: cell.launch(), 16) * 1e3
+            out[f"{name}:b{batch}"] = {"scopes": per_scope, "table_ns_per_problem": us * 1e3 / batch,
+                                       "table_gbs": cell.bytes / (us / 1e6) / 1e9,
+                                       "table_frac_hbm": cell.bytes / (us / 1e6) / 1e9 / peaks["hbm_gbs"]}
+            del cell
+    return out
+
+
 def run_extras(peaks, which):
     out = {}
     for name, fn in (("plain_posv_n6", lambda: extra_plain_posv(peaks)), ("mixed_size", lambda: extra_varsize(peaks)),
                      ("tensor_core_gemm", lambda: extra_tc_gemm(peaks)), ("refined_posv", lambda: extra_refine(peaks)),
-                     ("learned_placement", extra_learned)):
+                     ("learned_placement", extra_learned), ("latency", extra_latency),
+                     ("batch_scaling", lambda: extra_batch_scaling(peaks)),
+                     ("riccati_gain", lambda: extra_riccati(peaks)), ("robotics_ops", lambda: extra_robo(peaks))):
         if which != "all" and name not in which.split(","):
             continue
         try:
@@ -630,11 +788,12 @@ def main():
 
     peaks = load_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    fp32_peak = fp32_peak_tflops(sms, peaks["sm_max_mhz"])
+    pipes = measure_peaks()
+    fp32_peak = pipes["fp32_ffma"]["tflops"]
     rows = []
     for c, (s, p), us_t, (ps, pp), us_p in zip(cells, tuned, per_tuned, plain, per_plain):
         t_bw = c.bytes / (peaks["hbm_gbs"] * 1e9)
-        t_fl = c.flops / (fp32_peak * 1e12)
+        t_fl = c.flops / (fp32_peak * 1e12)  # measured FFMA peak
         bound = "hbm" if t_bw >= t_fl else "alu"
         t_roof = max(t_bw, t_fl)
         rows.append({"op": c.op, "n": c.n, "placement": f"{g.SCOPE_NAMES[s]}x{p}", "us": round(us_t * 1e3, 2),
@@ -651,7 +810,7 @@ def main():
         roof = {"bound": "alu", "achieved": dc.flops / dur / 1e12, "peak": fp32_peak, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["peak_src"] = (f"{peaks['src']} HBM copy" if roof["bound"] == "hbm" else
-                        f"FP32 SIMT {sms} SMs x 128 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz")
+                        "measured FP32 FFMA probe (glass_peak_probe)")
     key = f"{dc.op}:{dc.n}:{dr['placement']}"
     roof["kernel"] = key
     roof["traffic"] = traffic_for(key)
@@ -663,7 +822,9 @@ def main():
             "clocks": clocks,
             "plain": {"value": problems * args.steps / (t_plain / 1e3), "ms_per_step": t_plain / args.steps,
                       "speedup_tuned_over_plain": t_plain / t_tuned},
-            "hbm_weighted_frac": sum(r["frac"] * r["us"] for r in rows) / sum(r["us"] for r in rows)}
+            "hbm_weighted_frac": sum(r["frac"] * r["us"] for r in rows) / sum(r["us"] for r in rows),
+            "peaks": {"hbm_gbs": peaks["hbm_gbs"], "hbm_src": peaks["src"], **pipes,
+                      "fp32_nominal_tflops": fp32_peak_tflops(sms, peaks["sm_max_mhz"])}}
     if t_e2e is not None:
         line["e2e"] = {"value": problems * args.steps / (t_e2e / 1e3), "unit": "matrices/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -74,7 +74,9 @@ typedef enum {
     GLASS_SCOPE_AUTO = -1,
     GLASS_SCOPE_THREAD = 0, /* one problem per thread, 32*pack problems per CTA */
     GLASS_SCOPE_WARP = 1,   /* one problem per warp, pack warps per CTA        */
-    GLASS_SCOPE_BLOCK = 2   /* one problem per team of threads, pack teams/CTA */
+    GLASS_SCOPE_BLOCK = 2,  /* one problem per team of threads, pack teams/CTA */
+    GLASS_SCOPE_COMPOSED = 3 /* composite operations only: one library call per
+                                primitive step, intermediates in global memory */
 } glass_scope;
 
 /* Operation identifiers of the placement table (the six swept operations
@@ -284,6 +286,137 @@ glass_status glass_mlp_loss_grad(int din, const float *w, int rows, const float 
 glass_status glass_mlp_adam(int nparams, float *w, const float *grad, float *m, float *v,
                             int t, float lr, float beta1, float beta2, float eps,
                             glass_stream_t stream);
+
+/* ------------------------------------------------- composite operations */
+
+/* Batched GEMM with operand transposes and scaling (Sec. III-B "BLAS
+ * L1-L3"; the BLAS xGEMM contract):
+ *   C = alpha op(A) op(B) + beta C,  op(X) = X (trans 0) or X^T (trans 1),
+ * C m x n, op(A) m x k, op(B) k x n, 1 <= m, n, k <= 64, FP32, column-major
+ * with leading dimensions of the STORED operands (A is k x m when transa).
+ * With beta == 0, C is not read.  Placement: warp (one warp per problem) or
+ * block (a 128-thread team), pack problems per CTA; auto picks by size.
+ * Operands are staged in shared memory with cp.async. */
+glass_status glass_batched_gemm_ex(int transa, int transb, int m, int n, int k, float alpha,
+                                   const void *A, int lda, long long sA, const void *B, int ldb,
+                                   long long sB, float beta, void *C, int ldc, long long sC,
+                                   int batch, const glass_opts *opts, glass_stream_t stream);
+
+/* LQR feedback gain (Sec. III-B fused operations; Sec. IV-E, Fig. 7):
+ *   K = (R + B^T P B)^{-1} B^T P A
+ * A nx x nx, B nx x nu, P nx x nx (symmetric: the cost-to-go of the
+ * Riccati recursion), R nu x nu (symmetric positive definite), K nu x nx;
+ * 1 <= nx, nu <= 64; FP32, each operand packed column-major (leading
+ * dimension = rows) with batch stride s* in elements (inputs may use 0).
+ * info[b] is the Cholesky info of S = R + B^T P B (0, or j+1 for the first
+ * failing column; K is unspecified then).
+ * Two placements compute it (fusion granularity is itself a placement,
+ * Sec. IV-E): a fused kernel (scope warp or block, pack problems per CTA)
+ * that keeps P B, S, B^T P A and the factor of S in shared memory, or the
+ * composition (scope GLASS_SCOPE_COMPOSED) of glass_batched_gemm (P B),
+ * one device copy (S = R), glass_batched_gemm_ex (S += B^T (P B);
+ * K = (P B)^T A) and glass_batched_posv (K = S^{-1} K), intermediates in the
+ * caller's workspace ws of at least glass_riccati_workspace(nx, nu, batch)
+ * bytes (256-byte aligned).  Both form B^T P A as (P B)^T A.  Auto resolves
+ * from a measured table; the composition is chosen only when ws is large
+ * enough, and requesting it without that workspace is GLASS_ERR_WORKSPACE. */
+size_t glass_riccati_workspace(int nx, int nu, int batch);
+glass_status glass_riccati_gain(int nx, int nu, const void *A, long long sA, const void *B,
+                                long long sB, const void *P, long long sP, const void *R,
+                                long long sR, void *K, long long sK, int *info, int batch,
+                                void *ws, size_t ws_bytes, const glass_opts *opts,
+                                glass_stream_t stream);
+
+/* The placement glass_riccati_gain resolves for (nx, nu, batch) when the
+ * composition is (composed_ok != 0) or is not available. */
+glass_status glass_riccati_placement(int nx, int nu, int batch, int composed_ok,
+                                     glass_placement *out);
+/* 1 when the fused kernel can run (nx, nu) at placement p, else 0. */
+int glass_riccati_feasible(int nx, int nu, glass_placement p);
+
+/* ------------------------------------------------- robotics operations */
+
+/* The robotics operations of the paper's placement table (Sec. IV-E,
+ * Table II), each at thread, warp or block scope.  Conventions (the paper
+ * requires an operation's interface to fix them, Sec. III-B):
+ *  - quaternion q = (w, x, y, z), Hamilton product, unit norm expected;
+ *  - rotation vector d: angle |d| about d / |d|, Exp(d) = (cos |d|/2,
+ *    sin(|d|/2) d / |d|), Log its inverse on the w >= 0 hemisphere;
+ *  - retractions perturb on the right: quat_retract(q, d) = q Exp(d),
+ *    se3_retract(T, xi) = T Exp(xi); quat_error(q1, q2) = Log(q1^-1 q2);
+ *  - twists xi and motion vectors are (linear, angular);
+ *    motion_cross(v, m) = v x m = (w x m_lin + v_lin x m_ang, w x m_ang),
+ *    w = v_ang;
+ *  - 4x4 homogeneous transforms and 3x3 matrices are column-major; the
+ *    bottom row of an input transform is not read, outputs get (0 0 0 1);
+ *  - eig3 (symmetric A): eigenvalues ascending, eigenvector columns with
+ *    their largest-magnitude component positive; only the lower triangle is
+ *    not enough -- all nine entries are read and A must be symmetric;
+ *  - svd3: M = U diag(s) V^T, s descending, s >= 0, U and V orthogonal;
+ *  - closest_rotation(M) = U diag(1, 1, det(U V^T)) V^T, the rotation
+ *    nearest M in the Frobenius norm;
+ *  - argmax: the first index of the largest of n values (NaN inputs
+ *    unspecified); softmax: exp(x_i - max) / sum_j exp(x_j - max).
+ * Storage is FP32, problem b's operands packed at b times their size
+ * (q: 4, d: 3, T: 16, xi: 6, v/m: 6, 3x3: 9, eigen/singular values: 3);
+ * quaternion and transform arrays must be 16-byte aligned.  argmax and
+ * softmax read x[b*sx + i], i < n, and write idx[b] / y[b*sy + i].
+ * Placement: scope thread (one problem per thread, 32*pack per CTA), warp
+ * (one problem per warp) or block (a 64-thread team, pack <= 4); auto
+ * resolves from the measured table.  The element-wise operations run on the
+ * first thread of a warp or block team; argmax and softmax spread the n
+ * values over the team. */
+typedef enum {
+    GLASS_ROBO_QUAT_RETRACT = 0,
+    GLASS_ROBO_QUAT_ERROR = 1,
+    GLASS_ROBO_SE3_RETRACT = 2,
+    GLASS_ROBO_MOTION_CROSS = 3,
+    GLASS_ROBO_EIG3 = 4,
+    GLASS_ROBO_SVD3 = 5,
+    GLASS_ROBO_CLOSEST_ROTATION = 6,
+    GLASS_ROBO_ARGMAX = 7,
+    GLASS_ROBO_SOFTMAX = 8,
+    GLASS_ROBO_NUM_OPS = 9
+} glass_robo_op;
+
+glass_status glass_batched_quat_retract(const void *q, const void *d, void *out, int batch,
+                                        const glass_opts *opts, glass_stream_t stream);
+glass_status glass_batched_quat_error(const void *q1, const void *q2, void *out, int batch,
+                                      const glass_opts *opts, glass_stream_t stream);
+glass_status glass_batched_se3_retract(const void *T, const void *xi, void *out, int batch,
+                                       const glass_opts *opts, glass_stream_t stream);
+glass_status glass_batched_motion_cross(const void *v, const void *m, void *out, int batch,
+                                        const glass_opts *opts, glass_stream_t stream);
+glass_status glass_batched_eig3(const void *A, void *w, void *V, int batch,
+                                const glass_opts *opts, glass_stream_t stream);
+glass_status glass_batched_svd3(const void *M, void *U, void *s, void *V, int batch,
+                                const glass_opts *opts, glass_stream_t stream);
+glass_status glass_batched_closest_rotation(const void *M, void *R, int batch,
+                                            const glass_opts *opts, glass_stream_t stream);
+glass_status glass_batched_argmax(int n, const void *x, long long sx, int *idx, int batch,
+                                  const glass_opts *opts, glass_stream_t stream);
+glass_status glass_batched_softmax(int n, const void *x, long long sx, void *y, long long sy,
+                                   int batch, const glass_opts *opts, glass_stream_t stream);
+
+/* The placement the robotics operation `op` resolves at `batch` (n: the
+ * length for argmax/softmax, else ignored), and its feasibility test. */
+glass_status glass_robo_placement(int op, int n, int batch, glass_placement *out);
+int glass_robo_feasible(int op, int n, glass_placement p);
+
+/* ------------------------------------------------------- measurement aid */
+
+/* Pipe-throughput probe (no counterpart in the paper; it supplies the
+ * measured peaks the rooflines are quoted against).  Launches `blocks` CTAs
+ * of `threads` threads (32..256, a multiple of 32) that keep one pipe busy
+ * with independent work for `iters` iterations:
+ *   kind 0: FP32 FFMA, 1: FP64 DFMA, 2: TF32 mma.sync m16n8k8,
+ *   3: BF16 mma.sync m16n8k16 (FP32 accumulation).
+ * sink: device scratch of blocks*threads elements (float; double for kind
+ * 1), written only to keep the work live.  *flops (host, may be null)
+ * receives the floating-point operations of one launch (an FMA counts 2).
+ * Time the launch on `stream` with events; flops / time is the peak. */
+glass_status glass_peak_probe(int kind, int iters, int blocks, int threads, void *sink,
+                              double *flops, glass_stream_t stream);
 
 /* ----------------------------------------------------------- diagnostics */
 

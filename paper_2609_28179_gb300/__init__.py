@@ -29,10 +29,13 @@ GLASS_ERR_WORKSPACE = 5
 GLASS_F32, GLASS_F64, GLASS_BF16 = 0, 1, 2
 GLASS_MATH_FP32, GLASS_MATH_BF16_TC, GLASS_MATH_TF32_TC, GLASS_MATH_3XTF32_TC = 0, 1, 2, 3
 GLASS_LAYOUT_COLMAJOR, GLASS_LAYOUT_INTERLEAVED32 = 0, 1
-GLASS_SCOPE_AUTO, GLASS_SCOPE_THREAD, GLASS_SCOPE_WARP, GLASS_SCOPE_BLOCK = -1, 0, 1, 2
+GLASS_SCOPE_AUTO, GLASS_SCOPE_THREAD, GLASS_SCOPE_WARP, GLASS_SCOPE_BLOCK, GLASS_SCOPE_COMPOSED = -1, 0, 1, 2, 3
 (GLASS_OP_GEMM, GLASS_OP_POSV, GLASS_OP_TRSM, GLASS_OP_GETRF_GETRS, GLASS_OP_ROT3, GLASS_OP_SE3,
  GLASS_OP_POTRF, GLASS_OP_POTRS) = range(8)
-SCOPE_NAMES = {0: "thread", 1: "warp", 2: "block"}
+SCOPE_NAMES = {0: "thread", 1: "warp", 2: "block", 3: "composed"}
+# robotics operations (glass_robo_op)
+ROBO_OPS = ["quat_retract", "quat_error", "se3_retract", "motion_cross", "eig3", "svd3", "closest_rotation",
+            "argmax", "softmax"]
 # The 12 placements of the table / cost model, index = scope*4 + log2(pack).
 PLACEMENTS = [(s, p) for s in (0, 1, 2) for p in (1, 2, 4, 8)]
 
@@ -89,6 +92,25 @@ _SIGS = {
     "glass_mlp_loss_grad": (_i, [_i, _P, _i, _P, _P, _P, _P, _P, _P, _sz, _P]),
     "glass_mlp_adam": (_i, [_i, _P, _P, _P, _P, _i, _f, _f, _f, _f, _P]),
     "glass_last_device_status": (_i, [_P]),
+    "glass_batched_gemm_ex": (_i, [_i, _i, _i, _i, _i, ctypes.c_float, _P, _i, _ll, _P, _i, _ll, ctypes.c_float,
+                                   _P, _i, _ll, _i, _OPTS, _P]),
+    "glass_riccati_workspace": (ctypes.c_size_t, [_i, _i, _i]),
+    "glass_riccati_gain": (_i, [_i, _i, _P, _ll, _P, _ll, _P, _ll, _P, _ll, _P, _ll, _P, _i, _P, ctypes.c_size_t,
+                                _OPTS, _P]),
+    "glass_riccati_placement": (_i, [_i, _i, _i, _i, ctypes.POINTER(glass_placement)]),
+    "glass_riccati_feasible": (_i, [_i, _i, glass_placement]),
+    "glass_batched_quat_retract": (_i, [_P, _P, _P, _i, _OPTS, _P]),
+    "glass_batched_quat_error": (_i, [_P, _P, _P, _i, _OPTS, _P]),
+    "glass_batched_se3_retract": (_i, [_P, _P, _P, _i, _OPTS, _P]),
+    "glass_batched_motion_cross": (_i, [_P, _P, _P, _i, _OPTS, _P]),
+    "glass_batched_eig3": (_i, [_P, _P, _P, _i, _OPTS, _P]),
+    "glass_batched_svd3": (_i, [_P, _P, _P, _P, _i, _OPTS, _P]),
+    "glass_batched_closest_rotation": (_i, [_P, _P, _i, _OPTS, _P]),
+    "glass_batched_argmax": (_i, [_i, _P, _ll, _P, _i, _OPTS, _P]),
+    "glass_batched_softmax": (_i, [_i, _P, _ll, _P, _ll, _i, _OPTS, _P]),
+    "glass_robo_placement": (_i, [_i, _i, _i, ctypes.POINTER(glass_placement)]),
+    "glass_robo_feasible": (_i, [_i, _i, glass_placement]),
+    "glass_peak_probe": (_i, [_i, _i, _i, _i, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "glass_status_string": (ctypes.c_char_p, [_i]),
     "glass_version": (ctypes.c_char_p, []),
 }
@@ -254,6 +276,87 @@ def glass_mlp_adam(nparams, w, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e
 
 def glass_last_device_status(stream=None):
     return lib().glass_last_device_status(_stream(stream))
+
+
+def glass_batched_gemm_ex(transa, transb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, opts=None,
+                          stream=None):
+    return lib().glass_batched_gemm_ex(transa, transb, m, n, k, alpha, _ptr(A), lda, sA, _ptr(B), ldb, sB, beta,
+                                       _ptr(C), ldc, sC, batch, _opts(opts), _stream(stream))
+
+
+def glass_riccati_workspace(nx, nu, batch):
+    return lib().glass_riccati_workspace(nx, nu, batch)
+
+
+def glass_riccati_gain(nx, nu, A, sA, B, sB, P, sP, R, sR, K, sK, info, batch, ws=None, ws_bytes=0, opts=None,
+                       stream=None):
+    return lib().glass_riccati_gain(nx, nu, _ptr(A), sA, _ptr(B), sB, _ptr(P), sP, _ptr(R), sR, _ptr(K), sK,
+                                    _ptr(info), batch, _ptr(ws), ws_bytes, _opts(opts), _stream(stream))
+
+
+def glass_riccati_placement(nx, nu, batch, composed_ok=True):
+    """Returns (status, (scope, pack))."""
+    out = glass_placement()
+    s = lib().glass_riccati_placement(nx, nu, batch, int(bool(composed_ok)), ctypes.byref(out))
+    return s, (out.scope, out.pack)
+
+
+def glass_riccati_feasible(nx, nu, scope, pack):
+    return bool(lib().glass_riccati_feasible(nx, nu, glass_placement(scope, pack)))
+
+
+def glass_batched_quat_retract(q, d, out, batch, opts=None, stream=None):
+    return lib().glass_batched_quat_retract(_ptr(q), _ptr(d), _ptr(out), batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_quat_error(q1, q2, out, batch, opts=None, stream=None):
+    return lib().glass_batched_quat_error(_ptr(q1), _ptr(q2), _ptr(out), batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_se3_retract(T, xi, out, batch, opts=None, stream=None):
+    return lib().glass_batched_se3_retract(_ptr(T), _ptr(xi), _ptr(out), batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_motion_cross(v, m, out, batch, opts=None, stream=None):
+    return lib().glass_batched_motion_cross(_ptr(v), _ptr(m), _ptr(out), batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_eig3(A, w, V, batch, opts=None, stream=None):
+    return lib().glass_batched_eig3(_ptr(A), _ptr(w), _ptr(V), batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_svd3(M, U, s, V, batch, opts=None, stream=None):
+    return lib().glass_batched_svd3(_ptr(M), _ptr(U), _ptr(s), _ptr(V), batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_closest_rotation(M, R, batch, opts=None, stream=None):
+    return lib().glass_batched_closest_rotation(_ptr(M), _ptr(R), batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_argmax(n, x, sx, idx, batch, opts=None, stream=None):
+    return lib().glass_batched_argmax(n, _ptr(x), sx, _ptr(idx), batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_softmax(n, x, sx, y, sy, batch, opts=None, stream=None):
+    return lib().glass_batched_softmax(n, _ptr(x), sx, _ptr(y), sy, batch, _opts(opts), _stream(stream))
+
+
+def glass_robo_placement(op, n, batch):
+    """Returns (status, (scope, pack))."""
+    out = glass_placement()
+    s = lib().glass_robo_placement(op, n, batch, ctypes.byref(out))
+    return s, (out.scope, out.pack)
+
+
+def glass_robo_feasible(op, n, scope, pack):
+    return bool(lib().glass_robo_feasible(op, n, glass_placement(scope, pack)))
+
+
+def glass_peak_probe(kind, iters, blocks, threads, sink, stream=None):
+    """Launch one pipe-throughput probe; returns (status, flops of the launch)."""
+    f = ctypes.c_double(0.0)
+    st = lib().glass_peak_probe(kind, iters, blocks, threads, _ptr(sink), ctypes.byref(f), _stream(stream))
+    return st, f.value
 
 
 def glass_status_string(s):

@@ -10,6 +10,8 @@
 
 #include "common.cuh"
 #include "placement_table.h"
+#include "riccati_table.h"
+#include "robo_table.h"
 
 namespace glass {
 
@@ -221,6 +223,68 @@ glass_status check_order(int n) {
     if (n < 1) return GLASS_ERR_INVALID_VALUE;
     if (n > 64) return GLASS_ERR_UNSUPPORTED;
     return GLASS_OK;
+}
+
+// ------------------------------------------------- robotics operations
+Placement robo_resolve(int op, int n, int batch) {
+    const int bi = nearest_index(kRoboB, kRoboNumB, batch > 0 ? batch : 1);
+    const Placement pl = decode(kRoboTable[op][bi]);
+    if (feasible_robo(op, n, pl)) return pl;
+    return Placement{SCOPE_THREAD, 1};
+}
+
+glass_status robo_placement_of(int op, int n, int batch, const glass_opts &o, Placement &pl) {
+    if (o.dtype != GLASS_F32 || o.math != GLASS_MATH_FP32 || o.layout != GLASS_LAYOUT_COLMAJOR)
+        return GLASS_ERR_UNSUPPORTED;
+    if (o.placement.scope == GLASS_SCOPE_AUTO) {
+        pl = robo_resolve(op, n, batch);
+        if (o.placement.pack != 0) {
+            if (!valid_pack(o.placement.pack)) return GLASS_ERR_INVALID_VALUE;
+            pl.pack = o.placement.pack;
+        }
+    } else {
+        pl = Placement{o.placement.scope, o.placement.pack == 0 ? 1 : o.placement.pack};
+    }
+    return feasible_robo(op, n, pl) ? GLASS_OK : GLASS_ERR_INVALID_VALUE;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// ------------------------------------------------------- LQR gain placement
+constexpr int kComposedCode = 12;
+
+size_t ric_workspace(int nx, int nu, int batch) {
+    const size_t pb = ((size_t)batch * nx * nu + 63) / 64 * 64;
+    return (pb + (size_t)batch * nu * nu) * 4;
+}
+
+Placement ric_fused_fallback(int nx, int nu, Placement want) {
+    for (int s = want.scope; s <= SCOPE_BLOCK; ++s)
+        for (int pk = want.pack; pk >= 1; pk >>= 1) {
+            const Placement q{s, pk};
+            if (feasible_riccati(nx, nu, q)) return q;
+        }
+    return Placement{SCOPE_BLOCK, 1};
+}
+
+Placement ric_resolve(int nx, int nu, int batch, bool composed_ok) {
+    int best = 0;
+    double bd = 1e300;
+    for (int i = 0; i < kRicNum; ++i) {
+        const double d = fabs(log2((double)kRicNx[i]) - log2((double)nx)) + fabs(log2((double)kRicNu[i]) - log2((double)nu));
+        if (d < bd - 1e-12) { bd = d; best = i; }
+    }
+    const int bi = nearest_index(kRicB, kRicNumB, batch > 0 ? batch : 1);
+    const unsigned char code = kRicTable[best][bi];
+    if (code == kComposedCode) {
+        if (composed_ok) return Placement{GLASS_SCOPE_COMPOSED, 1};
+        return ric_fused_fallback(nx, nu, Placement{SCOPE_WARP, 1});
+    }
+    const Placement pl = decode(code);
+    if (feasible_riccati(nx, nu, pl)) return pl;
+    const Placement q = ric_fused_fallback(nx, nu, pl);
+    if (!feasible_riccati(nx, nu, q) && composed_ok) return Placement{GLASS_SCOPE_COMPOSED, 1};
+    return q;
 }
 
 }  // namespace
@@ -441,6 +505,192 @@ glass_status glass_posv_varsize(int batch, const int *n_dev, const long long *of
     return from_cuda(launch_posv_varsize(batch, n_dev, offA_dev, offB_dev, nrhs, static_cast<float *>(A),
                                          static_cast<float *>(B), info, ws, wpc, status,
                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_batched_gemm_ex(int transa, int transb, int m, int n, int k, float alpha, const void *A, int lda,
+                                   long long sA, const void *B, int ldb, long long sB, float beta, void *C, int ldc,
+                                   long long sC, int batch, const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if ((transa != 0 && transa != 1) || (transb != 0 && transb != 1) || m < 1 || n < 1 || k < 1 || batch < 0)
+        return GLASS_ERR_INVALID_VALUE;
+    if (m > 64 || n > 64 || k > 64) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32 || o.math != GLASS_MATH_FP32 || o.layout != GLASS_LAYOUT_COLMAJOR)
+        return GLASS_ERR_UNSUPPORTED;
+    const int ra = transa ? k : m, ca = transa ? m : k, rb = transb ? n : k, cb = transb ? k : n;
+    if (!operand_ok(A, lda, sA, ra, ca, false, o.layout) || !operand_ok(B, ldb, sB, rb, cb, false, o.layout) ||
+        !operand_ok(C, ldc, sC, m, n, true, o.layout))
+        return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    if (o.placement.scope == GLASS_SCOPE_AUTO) {
+        pl = m * n <= 512 ? Placement{SCOPE_WARP, 4} : Placement{SCOPE_BLOCK, 1};
+        if (o.placement.pack != 0) {
+            if (!valid_pack(o.placement.pack)) return GLASS_ERR_INVALID_VALUE;
+            pl.pack = o.placement.pack;
+        }
+        while (!feasible_gemm_ex(transa, transb, m, n, k, pl) && pl.pack > 1) pl.pack >>= 1;
+    } else {
+        if (o.placement.scope != GLASS_SCOPE_WARP && o.placement.scope != GLASS_SCOPE_BLOCK)
+            return GLASS_ERR_INVALID_VALUE;
+        pl = Placement{o.placement.scope, o.placement.pack == 0 ? 1 : o.placement.pack};
+        if (!valid_pack(pl.pack)) return GLASS_ERR_INVALID_VALUE;
+    }
+    if (!feasible_gemm_ex(transa, transb, m, n, k, pl)) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_gemm_ex(transa, transb, m, n, k, alpha, make_mat(A, lda, sA, ra, ca, o.layout),
+                                    make_mat(B, ldb, sB, rb, cb, o.layout), beta, make_mat(C, ldc, sC, m, n, o.layout),
+                                    batch, pl, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t glass_riccati_workspace(int nx, int nu, int batch) {
+    if (nx < 1 || nu < 1 || nx > 64 || nu > 64 || batch < 0) return 0;
+    return ric_workspace(nx, nu, batch);
+}
+
+glass_status glass_riccati_gain(int nx, int nu, const void *A, long long sA, const void *B, long long sB, const void *P,
+                                long long sP, const void *R, long long sR, void *K, long long sK, int *info, int batch,
+                                void *ws, size_t ws_bytes, const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if (nx < 1 || nu < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (nx > 64 || nu > 64) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32 || o.math != GLASS_MATH_FP32 || o.layout != GLASS_LAYOUT_COLMAJOR)
+        return GLASS_ERR_UNSUPPORTED;
+    if (!A || !B || !P || !R || !K || !info) return GLASS_ERR_INVALID_VALUE;
+    if (sA < 0 || sB < 0 || sP < 0 || sR < 0 || sK < (long long)nu * nx) return GLASS_ERR_INVALID_VALUE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // the composition copies each problem's R: it needs sR >= nu * nu
+    const bool ws_ok = ws != nullptr && ws_bytes >= ric_workspace(nx, nu, batch) &&
+                       (reinterpret_cast<uintptr_t>(ws) & 255) == 0 && sR >= (long long)nu * nu;
+    Placement pl;
+    if (o.placement.scope == GLASS_SCOPE_AUTO) {
+        pl = ric_resolve(nx, nu, batch, ws_ok);
+        if (o.placement.pack != 0 && pl.scope != GLASS_SCOPE_COMPOSED) {
+            if (!valid_pack(o.placement.pack)) return GLASS_ERR_INVALID_VALUE;
+            pl.pack = o.placement.pack;
+        }
+    } else if (o.placement.scope == GLASS_SCOPE_COMPOSED) {
+        if (!ws_ok) return GLASS_ERR_WORKSPACE;
+        pl = Placement{GLASS_SCOPE_COMPOSED, 1};
+    } else {
+        if (o.placement.scope != GLASS_SCOPE_WARP && o.placement.scope != GLASS_SCOPE_BLOCK)
+            return GLASS_ERR_INVALID_VALUE;
+        pl = Placement{o.placement.scope, o.placement.pack == 0 ? 1 : o.placement.pack};
+        if (!valid_pack(pl.pack)) return GLASS_ERR_INVALID_VALUE;
+    }
+    if (pl.scope == GLASS_SCOPE_COMPOSED) {
+        // one call per primitive, each with its own measured placement
+        float *PB = static_cast<float *>(ws);
+        float *S = PB + ((size_t)batch * nx * nu + 63) / 64 * 64;
+        const glass_opts a = kDefaultOpts;
+        const long long sPB = (long long)nx * nu, sS = (long long)nu * nu;
+        GLASS_TRY(glass_batched_gemm(nx, nu, nx, P, nx, sP, B, nx, sB, PB, nx, sPB, batch, &a, stream));
+        if (cudaMemcpy2DAsync(S, (size_t)sS * 4, R, (size_t)sR * 4, (size_t)sS * 4, (size_t)batch,
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return GLASS_ERR_CUDA;
+        GLASS_TRY(glass_batched_gemm_ex(1, 0, nu, nu, nx, 1.f, B, nx, sB, PB, nx, sPB, 1.f, S, nu, sS, batch, &a,
+                                        stream));
+        GLASS_TRY(glass_batched_gemm_ex(1, 0, nu, nx, nx, 1.f, PB, nx, sPB, A, nx, sA, 0.f, K, nu, sK, batch, &a,
+                                        stream));
+        return glass_batched_posv(nu, nx, S, nu, sS, K, nu, sK, info, batch, &a, stream);
+    }
+    if (!feasible_riccati(nx, nu, pl)) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_riccati(nx, nu, static_cast<const float *>(A), sA, static_cast<const float *>(B), sB,
+                                    static_cast<const float *>(P), sP, static_cast<const float *>(R), sR,
+                                    static_cast<float *>(K), sK, info, batch, pl, st));
+}
+
+glass_status glass_riccati_placement(int nx, int nu, int batch, int composed_ok, glass_placement *out) {
+    if (out == nullptr || nx < 1 || nu < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (nx > 64 || nu > 64) return GLASS_ERR_UNSUPPORTED;
+    const Placement pl = ric_resolve(nx, nu, batch, composed_ok != 0);
+    out->scope = pl.scope;
+    out->pack = pl.pack;
+    return GLASS_OK;
+}
+
+int glass_riccati_feasible(int nx, int nu, glass_placement p) {
+    return feasible_riccati(nx, nu, Placement{p.scope, p.pack}) ? 1 : 0;
+}
+
+#define GLASS_ROBO_ENTRY(op, n, a, b, sa, o1, o2, o3, so, idx)                                           \
+    const glass_opts &o = opts_or_default(opts);                                                          \
+    GLASS_TRY(check_common(o));                                                                           \
+    if (batch < 0) return GLASS_ERR_INVALID_VALUE;                                                        \
+    if (batch == 0) return GLASS_OK;                                                                      \
+    Placement pl;                                                                                         \
+    GLASS_TRY(robo_placement_of(op, n, batch, o, pl));                                                    \
+    return from_cuda(launch_robo(op, n, static_cast<const float *>(a), static_cast<const float *>(b), sa,  \
+                                 static_cast<float *>(o1), static_cast<float *>(o2), static_cast<float *>(o3), \
+                                 so, idx, batch, pl, reinterpret_cast<cudaStream_t>(stream)))
+
+glass_status glass_batched_quat_retract(const void *q, const void *d, void *out, int batch, const glass_opts *opts,
+                                        glass_stream_t stream) {
+    if (batch > 0 && (!q || !d || !out || !aligned16(q) || !aligned16(out))) return GLASS_ERR_INVALID_VALUE;
+    GLASS_ROBO_ENTRY(ROBO_QUAT_RETRACT, 0, q, d, 0, out, nullptr, nullptr, 0, nullptr);
+}
+
+glass_status glass_batched_quat_error(const void *q1, const void *q2, void *out, int batch, const glass_opts *opts,
+                                      glass_stream_t stream) {
+    if (batch > 0 && (!q1 || !q2 || !out || !aligned16(q1) || !aligned16(q2))) return GLASS_ERR_INVALID_VALUE;
+    GLASS_ROBO_ENTRY(ROBO_QUAT_ERROR, 0, q1, q2, 0, out, nullptr, nullptr, 0, nullptr);
+}
+
+glass_status glass_batched_se3_retract(const void *T, const void *xi, void *out, int batch, const glass_opts *opts,
+                                       glass_stream_t stream) {
+    if (batch > 0 && (!T || !xi || !out || !aligned16(T) || !aligned16(out))) return GLASS_ERR_INVALID_VALUE;
+    GLASS_ROBO_ENTRY(ROBO_SE3_RETRACT, 0, T, xi, 0, out, nullptr, nullptr, 0, nullptr);
+}
+
+glass_status glass_batched_motion_cross(const void *v, const void *m, void *out, int batch, const glass_opts *opts,
+                                        glass_stream_t stream) {
+    if (batch > 0 && (!v || !m || !out)) return GLASS_ERR_INVALID_VALUE;
+    GLASS_ROBO_ENTRY(ROBO_MOTION_CROSS, 0, v, m, 0, out, nullptr, nullptr, 0, nullptr);
+}
+
+glass_status glass_batched_eig3(const void *A, void *w, void *V, int batch, const glass_opts *opts,
+                                glass_stream_t stream) {
+    if (batch > 0 && (!A || !w || !V)) return GLASS_ERR_INVALID_VALUE;
+    GLASS_ROBO_ENTRY(ROBO_EIG3, 0, A, nullptr, 0, w, V, nullptr, 0, nullptr);
+}
+
+glass_status glass_batched_svd3(const void *M, void *U, void *sv, void *V, int batch, const glass_opts *opts,
+                                glass_stream_t stream) {
+    if (batch > 0 && (!M || !U || !sv || !V)) return GLASS_ERR_INVALID_VALUE;
+    GLASS_ROBO_ENTRY(ROBO_SVD3, 0, M, nullptr, 0, U, sv, V, 0, nullptr);
+}
+
+glass_status glass_batched_closest_rotation(const void *M, void *R, int batch, const glass_opts *opts,
+                                            glass_stream_t stream) {
+    if (batch > 0 && (!M || !R)) return GLASS_ERR_INVALID_VALUE;
+    GLASS_ROBO_ENTRY(ROBO_CLOSEST_ROTATION, 0, M, nullptr, 0, R, nullptr, nullptr, 0, nullptr);
+}
+
+glass_status glass_batched_argmax(int n, const void *x, long long sx, int *idx, int batch, const glass_opts *opts,
+                                  glass_stream_t stream) {
+    if (n < 1 || (batch > 0 && (!x || !idx || sx < 0 || (batch > 1 && sx < n)))) return GLASS_ERR_INVALID_VALUE;
+    GLASS_ROBO_ENTRY(ROBO_ARGMAX, n, x, nullptr, sx, nullptr, nullptr, nullptr, 0, idx);
+}
+
+glass_status glass_batched_softmax(int n, const void *x, long long sx, void *y, long long sy, int batch,
+                                   const glass_opts *opts, glass_stream_t stream) {
+    if (n < 1 || (batch > 0 && (!x || !y || sx < 0 || sy < n))) return GLASS_ERR_INVALID_VALUE;
+    GLASS_ROBO_ENTRY(ROBO_SOFTMAX, n, x, nullptr, sx, y, nullptr, nullptr, sy, nullptr);
+}
+#undef GLASS_ROBO_ENTRY
+
+glass_status glass_robo_placement(int op, int n, int batch, glass_placement *out) {
+    if (out == nullptr || op < 0 || op >= GLASS_ROBO_NUM_OPS || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    const Placement pl = robo_resolve(op, n < 1 ? 1 : n, batch);
+    out->scope = pl.scope;
+    out->pack = pl.pack;
+    return GLASS_OK;
+}
+
+int glass_robo_feasible(int op, int n, glass_placement p) {
+    if (op < 0 || op >= GLASS_ROBO_NUM_OPS) return 0;
+    return feasible_robo(op, n, Placement{p.scope, p.pack}) ? 1 : 0;
 }
 
 glass_status glass_get_placement(int op, int n, int k, int batch, int dtype, int use_learned, glass_placement *out) {

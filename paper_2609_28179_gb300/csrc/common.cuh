@@ -88,6 +88,12 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
+// 4-byte form (through L1): any float-aligned element, so strided and
+// unaligned operands can be staged without registers as well.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
@@ -275,6 +281,30 @@ size_t varsize_workspace(int batch);
 cudaError_t launch_posv_varsize(int batch, const int *n_dev, const long long *offA,
                                 const long long *offB, int nrhs, float *A, float *B, int *info,
                                 void *ws, int warps_per_cta, unsigned *status, cudaStream_t st);
+// k_riccati.cu
+bool feasible_gemm_ex(int ta, int tb, int m, int n, int k, Placement pl);
+cudaError_t launch_gemm_ex(int ta, int tb, int m, int n, int k, float alpha, Mat A, Mat B, float beta, Mat C,
+                           int batch, Placement pl, cudaStream_t st);
+size_t riccati_floats(int nx, int nu);
+bool feasible_riccati(int nx, int nu, Placement pl);
+cudaError_t launch_riccati(int nx, int nu, const float *A, long long sA, const float *B, long long sB,
+                           const float *P, long long sP, const float *R, long long sR, float *K, long long sK,
+                           int *info, int batch, Placement pl, cudaStream_t st);
+// k_robo.cu (op = glass_robo_op)
+enum RoboOp {
+    ROBO_QUAT_RETRACT = GLASS_ROBO_QUAT_RETRACT,
+    ROBO_QUAT_ERROR = GLASS_ROBO_QUAT_ERROR,
+    ROBO_SE3_RETRACT = GLASS_ROBO_SE3_RETRACT,
+    ROBO_MOTION_CROSS = GLASS_ROBO_MOTION_CROSS,
+    ROBO_EIG3 = GLASS_ROBO_EIG3,
+    ROBO_SVD3 = GLASS_ROBO_SVD3,
+    ROBO_CLOSEST_ROTATION = GLASS_ROBO_CLOSEST_ROTATION,
+    ROBO_ARGMAX = GLASS_ROBO_ARGMAX,
+    ROBO_SOFTMAX = GLASS_ROBO_SOFTMAX
+};
+bool feasible_robo(int op, int n, Placement pl);
+cudaError_t launch_robo(int op, int n, const float *a, const float *b, long long sa, float *o1, float *o2, float *o3,
+                        long long so, int *idx, int batch, Placement pl, cudaStream_t st);
 // k_mlp.cu
 size_t mlp_workspace(int rows);
 cudaError_t launch_mlp_forward(int din, const float *w, int rows, const float *X, float *Y,

@@ -9,9 +9,10 @@
 //      the same diagonal rules as every other scope (Sec. III-B
 //      factorizations; LAPACK info);
 //   2. trailing update A22 -= L21 L21^T on the tensor cores: mma.sync
-//      m16n8k8 TF32 over the 16x8 tiles of A22 that meet its lower
-//      triangle, each product split 3xTF32 (a = a_hi + a_lo; hi*hi + hi*lo +
-//      lo*hi) so the update keeps FP32-level accuracy; FP32 accumulation.
+//      m16n8k8 TF32 over the 16x16 tiles of A22 that meet its lower
+//      triangle (two independent 16x8 accumulators), each product split
+//      3xTF32 (a = a_hi + a_lo; hi*hi + hi*lo + lo*hi) so the update keeps
+//      FP32-level accuracy; FP32 accumulation.
 // Panel and tile loops run at run time, so the code stays small (the fully
 // unrolled register form of the 64-column factorization spends a quarter of
 // its stalls on instruction fetch).  Rows and columns from n to NMAX are
@@ -47,68 +48,174 @@ struct Shape {
     static constexpr int R = NMAX / 32;  // rows per lane
 };
 
-// In-place Cholesky of the lower triangle of As (order n <= NMAX); dv[j]
-// receives 1 / l_jj.  Returns info (uniform).
-template <int NMAX>
-__device__ __forceinline__ int potrf(float *As, int n, float *dv, bool fp64diag) {
+// Stage the column-major n x n operand at ga (leading dimension lda) into As
+// (pitch LD) with cp.async copies, every copy of the lane in flight at once:
+// 16-byte copies when n and lda are multiples of 4 and ga is 16-byte aligned,
+// 4-byte copies otherwise.  Everything outside the operand is zero; LOWER
+// skips what lies above the diagonal (16-byte groups wholly above it in the
+// vector form) and leaves it zero or as read -- it is never used.  Ends with
+// the copies complete and visible to the warp.
+template <int NMAX, bool LOWER>
+__device__ __forceinline__ void stage(float *As, const float *ga, long long lda, int n) {
     constexpr int LD = Shape<NMAX>::LD;
     constexpr int R = Shape<NMAX>::R;
+    const int lane = threadIdx.x & 31;
+    const bool vec = (n & 3) == 0 && (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(ga) & 15) == 0;
+    if (vec) {
+#pragma unroll 4
+        for (int e = lane; e < NMAX * NMAX / 4; e += 32) {
+            const int k = e / (NMAX / 4), r = 4 * (e % (NMAX / 4));
+            float *d = As + k * LD + r;
+            if (k < n && r < n && (!LOWER || r + 3 >= k)) cp_async16(d, ga + (long long)k * lda + r);
+            else *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+#pragma unroll 4
+        for (int k = 0; k < NMAX; ++k)
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = lane + 32 * q;
+                float *d = As + k * LD + i;
+                if (k < n && i < n && (!LOWER || i >= k)) cp_async4(d, ga + (long long)k * lda + i);
+                else *d = 0.f;
+            }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+}
+
+// Write the n x n result in As back to ga (LOWER: the lower triangle only,
+// the rest of ga keeps its contents), 16-byte stores where whole 16-byte
+// groups are written and the operand is aligned as for stage().
+template <int NMAX, bool LOWER>
+__device__ __forceinline__ void unstage(float *ga, long long lda, const float *As, int n) {
+    constexpr int LD = Shape<NMAX>::LD;
+    constexpr int R = Shape<NMAX>::R;
+    const int lane = threadIdx.x & 31;
+    const bool vec = (n & 3) == 0 && (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(ga) & 15) == 0;
+    float *wg = opaque(ga);
+    if (vec) {
+#pragma unroll 4
+        for (int e = lane; e < NMAX * NMAX / 4; e += 32) {
+            const int k = e / (NMAX / 4), r = 4 * (e % (NMAX / 4));
+            if (k >= n || r >= n || (LOWER && r + 3 < k)) continue;
+            const float4 v = *reinterpret_cast<const float4 *>(As + k * LD + r);
+            float *d = wg + (long long)k * lda + r;
+            if (!LOWER || r >= k) {
+                __stcs(reinterpret_cast<float4 *>(d), v);
+            } else {  // the group holding the diagonal
+                if (r >= k) d[0] = v.x;
+                if (r + 1 >= k) d[1] = v.y;
+                if (r + 2 >= k) d[2] = v.z;
+                d[3] = v.w;
+            }
+        }
+    } else {
+#pragma unroll 4
+        for (int k = 0; k < NMAX; ++k)
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = lane + 32 * q;
+                if (k < n && i < n && (!LOWER || i >= k)) wg[(long long)k * lda + i] = As[k * LD + i];
+            }
+    }
+}
+
+// Panel c0 of the factorization (rows held in slots q >= QLO; the slots
+// below hold rows above the panel only), right-looking in registers.  Per
+// column the raw entries of rows c0..c0+15 are published to a 16-float
+// shared segment (two, alternating) and read back by every lane as 16-byte
+// broadcasts: the pivot comes from there and l_kj = a_kj / l_jj is formed
+// in each lane, so the update of column k is one multiply and one fused
+// multiply-add per row.  Rows above the diagonal are updated too -- their
+// values are never read and never written back.  The lower part is written
+// back and mirrored, transposed, into the unused upper triangle
+// (As[i * LD + r] = l_ir for r < i), where the backward solve reads rows of
+// L as contiguous columns.
+template <int NMAX, int QLO>
+__device__ __forceinline__ void panel(float *As, int n, int c0, float *dv, float *bc, bool fp64diag, int &info) {
+    constexpr int LD = Shape<NMAX>::LD;
+    constexpr int R = Shape<NMAX>::R;
+    const int lane = threadIdx.x & 31;
+    float p[R][16];
+#pragma unroll
+    for (int q = QLO; q < R; ++q)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) p[q][k] = As[(c0 + k) * LD + lane + 32 * q];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int cj = c0 + j;
+        if (cj < n) {
+            float *buf = bc + 16 * (j & 1);
+#pragma unroll
+            for (int q = QLO; q < R; ++q) {
+                const int i = lane + 32 * q;
+                if (i >= c0 && i < c0 + 16) buf[i - c0] = p[q][j];
+            }
+            __syncwarp();
+            float s[16];
+            {
+                const float4 *b4 = reinterpret_cast<const float4 *>(buf);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const float4 v = b4[m];
+                    s[4 * m] = v.x;
+                    s[4 * m + 1] = v.y;
+                    s[4 * m + 2] = v.z;
+                    s[4 * m + 3] = v.w;
+                }
+            }
+            const float d = s[j];
+            if (!(d > 0.f) && info == 0) info = cj + 1;
+            float l, r;
+            chol_diag(d, fp64diag, l, r);
+            if (lane == 0) dv[cj] = r;
+#pragma unroll
+            for (int q = QLO; q < R; ++q) p[q][j] = (lane + 32 * q == cj) ? l : p[q][j] * r;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {  // fixed range: keeps p[][] in registers
+                if (k > j) {
+                    const float lkj = s[k] * r;
+#pragma unroll
+                    for (int q = QLO; q < R; ++q) p[q][k] = fmaf(-p[q][j], lkj, p[q][k]);
+                }
+            }
+        }
+    }
+    float *wp = opaque(As);
+#pragma unroll
+    for (int q = QLO; q < R; ++q) {
+        const int i = lane + 32 * q;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (i >= c0 + k && i < n) wp[(c0 + k) * LD + i] = p[q][k];
+        if (i >= c0 + 16 && i < n) {
+            float4 *dst = reinterpret_cast<float4 *>(wp + i * LD + c0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dst[k] = make_float4(p[q][4 * k], p[q][4 * k + 1], p[q][4 * k + 2], p[q][4 * k + 3]);
+        } else if (i > c0 && i < n) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (c0 + k < i) wp[i * LD + c0 + k] = p[q][k];
+        }
+    }
+    __syncwarp();
+}
+
+// In-place Cholesky of the lower triangle of As (order n <= NMAX); dv[j]
+// receives 1 / l_jj; bc is 32 floats (16-byte aligned) of per-warp scratch.
+// Returns info (uniform).
+template <int NMAX>
+__device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, bool fp64diag) {
+    constexpr int LD = Shape<NMAX>::LD;
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     int info = 0;
     for (int c0 = 0; c0 < n; c0 += 16) {
         // ---- 1. panel on the SIMT pipe
-        float p[R][16];
-#pragma unroll
-        for (int q = 0; q < R; ++q)
-#pragma unroll
-            for (int k = 0; k < 16; ++k) p[q][k] = As[(c0 + k) * LD + lane + 32 * q];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int cj = c0 + j;
-            if (cj < n) {
-                const int qj = cj >> 5;
-                float dsel = p[0][j];
-#pragma unroll
-                for (int q = 1; q < R; ++q)
-                    if (qj == q) dsel = p[q][j];
-                const float d = __shfl_sync(GLASS_FULL_MASK, dsel, cj & 31);
-                if (!(d > 0.f) && info == 0) info = cj + 1;
-                float l, r;
-                chol_diag(d, fp64diag, l, r);
-                if (lane == 0) dv[cj] = r;
-#pragma unroll
-                for (int q = 0; q < R; ++q) {
-                    const int i = lane + 32 * q;
-                    if (i == cj) p[q][j] = l;
-                    else if (i > cj) p[q][j] *= r;
-                }
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {  // fixed range: keeps p[][] in registers
-                    const int ck = c0 + k;
-                    if (k > j && ck < n) {
-                        const int qk = ck >> 5;
-                        float sel = p[0][j];
-#pragma unroll
-                        for (int q = 1; q < R; ++q)
-                            if (qk == q) sel = p[q][j];
-                        const float lkj = __shfl_sync(GLASS_FULL_MASK, sel, ck & 31);
-#pragma unroll
-                        for (int q = 0; q < R; ++q)
-                            if (lane + 32 * q >= ck) p[q][k] = fmaf(-p[q][j], lkj, p[q][k]);
-                    }
-                }
-            }
-        }
+        if (c0 < 32) panel<NMAX, 0>(As, n, c0, dv, bc, fp64diag, info);
+        else panel<NMAX, 1>(As, n, c0, dv, bc, fp64diag, info);
+        // ---- 2. trailing update on the tensor cores, 16 x 16 per step
         float *wp = opaque(As);
-#pragma unroll
-        for (int q = 0; q < R; ++q)
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int i = lane + 32 * q;
-                if (i >= c0 + k && i < n) wp[(c0 + k) * LD + i] = p[q][k];
-            }
-        __syncwarp();
-        // ---- 2. trailing update on the tensor cores
         const int r0 = c0 + 16;
         for (int R0 = r0; R0 < n; R0 += 16) {
             unsigned ah[2][4], al[2][4];
@@ -120,23 +227,42 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, bool fp64diag)
                 split(-col[4 * LD + R0 + g], ah[kk][2], al[kk][2]);
                 split(-col[4 * LD + R0 + g + 8], ah[kk][3], al[kk][3]);
             }
-            for (int C0 = r0; C0 < n && C0 <= R0 + 15; C0 += 8) {
-                float *c = As + (C0 + 2 * t) * LD + R0 + g;
-                float acc[4] = {c[0], c[LD], c[8], c[LD + 8]};
+            for (int C0 = r0; C0 <= R0; C0 += 16) {
+                const bool two = C0 + 8 < n;
+                float *c = wp + (C0 + 2 * t) * LD + R0 + g;
+                float a0[4] = {c[0], c[LD], c[8], c[LD + 8]};
+                float a1[4] = {0.f, 0.f, 0.f, 0.f};
+                if (two) {
+                    a1[0] = c[8 * LD];
+                    a1[1] = c[9 * LD];
+                    a1[2] = c[8 * LD + 8];
+                    a1[3] = c[9 * LD + 8];
+                }
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {
                     const float *col = As + (c0 + 8 * kk + t) * LD;
-                    unsigned bh[2], bl[2];
-                    split(col[C0 + g], bh[0], bl[0]);
-                    split(col[4 * LD + C0 + g], bh[1], bl[1]);
-                    mma_tf32(acc, al[kk], bh);
-                    mma_tf32(acc, ah[kk], bl);
-                    mma_tf32(acc, ah[kk], bh);
+                    unsigned bh0[2], bl0[2], bh1[2], bl1[2];
+                    split(col[C0 + g], bh0[0], bl0[0]);
+                    split(col[4 * LD + C0 + g], bh0[1], bl0[1]);
+                    split(col[C0 + 8 + g], bh1[0], bl1[0]);
+                    split(col[4 * LD + C0 + 8 + g], bh1[1], bl1[1]);
+                    mma_tf32(a0, al[kk], bh0);
+                    mma_tf32(a1, al[kk], bh1);
+                    mma_tf32(a0, ah[kk], bl0);
+                    mma_tf32(a1, ah[kk], bl1);
+                    mma_tf32(a0, ah[kk], bh0);
+                    mma_tf32(a1, ah[kk], bh1);
                 }
-                c[0] = acc[0];
-                c[LD] = acc[1];
-                c[8] = acc[2];
-                c[LD + 8] = acc[3];
+                c[0] = a0[0];
+                c[LD] = a0[1];
+                c[8] = a0[2];
+                c[LD + 8] = a0[3];
+                if (two) {
+                    c[8 * LD] = a1[0];
+                    c[9 * LD] = a1[1];
+                    c[8 * LD + 8] = a1[2];
+                    c[9 * LD + 8] = a1[3];
+                }
             }
         }
         __syncwarp();
@@ -145,19 +271,23 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, bool fp64diag)
 }
 
 // One right-hand side held like the rows (x[q] = row lane + 32q) against L
-// in shared memory: x <- L^{-1} x, then x <- L^{-T} x.
+// in shared memory: x <- L^{-1} x down the columns of L, then x <- L^{-T} x
+// down the columns of the mirrored upper triangle (both column-oriented: one
+// broadcast and one fused multiply-add per row and step, no reductions).
 template <int NMAX>
 __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&x)[Shape<NMAX>::R], int n) {
     constexpr int LD = Shape<NMAX>::LD;
     constexpr int R = Shape<NMAX>::R;
     const int lane = threadIdx.x & 31;
-    for (int i = 0; i < n; ++i) {
-        const int qi = i >> 5;
-        float sel = x[0];
+    auto get = [&](int i) {
+        float s = x[0];
 #pragma unroll
         for (int q = 1; q < R; ++q)
-            if (qi == q) sel = x[q];
-        const float yi = __shfl_sync(GLASS_FULL_MASK, sel, i & 31) * dv[i];
+            if ((i >> 5) == q) s = x[q];
+        return __shfl_sync(GLASS_FULL_MASK, s, i & 31);
+    };
+    for (int i = 0; i < n; ++i) {
+        const float yi = get(i) * dv[i];
         const float *col = As + i * LD;
 #pragma unroll
         for (int q = 0; q < R; ++q) {
@@ -167,23 +297,14 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
         }
     }
     for (int i = n - 1; i >= 0; --i) {
+        const float xi = get(i) * dv[i];
         const float *col = As + i * LD;
-        float part = 0.f;
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int row = lane + 32 * q;
-            if (row > i && row < n) part = fmaf(col[row], x[q], part);
+            if (row == i) x[q] = xi;
+            else if (row < i) x[q] = fmaf(-col[row], xi, x[q]);
         }
-        const float s = warp_sum(part);
-        const int qi = i >> 5;
-        float sel = x[0];
-#pragma unroll
-        for (int q = 1; q < R; ++q)
-            if (qi == q) sel = x[q];
-        const float xi = (__shfl_sync(GLASS_FULL_MASK, sel, i & 31) - s) * dv[i];
-#pragma unroll
-        for (int q = 0; q < R; ++q)
-            if (lane + 32 * q == i) x[q] = xi;
     }
 }
 

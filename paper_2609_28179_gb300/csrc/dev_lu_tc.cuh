@@ -1,0 +1,289 @@
+// dev_lu_tc.cuh -- warp-scope blocked LU with partial pivoting and
+// tensor-core trailing updates, for orders 33..64.
+//
+// One warp owns one problem in its shared memory (column-major, pitch
+// LD = NMAX + 8, rows and columns beyond n zero).  Per 16-column panel:
+//   1. the panel (rows c0..n-1) is factored in registers, row i in lane
+//      i % 32; the pivot of column j is the largest |a_ij| among the rows not
+//      yet eliminated, the smallest current row index on ties, and rows never
+//      move inside the panel -- only their logical positions change (the same
+//      rule and result as explicit interchanges);
+//   2. the rows c0..n-1 of every other column, and the record of which
+//      original row each logical row holds, are permuted to the panel's final
+//      order, so logical and physical rows agree again (the interchanges
+//      LAPACK applies to the columns left and right of a panel);
+//   3. U12 = L11^{-1} A12 (unit lower, one column per lane);
+//   4. A22 -= L21 U12 on the tensor cores: mma.sync m16n8k8, 3xTF32 split,
+//      FP32 accumulation, two independent accumulator tiles per step.
+// Once c0 >= 32 the rows held in the first register slot are all eliminated,
+// so the panel and the interchanges run on the second slot only (QLO = 1).
+// ipiv is produced in sequential-interchange form (Sec. III-B
+// factorizations; the xGETF2 step order of the oracle), info on the first
+// exactly zero pivot.
+#pragma once
+
+#include "dev_chol_tc.cuh"
+
+namespace glass {
+namespace tclu {
+
+using tcwarp::mma_tf32;
+using tcwarp::split;
+
+template <int NMAX>
+struct Shape {
+    static constexpr int LD = NMAX + 8;
+    static constexpr int R = NMAX / 32;
+};
+
+// Steps 1 and 2 for the panel at c0; rows held in slots q >= QLO.
+template <int NMAX, int QLO>
+__device__ __forceinline__ void panel(float *As, int *prow, int n, int c0, int *ipiv_s, float *dv, int &info) {
+    constexpr int LD = Shape<NMAX>::LD;
+    constexpr int R = Shape<NMAX>::R;
+    const int lane = threadIdx.x & 31;
+    float p[R][16];
+    int pos[R];
+    bool done[R];
+#pragma unroll
+    for (int q = QLO; q < R; ++q) {
+        const int row = lane + 32 * q;
+        pos[q] = row;
+        done[q] = row < c0 || row >= n;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) p[q][k] = As[(c0 + k) * LD + row];
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int cj = c0 + j;
+        if (cj < n) {
+            // this lane's candidate: largest |a|, then smallest position
+            unsigned key = 0, kpos = 0xffffffffu;
+            int kq = QLO;
+#pragma unroll
+            for (int q = QLO; q < R; ++q) {
+                if (!done[q]) {
+                    const unsigned kk = __float_as_uint(fabsf(p[q][j])) + 1u;
+                    if (kk > key || (kk == key && (unsigned)pos[q] < kpos)) {
+                        key = kk;
+                        kpos = pos[q];
+                        kq = q;
+                    }
+                }
+            }
+            const unsigned kmax = __reduce_max_sync(GLASS_FULL_MASK, key);
+            unsigned tie = __ballot_sync(GLASS_FULL_MASK, key == kmax);
+            if (__popc(tie) > 1) {
+                const unsigned pmin = __reduce_min_sync(GLASS_FULL_MASK, key == kmax ? kpos : 0xffffffffu);
+                tie = __ballot_sync(GLASS_FULL_MASK, key == kmax && kpos == pmin);
+            }
+            const int wl = __ffs(tie) - 1;
+            const unsigned packed = __shfl_sync(GLASS_FULL_MASK, (kpos << 4) | (unsigned)kq, wl);
+            const int ppos = (int)(packed >> 4), wq = (int)(packed & 15u);
+#pragma unroll
+            for (int q = QLO; q < R; ++q) {
+                if (pos[q] == cj) pos[q] = ppos;
+                if (q == wq && lane == wl) {
+                    pos[q] = cj;
+                    done[q] = true;
+                }
+            }
+            float sel = p[QLO][j];
+#pragma unroll
+            for (int q = QLO + 1; q < R; ++q)
+                if (wq == q) sel = p[q][j];
+            const float pv = __shfl_sync(GLASS_FULL_MASK, sel, wl);
+            const float rc = pv != 0.f ? 1.0f / pv : 0.f;
+            if (lane == 0) {
+                ipiv_s[cj] = ppos;
+                dv[cj] = rc;
+            }
+            if (pv == 0.f) {
+                if (info == 0) info = cj + 1;
+                continue;
+            }
+            float m[R];
+#pragma unroll
+            for (int q = QLO; q < R; ++q) {
+                m[q] = p[q][j] * rc;
+                if (!done[q]) p[q][j] = m[q];
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {  // fixed range: keeps p[][] in registers
+                if (k > j) {
+                    float s = p[QLO][k];
+#pragma unroll
+                    for (int q = QLO + 1; q < R; ++q)
+                        if (wq == q) s = p[q][k];
+                    const float pk = __shfl_sync(GLASS_FULL_MASK, s, wl);
+#pragma unroll
+                    for (int q = QLO; q < R; ++q)
+                        if (!done[q]) p[q][k] = fmaf(-m[q], pk, p[q][k]);
+                }
+            }
+        }
+    }
+    // ---- 2. panel to its logical rows; permute the other columns and prow
+    int pr[R];
+#pragma unroll
+    for (int q = QLO; q < R; ++q) pr[q] = prow[lane + 32 * q];
+    __syncwarp();
+    float *wp = opaque(As);
+#pragma unroll
+    for (int q = QLO; q < R; ++q) {
+        const int row = lane + 32 * q;
+        if (row >= c0 && row < n) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) wp[(c0 + k) * LD + pos[q]] = p[q][k];
+            prow[pos[q]] = pr[q];
+        }
+    }
+    for (int cb = 0; cb < n; cb += 16) {
+        if (cb == c0) continue;
+        float v[R][16];
+#pragma unroll
+        for (int q = QLO; q < R; ++q)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[q][k] = As[(cb + k) * LD + lane + 32 * q];
+        __syncwarp();
+#pragma unroll
+        for (int q = QLO; q < R; ++q) {
+            const int row = lane + 32 * q;
+            if (row >= c0 && row < n && pos[q] != row)
+#pragma unroll
+                for (int k = 0; k < 16; ++k) wp[(cb + k) * LD + pos[q]] = v[q][k];
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+}
+
+// In-place LU of As (order n <= NMAX).  prow[i] (initially i) receives the
+// original row held by logical row i; ipiv_s the interchanges, dv[j] = 1/u_jj.
+template <int NMAX>
+__device__ __forceinline__ int getrf(float *As, int n, int *prow, int *ipiv_s, float *dv) {
+    constexpr int LD = Shape<NMAX>::LD;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    int info = 0;
+    for (int c0 = 0; c0 < n; c0 += 16) {
+        if (c0 < 32) panel<NMAX, 0>(As, prow, n, c0, ipiv_s, dv, info);
+        else panel<NMAX, 1>(As, prow, n, c0, ipiv_s, dv, info);
+        float *wp = opaque(As);
+        // ---- 3. U12 = L11^{-1} A12, one column per lane
+        for (int c = c0 + 16 + lane; c < n; c += 32) {
+            float x[16];
+            const float4 *src = reinterpret_cast<const float4 *>(As + c * LD + c0);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float4 v4 = src[r];
+                x[4 * r] = v4.x;
+                x[4 * r + 1] = v4.y;
+                x[4 * r + 2] = v4.z;
+                x[4 * r + 3] = v4.w;
+            }
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const float *lcol = As + (c0 + r) * LD + c0;
+#pragma unroll
+                for (int s = 0; s < 16; ++s)
+                    if (s > r) x[s] = fmaf(-lcol[s], x[r], x[s]);
+            }
+            float4 *dst = reinterpret_cast<float4 *>(wp + c * LD + c0);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) dst[r] = make_float4(x[4 * r], x[4 * r + 1], x[4 * r + 2], x[4 * r + 3]);
+        }
+        __syncwarp();
+        // ---- 4. A22 -= L21 U12 on the tensor cores, 16 x 16 per step
+        const int r0 = c0 + 16;
+        for (int R0 = r0; R0 < n; R0 += 16) {
+            unsigned ah[2][4], al[2][4];
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const float *col = As + (c0 + 8 * kk + t) * LD;
+                split(-col[R0 + g], ah[kk][0], al[kk][0]);
+                split(-col[R0 + g + 8], ah[kk][1], al[kk][1]);
+                split(-col[4 * LD + R0 + g], ah[kk][2], al[kk][2]);
+                split(-col[4 * LD + R0 + g + 8], ah[kk][3], al[kk][3]);
+            }
+            for (int C0 = r0; C0 < n; C0 += 16) {
+                const bool two = C0 + 8 < n;
+                float *c = wp + (C0 + 2 * t) * LD + R0 + g;
+                float a0[4] = {c[0], c[LD], c[8], c[LD + 8]};
+                float a1[4] = {0.f, 0.f, 0.f, 0.f};
+                if (two) {
+                    a1[0] = c[8 * LD];
+                    a1[1] = c[9 * LD];
+                    a1[2] = c[8 * LD + 8];
+                    a1[3] = c[9 * LD + 8];
+                }
+                const float *u0 = As + (C0 + g) * LD + c0;
+                const float *u1 = u0 + 8 * LD;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    unsigned bh0[2], bl0[2], bh1[2], bl1[2];
+                    split(u0[8 * kk + t], bh0[0], bl0[0]);
+                    split(u0[8 * kk + t + 4], bh0[1], bl0[1]);
+                    split(u1[8 * kk + t], bh1[0], bl1[0]);
+                    split(u1[8 * kk + t + 4], bh1[1], bl1[1]);
+                    mma_tf32(a0, al[kk], bh0);
+                    mma_tf32(a1, al[kk], bh1);
+                    mma_tf32(a0, ah[kk], bl0);
+                    mma_tf32(a1, ah[kk], bl1);
+                    mma_tf32(a0, ah[kk], bh0);
+                    mma_tf32(a1, ah[kk], bh1);
+                }
+                c[0] = a0[0];
+                c[LD] = a0[1];
+                c[8] = a0[2];
+                c[LD + 8] = a0[3];
+                if (two) {
+                    c[8 * LD] = a1[0];
+                    c[9 * LD] = a1[1];
+                    c[8 * LD + 8] = a1[2];
+                    c[9 * LD + 8] = a1[3];
+                }
+            }
+        }
+        __syncwarp();
+    }
+    return info;
+}
+
+// One right-hand side already gathered into logical row order (x[q] = row
+// lane + 32q of P b): unit-lower forward and column-oriented upper backward
+// sweeps against the packed factor.
+template <int NMAX>
+__device__ __forceinline__ void getrs(const float *As, const float *dv, float (&x)[Shape<NMAX>::R], int n) {
+    constexpr int LD = Shape<NMAX>::LD;
+    constexpr int R = Shape<NMAX>::R;
+    const int lane = threadIdx.x & 31;
+    auto get = [&](int i) {
+        float s = x[0];
+#pragma unroll
+        for (int q = 1; q < R; ++q)
+            if ((i >> 5) == q) s = x[q];
+        return __shfl_sync(GLASS_FULL_MASK, s, i & 31);
+    };
+    for (int i = 0; i < n; ++i) {
+        const float yi = get(i);
+        const float *col = As + i * LD;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int row = lane + 32 * q;
+            if (row > i && row < n) x[q] = fmaf(-col[row], yi, x[q]);
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        const float xi = get(i) * dv[i];
+        const float *col = As + i * LD;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int row = lane + 32 * q;
+            if (row == i) x[q] = xi;
+            else if (row < i) x[q] = fmaf(-col[row], xi, x[q]);
+        }
+    }
+}
+
+}  // namespace tclu
+}  // namespace glass

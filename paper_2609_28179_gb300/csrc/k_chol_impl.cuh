@@ -14,6 +14,7 @@
 #include "dev_chol.cuh"
 #include "dev_rows.cuh"
 #include "dev_chol_tc.cuh"
+#include "dev_trsm_tc.cuh"
 
 namespace glass {
 namespace {
@@ -231,6 +232,13 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
     }
 }
 
+// Per-warp shared memory (floats) of k_chol_tc: A, 1/l_jj, two 16-float
+// broadcast segments.
+template <int NMAX>
+constexpr int tc_floats() {
+    return NMAX * tcwarp::Shape<NMAX>::LD + NMAX + 32;
+}
+
 // Warp scope, orders 33..64, no refinement: blocked Cholesky with
 // tensor-core trailing updates (dev_chol_tc.cuh) on the problem held in the
 // warp's shared memory; the solves run against L in shared memory.
@@ -240,20 +248,13 @@ __global__ void __launch_bounds__(256, 1) k_chol_tc(int n, int nrhs, Mat A, Mat 
     constexpr int R = tcwarp::Shape<NMAX>::R;
     extern __shared__ __align__(16) float smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *As = smem + w * (NMAX * LD + NMAX);
+    float *As = smem + w * tc_floats<NMAX>();
     float *dv = As + NMAX * LD;
+    float *bc = dv + NMAX;
     const int b = blockIdx.x * (blockDim.x >> 5) + w;
     if (b >= batch) return;  // whole warp
-    const float *ga = A.p + (long long)b * A.s;
-#pragma unroll 8
-    for (int k = 0; k < NMAX; ++k)
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int i = lane + 32 * q;
-            As[k * LD + i] = (k < n && i < n && i >= k) ? ga[(long long)k * A.ld + i] : 0.f;
-        }
-    __syncwarp();
-    const int inf = tcwarp::potrf<NMAX>(As, n, dv, fp64diag != 0);
+    tcwarp::stage<NMAX, true>(As, A.p + (long long)b * A.s, A.ld, n);
+    const int inf = tcwarp::potrf<NMAX>(As, n, dv, bc, fp64diag != 0);
     if (lane == 0) info[b] = inf;
     if (has_rhs(OP)) {
         for (int c = 0; c < nrhs; ++c) {
@@ -271,14 +272,48 @@ __global__ void __launch_bounds__(256, 1) k_chol_tc(int n, int nrhs, Mat A, Mat 
             }
         }
     }
-    float *wa = opaque(A.p + (long long)b * A.s);
-#pragma unroll 8
-    for (int k = 0; k < NMAX; ++k)
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int i = lane + 32 * q;
-            if (k < n && i < n && i >= k) wa[(long long)k * A.ld + i] = As[k * LD + i];
+    tcwarp::unstage<NMAX, true>(A.p + (long long)b * A.s, A.ld, As, n);
+}
+
+// Solves with many right-hand sides, orders 33..64 (trsm; potrs when BOTH):
+// a team of T threads per problem, blocked with tensor-core updates
+// (dev_trsm_tc.cuh); each warp of the team takes chunks of 32 right-hand
+// sides.
+template <int T, bool BOTH>
+__global__ void __launch_bounds__(256, 1) k_solve_tc(int n, int nrhs, Mat L, Mat B, int batch) {
+    using namespace tctrsm;
+    constexpr int W = T / 32;
+    extern __shared__ __align__(16) float smem[];
+    const int team = threadIdx.x / T, rank = threadIdx.x % T, w = rank >> 5;
+    const int b = blockIdx.x * (blockDim.x / T) + team;
+    const int bar = 1 + team;
+    float *Ls = smem + team * floats<T>();
+    float *dv = Ls + NMAX * LD;
+    float *Bs = dv + NMAX + w * CW * LD;
+    if (b >= batch || nrhs <= 0) return;  // whole team
+    const float *gl = L.p + (long long)b * L.s;
+    float *gb = B.p + (long long)b * B.s;
+    const bool vec = (n & 3) == 0 && (L.ld & 3) == 0 && (B.ld & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(gl) | reinterpret_cast<uintptr_t>(gb)) & 15) == 0;
+    stage_cols<true>(Ls, gl, L.ld, n, n, NMAX, vec, rank, T);
+    int c0 = w * CW;
+    if (c0 < nrhs) stage_cols<false>(Bs, gb + (long long)c0 * B.ld, B.ld, n, min(CW, nrhs - c0), CW, vec, rank & 31, 32);
+    cp_async_wait_all();
+    team_sync<T>(bar);
+    for (int i = rank; i < NMAX; i += T) dv[i] = i < n ? 1.0f / Ls[i * LD + i] : 0.f;
+    team_sync<T>(bar);
+    for (bool first = true; c0 < nrhs; c0 += W * CW, first = false) {
+        const int cols = min(CW, nrhs - c0);
+        if (!first) {
+            stage_cols<false>(Bs, gb + (long long)c0 * B.ld, B.ld, n, cols, CW, vec, rank & 31, 32);
+            cp_async_wait_all();
+            __syncwarp();
         }
+        forward(Ls, dv, Bs, n);
+        if (BOTH) backward_t(Ls, dv, Bs, n);
+        store_cols(gb + (long long)c0 * B.ld, B.ld, Bs, n, cols, vec);
+        __syncwarp();
+    }
 }
 
 // Solves with many right-hand sides (trsm; potrs when BOTH): a team of T
@@ -479,13 +514,13 @@ cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *in
 }
 
 // Shared memory of the blocked tensor-core Cholesky, per warp (bytes).
-inline size_t tc_smem(int n) {
-    const int N = n <= 32 ? 32 : 64;
-    return (size_t)(N * (N + 8) + N) * 4;
-}
+inline size_t tc_smem(int) { return (size_t)tc_floats<64>() * 4; }
 
-// Shared memory of the column-per-thread solve kernel, per problem (bytes).
-inline size_t solve_cols_per(int n, int nrhs) {
+// Shared memory of the many-right-hand-side solve kernels, per problem
+// (bytes), for a team of T threads: column-per-thread up to order 32,
+// blocked tensor-core form above.
+inline size_t solve_cols_per(int n, int nrhs, int T) {
+    if (n > 32) return (size_t)(T == 32 ? tctrsm::floats<32>() : tctrsm::floats<64>()) * 4;
     const int N = nmax_bucket(n);
     return (size_t)(N * N + N + (size_t)nrhs * col_pitch(n)) * 4;
 }
@@ -493,7 +528,7 @@ inline size_t solve_cols_per(int n, int nrhs) {
 template <int NMAX, int T, bool BOTH>
 cudaError_t launch_solve_cols(int n, int nrhs, const Mat &L, const Mat &B, int batch, int pack, cudaStream_t st) {
     auto kern = k_solve_cols<NMAX, T, BOTH>;
-    const size_t sm = solve_cols_per(n, nrhs) * pack;
+    const size_t sm = solve_cols_per(n, nrhs, T) * pack;
     cudaError_t e = prepare(kern, sm);
     if (e != cudaSuccess) return e;
     kern<<<ceil_div(batch, pack), T * pack, sm, st>>>(n, nrhs, L, B, batch);
@@ -502,6 +537,14 @@ cudaError_t launch_solve_cols(int n, int nrhs, const Mat &L, const Mat &B, int b
 
 template <int T, bool BOTH>
 cudaError_t solve_cols_dispatch(int n, int nrhs, const Mat &L, const Mat &B, int batch, int pack, cudaStream_t st) {
+    if (n > 32) {
+        auto kern = k_solve_tc<T, BOTH>;
+        const size_t sm = (size_t)tctrsm::floats<T>() * 4 * pack;
+        cudaError_t e = prepare(kern, sm);
+        if (e != cudaSuccess) return e;
+        kern<<<ceil_div(batch, pack), T * pack, sm, st>>>(n, nrhs, L, B, batch);
+        return cudaPeekAtLastError();
+    }
     switch (nmax_bucket(n)) {
         case 8: return launch_solve_cols<8, T, BOTH>(n, nrhs, L, B, batch, pack, st);
         case 16: return launch_solve_cols<16, T, BOTH>(n, nrhs, L, B, batch, pack, st);
@@ -576,13 +619,13 @@ size_t smem_of(int n, int nrhs, Placement pl, int refine) {
         case SCOPE_THREAD:
             return (size_t)32 * pl.pack * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4;
         case SCOPE_WARP: {
-            if (OP == C_TRSM) return solve_cols_per(n, nrhs) * pl.pack;
+            if (OP == C_TRSM) return solve_cols_per(n, nrhs, 32) * pl.pack;
             if (has_factor(OP) && !refine && n > 32) return tc_smem(n) * pl.pack;
             const int N = nmax_bucket(n);
             return (size_t)pl.pack * (N + (refine ? N * (N + 1) : 0)) * 4;
         }
         default:
-            if (OP == C_TRSM || OP == C_POTRS) return solve_cols_per(n, nrhs) * pl.pack;
+            if (OP == C_TRSM || OP == C_POTRS) return solve_cols_per(n, nrhs, 64) * pl.pack;
             return rows_team_bytes(n) * pl.pack;
     }
 }

@@ -1,8 +1,11 @@
 // k_lu.cu -- batched getrf + getrs (partial pivoting) at thread, warp and
 // block scope.  Thread scope stages 32*pack problems through shared memory;
-// warp scope loads rows straight into registers (one or two per lane);
-// block scope is a 64-thread row team (dev_rows.cuh), one row per thread.
+// warp scope loads rows straight into registers (one per lane) up to order
+// 32 and runs the blocked tensor-core factorization (dev_lu_tc.cuh) on the
+// problem in shared memory above that; block scope is a 64-thread row team
+// (dev_rows.cuh), one row per thread.
 #include "dev_lu.cuh"
+#include "dev_lu_tc.cuh"
 #include "dev_rows.cuh"
 
 namespace glass {
@@ -113,6 +116,51 @@ __global__ void __launch_bounds__(256, NMAX <= 32 ? 2 : 1) k_lu_warp(int n, int 
             if (k < n && lane + 32 * q < n) wa[(long long)k * A.ld + pos[q]] = a[q][k];
 }
 
+// Warp scope, orders 33..64: blocked LU with tensor-core trailing updates on
+// the problem held in the warp's shared memory (dev_lu_tc.cuh); per warp
+// A (NMAX x LD), 1/u_jj, the interchanges and the original row of each
+// logical row (the solve gathers b through it).
+template <int NMAX>
+constexpr int lu_tc_floats() {
+    return NMAX * tclu::Shape<NMAX>::LD + 3 * NMAX;
+}
+
+template <int NMAX>
+__global__ void __launch_bounds__(256, 1) k_lu_tc(int n, int nrhs, Mat A, int *ipiv, Mat B, int *info, int batch) {
+    constexpr int LD = tclu::Shape<NMAX>::LD;
+    constexpr int R = tclu::Shape<NMAX>::R;
+    extern __shared__ __align__(16) float smem[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *As = smem + w * lu_tc_floats<NMAX>();
+    float *dv = As + NMAX * LD;
+    int *ps = reinterpret_cast<int *>(dv + NMAX);
+    int *prow = ps + NMAX;
+    const int b = blockIdx.x * (blockDim.x >> 5) + w;
+    if (b >= batch) return;  // whole warp
+#pragma unroll
+    for (int q = 0; q < R; ++q) prow[lane + 32 * q] = lane + 32 * q;
+    tcwarp::stage<NMAX, false>(As, A.p + (long long)b * A.s, A.ld, n);
+    const int inf = tclu::getrf<NMAX>(As, n, prow, ps, dv);
+    if (lane == 0) info[b] = inf;
+    int *gp = ipiv + (long long)b * n;
+    for (int j = lane; j < n; j += 32) gp[j] = ps[j];
+    for (int c = 0; c < nrhs; ++c) {
+        float x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = lane + 32 * q;
+            x[q] = (i < n) ? B.cget(b, prow[i], c) : 0.f;
+        }
+        tclu::getrs<NMAX>(As, dv, x, n);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = lane + 32 * q;
+            if (i < n) B.cset(b, i, c, x[q]);
+        }
+    }
+    tcwarp::unstage<NMAX, false>(A.p + (long long)b * A.s, A.ld, As, n);
+}
+
 constexpr int kRS = 4;
 
 template <int NMAX>
@@ -167,7 +215,8 @@ constexpr size_t kMaxSmem = 227 * 1024;
 size_t smem_lu(int n, int nrhs, Placement pl) {
     switch (pl.scope) {
         case SCOPE_THREAD: return (size_t)32 * pl.pack * (odd_stride(n * n) + (nrhs > 0 ? odd_stride(n * nrhs) : 0)) * 4;
-        case SCOPE_WARP: return (size_t)pl.pack * 2 * 64 * 4;
+        case SCOPE_WARP:
+            return n > 32 ? (size_t)pl.pack * lu_tc_floats<64>() * 4 : (size_t)pl.pack * 2 * 32 * 4;
         default: {
             const int N = n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64;
             const int f = N == 8 ? lu_team_floats<8>() : N == 16 ? lu_team_floats<16>()
@@ -212,12 +261,12 @@ cudaError_t launch_getrf_getrs(int n, int nrhs, Mat A, int *ipiv, Mat B, int *in
     const int grid = ceil_div(batch, pl.pack);
     if (pl.scope == SCOPE_WARP) {
         const int th = 32 * pl.pack;
-        const int N = n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64;
+        if (n > 32) return go(k_lu_tc<64>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
+        const int N = n <= 8 ? 8 : n <= 16 ? 16 : 32;
         const size_t sw = (size_t)pl.pack * 2 * N * 4;
         if (N == 8) return go(k_lu_warp<8>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
         if (N == 16) return go(k_lu_warp<16>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
-        if (N == 32) return go(k_lu_warp<32>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
-        return go(k_lu_warp<64>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
+        return go(k_lu_warp<32>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
     }
     const int th = rows::T * pl.pack;
     if (n <= 8) return go(k_lu_rows<8>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);

@@ -21,6 +21,10 @@ Usage (on the GPU):
   python -m paper_2609_28179_gb300.tune codegen [--inp FILE]   # -> csrc/placement_table.h
   python -m paper_2609_28179_gb300.tune launch  --cells op:n:batch[:scope:pack] ...
       (one launch of each cell, for profilers; default placement = the table's)
+  python -m paper_2609_28179_gb300.tune riccati [--out FILE]   # LQR gain: fused vs composed
+  python -m paper_2609_28179_gb300.tune riccati-codegen        # -> csrc/riccati_table.h
+  python -m paper_2609_28179_gb300.tune robo [--out FILE]      # robotics ops (Table II)
+  python -m paper_2609_28179_gb300.tune robo-codegen           # -> csrc/robo_table.h
 """
 from __future__ import annotations
 
@@ -31,6 +35,8 @@ import os
 import random
 import statistics
 import sys
+
+import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TUNING = os.path.join(HERE, "tuning")
@@ -217,6 +223,273 @@ static const unsigned char kTable[{len(OPS)}][{len(SWEEP_N)}][{len(SWEEP_B)}] = 
     return out
 
 
+RICCATI_FILE = os.path.join(TUNING, "sm103_riccati.jsonl")
+RICCATI_H = os.path.join(HERE, "csrc", "riccati_table.h")
+COMPOSED = 3
+
+
+class RiccatiCell:
+    """Device inputs of the LQR gain at one (nx, nu) and batch, with a
+    launcher per placement (fused scope x pack, or the composition)."""
+
+    def __init__(self, nx, nu, batch, seed=4000, pool=None):
+        import torch
+        import paper_2609_28179_gb300 as g
+        from paper_2609_28179_gb300 import workloads as W
+        self.nx, self.nu, self.batch = nx, nu, batch
+        if pool is None:
+            host = W.riccati_inputs(nx, nu, batch, seed + nx * 100 + nu)
+            self.A, self.B, self.P, self.R = (torch.from_numpy(x).cuda() for x in host)
+        else:
+            self.A, self.B, self.P, self.R = (x[: n * batch] for x, n in
+                                              zip((pool.A, pool.B, pool.P, pool.R),
+                                                  (nx * nx, nx * nu, nx * nx, nu * nu)))
+        self.K = torch.empty(batch * nu * nx, device="cuda")
+        self.info = torch.empty(max(1, batch), dtype=torch.int32, device="cuda")
+        self.wsb = g.glass_riccati_workspace(nx, nu, batch)
+        self.ws = torch.empty(max(1, self.wsb), dtype=torch.uint8, device="cuda")
+        # bytes the method must touch: A, B, P, R in, K out
+        self.bytes = 4 * batch * (2 * nx * nx + nx * nu + nu * nu + nu * nx)
+
+    def placements(self):
+        import paper_2609_28179_gb300 as g
+        out = [(s, p) for s in (1, 2) for p in (1, 2, 4, 8) if g.glass_riccati_feasible(self.nx, self.nu, s, p)]
+        return out + [(COMPOSED, 1)]
+
+    def launch(self, scope=-1, pack=0):
+        import paper_2609_28179_gb300 as g
+        nx, nu = self.nx, self.nu
+        return g.glass_riccati_gain(nx, nu, self.A, nx * nx, self.B, nx * nu, self.P, nx * nx, self.R, nu * nu,
+                                    self.K, nu * nx, self.info, self.batch, self.ws, self.wsb,
+                                    g.make_opts(scope=scope, pack=pack))
+
+
+def riccati_sweep(out_path: str = RICCATI_FILE, iters: int = 5, seed: int = 17):
+    """Every placement of the LQR gain (fused scopes and packs, and the
+    composition) at each (nx, nu) of the workload and each sweep batch."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300 import workloads as W
+    from paper_2609_28179_gb300.cells import SWEEP_B
+    g.lib()
+    rng = random.Random(seed)
+    stream = torch.cuda.Stream()
+    with open(out_path, "w") as f:
+        for nx, nu in W.RICCATI_SIZES:
+            pool = RiccatiCell(nx, nu, max(SWEEP_B))
+            for batch in SWEEP_B:
+                cell = RiccatiCell(nx, nu, batch, pool=pool)
+                R = _reps(cell.bytes)
+                order = cell.placements()
+                rng.shuffle(order)
+                meas = {}
+                for scope, pack in order:
+                    g.check(cell.launch(scope, pack), f"riccati {nx}x{nu} {scope}x{pack}")
+                    torch.cuda.synchronize()
+                    graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(graph, stream=stream):
+                        for _ in range(R):
+                            cell.launch(scope, pack)
+                    samples = []
+                    for _ in range(iters):
+                        torch.cuda.synchronize()
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record()
+                        graph.replay()
+                        b.record()
+                        torch.cuda.synchronize()
+                        samples.append(a.elapsed_time(b) * 1e3 / R)
+                    del graph
+                    meas[(scope, pack)] = statistics.median(samples)
+                    f.write(json.dumps({"nx": nx, "nu": nu, "batch": batch, "scope": scope, "pack": pack,
+                                        "us": meas[(scope, pack)], "samples": samples, "reps": R}) + "\n")
+                f.flush()
+                best = choose({k: {"us": v} for k, v in meas.items()})
+                print(f"riccati {nx:2d}x{nu:2d} B={batch:6d} best={g.SCOPE_NAMES[best[0]]}x{best[1]} "
+                      f"{meas[best]:.2f}us composed={meas[(COMPOSED, 1)]:.2f}us", flush=True)
+                del cell
+            del pool
+            torch.cuda.empty_cache()
+
+
+def riccati_codegen(inp: str = RICCATI_FILE, out: str = RICCATI_H):
+    from paper_2609_28179_gb300 import workloads as W
+    from paper_2609_28179_gb300.cells import SWEEP_B
+    cells = {}
+    with open(inp) as f:
+        for line in f:
+            r = json.loads(line)
+            cells.setdefault((r["nx"], r["nu"], r["batch"]), {})[(r["scope"], r["pack"])] = r
+    rows = []
+    for nx, nu in W.RICCATI_SIZES:
+        codes = []
+        for b in SWEEP_B:
+            s, p = choose(cells[(nx, nu, b)])  # the composition ranks last on ties (scope 3)
+            codes.append(str(12 if s == COMPOSED else s * 4 + int(math.log2(p))))
+        rows.append("    {" + ", ".join(codes) + "},")
+    sizes = W.RICCATI_SIZES
+    text = f"""// riccati_table.h -- GENERATED by paper_2609_28179_gb300/tune.py; do not edit.
+// Placement of the LQR gain per ((nx, nu), batch) cell: code = scope * 4 +
+// log2(pack) for the fused kernel (scope 1 warp / 2 block), 12 = the
+// composition of primitive calls (Sec. IV-E: fusion granularity measured as
+// a placement).
+// source: {os.path.relpath(inp, os.path.dirname(HERE))} (GB300 measurements, 5 % dispatch margin)
+#pragma once
+namespace glass {{
+static const int kRicNum = {len(sizes)};
+static const int kRicNx[{len(sizes)}] = {{{", ".join(str(a) for a, _ in sizes)}}};
+static const int kRicNu[{len(sizes)}] = {{{", ".join(str(b) for _, b in sizes)}}};
+static const int kRicNumB = {len(SWEEP_B)};
+static const int kRicB[{len(SWEEP_B)}] = {{{", ".join(map(str, SWEEP_B))}}};
+static const unsigned char kRicTable[{len(sizes)}][{len(SWEEP_B)}] = {{
+{chr(10).join(rows)}
+}};
+}}  // namespace glass
+"""
+    with open(out, "w") as f:
+        f.write(text)
+    return out
+
+
+ROBO_FILE = os.path.join(TUNING, "sm103_robo.jsonl")
+ROBO_H = os.path.join(HERE, "csrc", "robo_table.h")
+ROBO_N = 16  # argmax / softmax length of the placement table (Table II)
+
+
+class RoboCell:
+    """Device inputs and outputs of one robotics operation at one batch."""
+
+    def __init__(self, op: int, batch: int, seed: int = 5000):
+        import torch
+        from paper_2609_28179_gb300 import workloads as W
+        self.op, self.batch = op, batch
+        dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+        empty = lambda n: torch.empty(max(1, n), device="cuda")
+        r = W.rng(seed + op)
+        if op in (0, 1):
+            self.a = dev(W.unit_quaternions(batch, seed))
+            self.b = dev(W.rotation_vectors(batch, seed + 1)) if op == 0 else dev(W.unit_quaternions(batch, seed + 2))
+            self.outs = [empty(4 * batch if op == 0 else 3 * batch)]
+            self.bytes = 4 * batch * (4 + 3 + (4 if op == 0 else 4 + 3 - 3))
+        elif op == 2:
+            self.a, self.b = dev(W.se3_transforms(batch, seed)), dev(W.twists(batch, seed + 1))
+            self.outs = [empty(16 * batch)]
+            self.bytes = 4 * batch * (16 + 6 + 16)
+        elif op == 3:
+            self.a, self.b = dev(r.standard_normal(6 * batch)), dev(r.standard_normal(6 * batch))
+            self.outs = [empty(6 * batch)]
+            self.bytes = 4 * batch * 18
+        elif op == 4:
+            self.a, self.b = dev(W.sym3(batch, seed)), None
+            self.outs = [empty(3 * batch), empty(9 * batch)]
+            self.bytes = 4 * batch * (9 + 12)
+        elif op in (5, 6):
+            self.a, self.b = dev(r.standard_normal(9 * batch)), None
+            self.outs = [empty(9 * batch), empty(3 * batch), empty(9 * batch)] if op == 5 else [empty(9 * batch)]
+            self.bytes = 4 * batch * (9 + (21 if op == 5 else 9))
+        else:
+            self.a, self.b = dev(r.standard_normal(ROBO_N * batch)), None
+            self.outs = [torch.empty(max(1, batch), dtype=torch.int32, device="cuda")] if op == 7 else \
+                [empty(ROBO_N * batch)]
+            self.bytes = 4 * batch * (ROBO_N + (1 if op == 7 else ROBO_N))
+
+    def launch(self, scope=-1, pack=0):
+        import paper_2609_28179_gb300 as g
+        o, B, a, b, out = g.make_opts(scope=scope, pack=pack), self.batch, self.a, self.b, self.outs
+        f = [g.glass_batched_quat_retract, g.glass_batched_quat_error, g.glass_batched_se3_retract,
+             g.glass_batched_motion_cross]
+        if self.op < 4:
+            return f[self.op](a, b, out[0], B, o)
+        if self.op == 4:
+            return g.glass_batched_eig3(a, out[0], out[1], B, o)
+        if self.op == 5:
+            return g.glass_batched_svd3(a, out[0], out[1], out[2], B, o)
+        if self.op == 6:
+            return g.glass_batched_closest_rotation(a, out[0], B, o)
+        if self.op == 7:
+            return g.glass_batched_argmax(ROBO_N, a, ROBO_N, out[0], B, o)
+        return g.glass_batched_softmax(ROBO_N, a, ROBO_N, out[0], ROBO_N, B, o)
+
+
+def robo_sweep(out_path: str = ROBO_FILE, iters: int = 5, seed: int = 19):
+    """Every placement of every robotics operation at each sweep batch."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300.cells import SWEEP_B
+    g.lib()
+    rng = random.Random(seed)
+    stream = torch.cuda.Stream()
+    with open(out_path, "w") as f:
+        for op, name in enumerate(g.ROBO_OPS):
+            for batch in SWEEP_B:
+                cell = RoboCell(op, batch)
+                R = _reps(cell.bytes)
+                order = [pl for pl in g.PLACEMENTS if g.glass_robo_feasible(op, ROBO_N, *pl)]
+                rng.shuffle(order)
+                meas = {}
+                for scope, pack in order:
+                    g.check(cell.launch(scope, pack), f"{name} {scope}x{pack}")
+                    torch.cuda.synchronize()
+                    graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(graph, stream=stream):
+                        for _ in range(R):
+                            cell.launch(scope, pack)
+                    samples = []
+                    for _ in range(iters):
+                        torch.cuda.synchronize()
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record()
+                        graph.replay()
+                        b.record()
+                        torch.cuda.synchronize()
+                        samples.append(a.elapsed_time(b) * 1e3 / R)
+                    del graph
+                    meas[(scope, pack)] = {"us": statistics.median(samples)}
+                    f.write(json.dumps({"op": name, "batch": batch, "scope": scope, "pack": pack,
+                                        "us": meas[(scope, pack)]["us"], "samples": samples, "reps": R,
+                                        "bytes": cell.bytes}) + "\n")
+                f.flush()
+                best = choose(meas)
+                print(f"{name:17s} B={batch:6d} best={g.SCOPE_NAMES[best[0]]}x{best[1]} "
+                      f"{meas[best]['us']:.2f}us", flush=True)
+                del cell
+                torch.cuda.empty_cache()
+
+
+def robo_codegen(inp: str = ROBO_FILE, out: str = ROBO_H):
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300.cells import SWEEP_B
+    cells = {}
+    with open(inp) as f:
+        for line in f:
+            r = json.loads(line)
+            cells.setdefault((r["op"], r["batch"]), {})[(r["scope"], r["pack"])] = r
+    rows = []
+    for name in g.ROBO_OPS:
+        codes = []
+        for b in SWEEP_B:
+            s, p = choose(cells[(name, b)])
+            codes.append(str(s * 4 + int(math.log2(p))))
+        rows.append(f"    /* {name} */ {{" + ", ".join(codes) + "},")
+    text = f"""// robo_table.h -- GENERATED by paper_2609_28179_gb300/tune.py; do not edit.
+// Placement of each robotics operation (glass_robo_op order) per batch
+// bucket: code = scope * 4 + log2(pack) (Sec. IV-E, Table II placements);
+// argmax and softmax measured at n = {ROBO_N}.
+// source: {os.path.relpath(inp, os.path.dirname(HERE))} (GB300 measurements, 5 % dispatch margin)
+#pragma once
+namespace glass {{
+static const int kRoboNumB = {len(SWEEP_B)};
+static const int kRoboB[{len(SWEEP_B)}] = {{{", ".join(map(str, SWEEP_B))}}};
+static const unsigned char kRoboTable[{len(g.ROBO_OPS)}][{len(SWEEP_B)}] = {{
+{chr(10).join(rows)}
+}};
+}}  // namespace glass
+"""
+    with open(out, "w") as f:
+        f.write(text)
+    return out
+
+
 def launch_cells(specs):
     """One launch of each cell 'op:n:batch[:scope:pack]' (device inputs)."""
     import torch
@@ -237,7 +510,8 @@ def launch_cells(specs):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["sweep", "random", "codegen", "launch"])
+    ap.add_argument("cmd", choices=["sweep", "random", "codegen", "launch", "riccati", "riccati-codegen", "robo",
+                                    "robo-codegen"])
     ap.add_argument("--cells", nargs="+", default=[])
     ap.add_argument("--out", default=None)
     ap.add_argument("--inp", default=GRID_FILE)
@@ -251,6 +525,14 @@ def main():
         random_points(args.out or os.path.join(TUNING, f"sm103_random_{args.seed}.jsonl"), args.count, args.seed)
     elif args.cmd == "launch":
         launch_cells(args.cells)
+    elif args.cmd == "riccati":
+        riccati_sweep(args.out or RICCATI_FILE)
+    elif args.cmd == "robo":
+        robo_sweep(args.out or ROBO_FILE)
+    elif args.cmd == "robo-codegen":
+        print(robo_codegen(args.inp if args.inp != GRID_FILE else ROBO_FILE))
+    elif args.cmd == "riccati-codegen":
+        print(riccati_codegen(args.inp if args.inp != GRID_FILE else RICCATI_FILE))
     else:
         print(codegen(args.inp))
 

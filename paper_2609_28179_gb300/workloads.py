@@ -191,3 +191,56 @@ def varsize_pack(sizes: np.ndarray, nrhs: int, seed: int):
         A[offA[i]:offA[i] + n * n] = a.T.reshape(-1).astype(np.float32)
         B[offB[i]:offB[i] + n * nrhs] = g.standard_normal(n * nrhs).astype(np.float32)
     return A, B, offA, offB
+
+
+# ------------------------------------------------------------ LQR gain inputs
+# (nx, nu) pairs of the LQR-gain workload: cart-pole, quadrotor, 7-DoF arm
+# (joint positions and velocities), a legged base with 12 actuated joints,
+# and the largest state the library serves.
+RICCATI_SIZES = [(4, 1), (12, 4), (14, 7), (36, 12), (64, 16)]
+
+
+def riccati_inputs(nx: int, nu: int, batch: int, seed: int):
+    """Packed column-major FP32 (A, B, P, R) for K = (R + B^T P B)^{-1} B^T P A:
+    A = I + 0.1 N(0,1) (a discretised stable-ish system), B ~ N(0,1),
+    P = M M^T + nx I (a cost-to-go, symmetric positive definite, exactly
+    symmetric after rounding), R = M M^T + nu I."""
+    g = rng(seed)
+    A = np.eye(nx) + 0.1 * g.standard_normal((batch, nx, nx))
+    B = g.standard_normal((batch, nx, nu))
+    Mp = g.standard_normal((batch, nx, nx))
+    P = Mp @ np.transpose(Mp, (0, 2, 1)) + nx * np.eye(nx)
+    Mr = g.standard_normal((batch, nu, nu))
+    R = Mr @ np.transpose(Mr, (0, 2, 1)) + nu * np.eye(nu)
+    P = 0.5 * (P + np.transpose(P, (0, 2, 1)))
+    R = 0.5 * (R + np.transpose(R, (0, 2, 1)))
+    return colmajor(A), colmajor(B), colmajor(P), colmajor(R)
+
+
+# ------------------------------------------------------- robotics operations
+def unit_quaternions(batch: int, seed: int) -> np.ndarray:
+    """(w, x, y, z) unit quaternions from normalised N(0,1)^4, [batch][4] FP32."""
+    q = rng(seed).standard_normal((batch, 4))
+    return (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32).reshape(-1)
+
+
+def rotation_vectors(batch: int, seed: int) -> np.ndarray:
+    """Rotation vectors with angle ~ U(0, pi) about uniform axes, [batch][3] FP32."""
+    g = rng(seed)
+    ax = g.standard_normal((batch, 3))
+    ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    return (ax * g.uniform(0.0, np.pi, (batch, 1))).astype(np.float32).reshape(-1)
+
+
+def twists(batch: int, seed: int) -> np.ndarray:
+    """(rho, phi): rho ~ N(0,1)^3, phi a rotation vector, [batch][6] FP32."""
+    g = rng(seed)
+    rho = g.standard_normal((batch, 3))
+    phi = rotation_vectors(batch, seed + 1).reshape(batch, 3)
+    return np.concatenate([rho, phi], axis=1).astype(np.float32).reshape(-1)
+
+
+def sym3(batch: int, seed: int) -> np.ndarray:
+    """Symmetric 3x3 matrices (M + M^T with M ~ N(0,1)), column-major FP32."""
+    M = rng(seed).standard_normal((batch, 3, 3))
+    return colmajor(M + np.transpose(M, (0, 2, 1)))

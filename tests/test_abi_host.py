@@ -120,3 +120,42 @@ def test_interleaved_layout_is_thread_scope_only(L):
     assert g.glass_batched_getrf_getrs(6, 1, BAD, 6, 36, BAD, BAD, 6, 6, BAD, 4, o, 0) == g.GLASS_ERR_UNSUPPORTED
     o = g.make_opts(layout=g.GLASS_LAYOUT_INTERLEAVED32)   # auto: no thread-scope kernel above n = 16
     assert g.glass_batched_posv(40, 1, BAD, 40, 1600, BAD, 40, 40, BAD, 4, o, 0) == g.GLASS_ERR_UNSUPPORTED
+
+
+def test_gemm_ex_and_riccati_argument_rules(L):
+    I, U = g.GLASS_ERR_INVALID_VALUE, g.GLASS_ERR_UNSUPPORTED
+    ex = g.glass_batched_gemm_ex
+    assert ex(2, 0, 4, 4, 4, 1.0, BAD, 4, 16, BAD, 4, 16, 0.0, BAD, 4, 16, 2, None, 0) == I           # trans flag
+    assert ex(1, 0, 4, 5, 3, 1.0, BAD, 2, 12, BAD, 3, 15, 0.0, BAD, 4, 20, 2, None, 0) == I           # lda < k (A^T)
+    assert ex(0, 1, 4, 5, 3, 1.0, BAD, 4, 12, BAD, 4, 15, 0.0, BAD, 4, 20, 2, None, 0) == I           # ldb < n (B^T)
+    assert ex(0, 0, 65, 4, 4, 1.0, BAD, 65, 260, BAD, 4, 16, 0.0, BAD, 65, 260, 2, None, 0) == U
+    assert ex(0, 0, 4, 4, 4, 1.0, None, 4, 16, None, 4, 16, 0.0, None, 4, 16, 0, None, 0) == g.GLASS_OK
+    o = g.make_opts(scope=g.GLASS_SCOPE_THREAD, pack=1)
+    assert ex(0, 0, 4, 4, 4, 1.0, BAD, 4, 16, BAD, 4, 16, 0.0, BAD, 4, 16, 2, o, 0) == I        # no thread scope
+    rg = g.glass_riccati_gain
+    assert rg(0, 1, BAD, 0, BAD, 0, BAD, 0, BAD, 0, BAD, 1, BAD, 2, None, 0, None, 0) == I
+    assert rg(65, 1, BAD, 0, BAD, 0, BAD, 0, BAD, 0, BAD, 65, BAD, 2, None, 0, None, 0) == U
+    assert rg(4, 2, BAD, 16, BAD, 8, BAD, 16, BAD, 4, BAD, 7, BAD, 2, None, 0, None, 0) == I                    # sK < nu*nx
+    assert rg(4, 2, BAD, 16, BAD, 8, BAD, 16, BAD, 4, BAD, 8, None, 2, None, 0, None, 0) == I                   # null info
+    o = g.make_opts(scope=g.GLASS_SCOPE_COMPOSED)
+    assert rg(4, 2, BAD, 16, BAD, 8, BAD, 16, BAD, 4, BAD, 8, BAD, 2, None, 0, o, 0) == g.GLASS_ERR_WORKSPACE
+    assert rg(4, 2, BAD, 16, BAD, 8, BAD, 16, BAD, 0, BAD, 8, BAD, 2, BAD, 1 << 20, o, 0) == g.GLASS_ERR_WORKSPACE
+    assert rg(4, 2, None, 0, None, 0, None, 0, None, 0, None, 8, None, 0, None, 0, None, 0) == g.GLASS_OK
+    assert g.glass_riccati_workspace(12, 4, 1000) >= 4 * 1000 * (12 * 4 + 4 * 4)
+    assert g.glass_riccati_workspace(0, 4, 10) == 0
+
+
+def test_riccati_placement_queries(L):
+    from paper_2609_28179_gb300 import workloads as W
+    for nx, nu in W.RICCATI_SIZES + [(1, 1), (64, 64), (20, 3)]:
+        for batch in (1, 64, 1024, 16384, 100000):
+            for ok in (True, False):
+                s, (scope, pack) = g.glass_riccati_placement(nx, nu, batch, ok)
+                assert s == g.GLASS_OK
+                if scope == g.GLASS_SCOPE_COMPOSED:
+                    assert ok
+                else:
+                    assert g.glass_riccati_feasible(nx, nu, scope, pack)
+    assert not g.glass_riccati_feasible(64, 64, g.GLASS_SCOPE_WARP, 8)   # shared memory
+    assert not g.glass_riccati_feasible(8, 8, g.GLASS_SCOPE_BLOCK, 4)    # 512 threads
+    assert not g.glass_riccati_feasible(8, 8, g.GLASS_SCOPE_THREAD, 1)
