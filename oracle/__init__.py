@@ -76,6 +76,11 @@ def _load():
             "oracle_closest_rotation_f64": (None, [_D, _D, _int]),
             "oracle_argmax_f64": (None, [_int, _D, _ll, _I, _int]),
             "oracle_softmax_f64": (None, [_int, _D, _ll, _D, _ll, _int]),
+            "oracle_dot_f64": (None, [_int, _D, _ll, _D, _ll, _D, _int]),
+            "oracle_gemv_f64": (None, [_int, _int, _int, ctypes.c_double, _D, _int, _ll, _D, _ll,
+                                       ctypes.c_double, _D, _ll, _int]),
+            "oracle_btd_matvec_f64": (None, [_int, _int, _D, _D, _D, _D, _int]),
+            "oracle_btd_posv_f64": (None, [_int, _int, _D, _D, _D, _I, _int]),
             "oracle_rot3_compose_f64": (None, [_int, _D, _ll, _D, _ll, _int]),
             "oracle_se3_apply_f64": (None, [_int, _D, _ll, _int, _D, _ll, _D, _ll, _int]),
             "oracle_mlp_nparams": (_ll, [_int, _int, _int]),
@@ -309,6 +314,40 @@ def softmax(n, x, batch, sx=None):
     y = _out(n * batch)
     _load().oracle_softmax_f64(n, _dp(_f64(x)), sx, _dp(y), n, batch)
     return y
+
+
+# ------------------------------------------------ BLAS-1/2, block-tridiagonal
+def dot(n, x, y, batch, sx=None, sy=None):
+    sx = n if sx is None else sx
+    sy = n if sy is None else sy
+    out = _out(batch)
+    _load().oracle_dot_f64(n, _dp(_f64(x)), sx, _dp(_f64(y)), sy, _dp(out), batch)
+    return out[:batch]
+
+
+def gemv(trans, m, n, alpha, A, lda, sA, x, sx, beta, y, sy, batch):
+    """y = alpha op(A) x + beta y; returns the new y (y may be None when beta == 0)."""
+    y = np.zeros(max(1, sy * batch), dtype=np.float64) if y is None else _f64(y)
+    _load().oracle_gemv_f64(int(bool(trans)), m, n, float(alpha), _dp(_f64(A)), lda, sA, _dp(_f64(x)), sx,
+                            float(beta), _dp(y), sy, batch)
+    return y
+
+
+def btd_matvec(nb, N, D, O, x, batch):
+    """y = T x, T symmetric block-tridiagonal (D: [batch][N][nb*nb], O: [batch][N-1][nb*nb])."""
+    y = _out(N * nb * batch)
+    _load().oracle_btd_matvec_f64(nb, N, _dp(_f64(D)), _dp(_f64(O) if N > 1 else np.zeros(1)), _dp(_f64(x)),
+                                  _dp(y), batch)
+    return y
+
+
+def btd_posv(nb, N, D, O, b, batch):
+    """(x, info) with T x = b by the dense Cholesky solve of the assembled T."""
+    x = _f64(b)
+    info = np.zeros(max(1, batch), dtype=np.int32)
+    _load().oracle_btd_posv_f64(nb, N, _dp(_f64(D)), _dp(_f64(O) if N > 1 else np.zeros(1)), _dp(x), _ip(info),
+                                batch)
+    return x, info[:batch]
 
 
 def rot3_compose(chain, Rs, batch, sRs=None, sR=9):

@@ -905,3 +905,99 @@ void oracle_softmax_f64(int n, const double *x, long long sx, double *y, long lo
         for (int i = 0; i < n; ++i) o[i] /= s;
     }
 }
+
+/* ======================================================================== */
+/* BLAS-1/2 and block-tridiagonal routines (Sec. III-B: "reductions, BLAS   */
+/* L1-L3"; "block-tridiagonal matrix-vector products and direct ...        */
+/* solvers commonly used in trajectory optimization").                     */
+/* ======================================================================== */
+
+/* dot: out[b] = sum_i x_i y_i over n entries (stride 1 within a problem). */
+void oracle_dot_f64(int n, const double *x, long long sx, const double *y, long long sy,
+                    double *out, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += x[(long long)b * sx + i] * y[(long long)b * sy + i];
+        out[b] = s;
+    }
+}
+
+/* gemv: y = alpha op(A) x + beta y, A m x n column-major (lda), op(A) = A
+ * (trans 0, x has n entries, y m) or A^T (trans 1, x has m, y n); with
+ * beta == 0, y is not read. */
+void oracle_gemv_f64(int trans, int m, int n, double alpha, const double *A, int lda, long long sA,
+                     const double *x, long long sx, double beta, double *y, long long sy, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const double *a = A + (long long)b * sA, *xb = x + (long long)b * sx;
+        double *yb = y + (long long)b * sy;
+        const int rows = trans ? n : m, inner = trans ? m : n;
+        for (int i = 0; i < rows; ++i) {
+            double s = 0.0;
+            for (int l = 0; l < inner; ++l)
+                s += (trans ? a[i * lda + l] : a[l * lda + i]) * xb[l];
+            yb[i] = beta == 0.0 ? alpha * s : alpha * s + beta * yb[i];
+        }
+    }
+}
+
+/* The symmetric block-tridiagonal matrix T of N diagonal blocks D_i (nb x nb,
+ * symmetric, all entries read) and N-1 sub-diagonal blocks O_i = T[i+1][i]
+ * (the super-diagonal blocks are their transposes), assembled densely
+ * (column-major, order N*nb). */
+static void btd_assemble(int nb, int N, const double *D, const double *O, double *T)
+{
+    const int m = N * nb;
+    for (int k = 0; k < m * m; ++k) T[k] = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int c = 0; c < nb; ++c)
+            for (int r = 0; r < nb; ++r) {
+                T[(i * nb + c) * m + i * nb + r] = D[(long long)i * nb * nb + c * nb + r];
+                if (i + 1 < N) {
+                    const double o = O[(long long)i * nb * nb + c * nb + r];
+                    T[(i * nb + c) * m + (i + 1) * nb + r] = o;      /* block (i+1, i) */
+                    T[((i + 1) * nb + r) * m + i * nb + c] = o;      /* block (i, i+1) = O^T */
+                }
+            }
+}
+
+/* y = T x per problem (x, y of N*nb entries). */
+void oracle_btd_matvec_f64(int nb, int N, const double *D, const double *O, const double *x,
+                           double *y, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const int m = N * nb;
+        double *T = (double *)malloc(sizeof(double) * (size_t)m * m);
+        btd_assemble(nb, N, D + (long long)b * N * nb * nb, O + (long long)b * (N > 1 ? N - 1 : 0) * nb * nb, T);
+        for (int r = 0; r < m; ++r) {
+            double s = 0.0;
+            for (int c = 0; c < m; ++c) s += T[c * m + r] * x[(long long)b * m + c];
+            y[(long long)b * m + r] = s;
+        }
+        free(T);
+    }
+}
+
+/* x = T^{-1} b for SPD T: the dense Cholesky solve of the assembled matrix
+ * (POTRF + POTRS of this file).  info[b] is the dense POTRF info: the first
+ * failing global column + 1. */
+void oracle_btd_posv_f64(int nb, int N, const double *D, const double *O, double *bx, int *info,
+                         int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const int m = N * nb;
+        double *T = (double *)malloc(sizeof(double) * (size_t)m * m);
+        btd_assemble(nb, N, D + (long long)b * N * nb * nb, O + (long long)b * (N > 1 ? N - 1 : 0) * nb * nb, T);
+        info[b] = potrf_one(m, T, m);
+        if (info[b] == 0) {
+            forward_lower(m, T, m, bx + (long long)b * m, 0);
+            backward_lower_transposed(m, T, m, bx + (long long)b * m);
+        }
+        free(T);
+    }
+}

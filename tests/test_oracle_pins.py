@@ -712,3 +712,87 @@ def test_argmax_and_softmax_against_numpy():
     assert np.abs(y - sp_softmax(x, axis=1)).max() <= 1e-15
     big = oracle.softmax(n, (x + 1000.0).reshape(-1), batch).reshape(batch, n)  # shift invariance, no overflow
     assert np.abs(big - y).max() <= 1e-12                       # x + 1000 rounds at ~1e-13
+
+
+# ------------------------------------------- BLAS-1/2 and block-tridiagonal
+def test_dot_and_gemv_against_numpy():
+    rng = np.random.default_rng(120)
+    batch, n = 9, 37
+    x, y = rng.standard_normal((batch, n + 2)), rng.standard_normal((batch, n + 5))
+    got = oracle.dot(n, x.reshape(-1), y.reshape(-1), batch, sx=n + 2, sy=n + 5)
+    assert np.abs(got - np.einsum("bi,bi->b", x[:, :n], y[:, :n])).max() <= 1e-13
+    assert oracle.dot(3, [1.0, 2.0, 3.0], [4.0, -5.0, 6.0], 1)[0] == 12.0
+    m, k = 6, 5
+    A = rng.standard_normal((batch, m, k))
+    lda = m + 1
+    a, sA = np.zeros((batch, k, lda)), k * lda
+    a[:, :, :m] = A.transpose(0, 2, 1)
+    for trans in (0, 1):
+        xin = rng.standard_normal((batch, m if trans else k))
+        yin = rng.standard_normal((batch, k if trans else m))
+        out = oracle.gemv(trans, m, k, 2.0, a.reshape(-1), lda, sA, xin.reshape(-1), xin.shape[1], -1.0,
+                          yin.reshape(-1), yin.shape[1], batch).reshape(batch, -1)
+        opA = A.transpose(0, 2, 1) if trans else A
+        want = 2.0 * np.einsum("bij,bj->bi", opA, xin) - yin
+        assert np.abs(out - want).max() <= 1e-13
+
+
+def _btd_case(nb, N, batch, seed, shift=None):
+    rng = np.random.default_rng(seed)
+    D = rng.standard_normal((batch, N, nb, nb))
+    D = D @ D.transpose(0, 1, 3, 2) + (2.0 * nb + 2.0 if shift is None else shift) * np.eye(nb)
+    O = rng.standard_normal((batch, max(N - 1, 1), nb, nb))[:, :max(N - 1, 0)]
+    return D, O
+
+
+def _btd_dense(D, O):
+    batch, N, nb = D.shape[0], D.shape[1], D.shape[2]
+    T = np.zeros((batch, N * nb, N * nb))
+    for i in range(N):
+        T[:, i * nb:(i + 1) * nb, i * nb:(i + 1) * nb] = D[:, i]
+        if i + 1 < N:
+            T[:, (i + 1) * nb:(i + 2) * nb, i * nb:(i + 1) * nb] = O[:, i]
+            T[:, i * nb:(i + 1) * nb, (i + 1) * nb:(i + 2) * nb] = O[:, i].transpose(0, 2, 1)
+    return T
+
+
+def _btd_flat(X):
+    return np.ascontiguousarray(X.transpose(0, 1, 3, 2)).reshape(-1)     # column-major blocks
+
+
+@pytest.mark.parametrize("nb,N", [(1, 1), (1, 7), (3, 5), (6, 10), (12, 4)])
+def test_btd_matvec_and_solve_against_banded_cholesky(nb, N):
+    batch = 5
+    D, O = _btd_case(nb, N, batch, 130 + nb + N)
+    rng = np.random.default_rng(131)
+    x = rng.standard_normal((batch, N * nb))
+    y = oracle.btd_matvec(nb, N, _btd_flat(D), _btd_flat(O), x.reshape(-1), batch).reshape(batch, -1)
+    T = _btd_dense(D, O)
+    assert np.abs(y - np.einsum("bij,bj->bi", T, x)).max() <= 1e-12 * np.abs(y).max()
+    b = rng.standard_normal((batch, N * nb))
+    X, info = oracle.btd_posv(nb, N, _btd_flat(D), _btd_flat(O), b.reshape(-1), batch)
+    assert (info == 0).all()
+    X = X.reshape(batch, -1)
+    for k in range(batch):
+        # SciPy's banded Cholesky (lower form, bandwidth 2nb-1): an independent solver
+        m, u = N * nb, 2 * nb - 1
+        ab = np.zeros((u + 1, m))
+        for d in range(u + 1):
+            ab[d, :m - d] = np.diagonal(T[k], -d)
+        cb = sla.cholesky_banded(ab, lower=True)
+        want = sla.cho_solve_banded((cb, True), b[k])
+        assert np.abs(X[k] - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_btd_scalar_tridiagonal_closed_form_and_info():
+    # nb = 1: the 1-D Laplacian tridiag(-1, 2, -1) of order 4 with b = (1,0,0,1): x = (1,1,1,1)
+    D = np.full((1, 4, 1, 1), 2.0)
+    O = np.full((1, 3, 1, 1), -1.0)
+    X, info = oracle.btd_posv(1, 4, _btd_flat(D), _btd_flat(O), [1.0, 0.0, 0.0, 1.0], 1)
+    assert info[0] == 0 and np.abs(X - 1.0).max() <= 1e-15
+    # an indefinite second diagonal block: the dense factor fails in its first column (global 3)
+    D, O = _btd_case(2, 3, 1, 132)
+    D[0, 1] = -np.eye(2)
+    O[:] = 0.0
+    _, info = oracle.btd_posv(2, 3, _btd_flat(D), _btd_flat(O), np.zeros(6), 1)
+    assert info[0] == 3
