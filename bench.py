@@ -154,9 +154,12 @@ def time_steps(cells, placements, steps, warmup, stream_events=True):
     return total, per
 
 
-def e2e_steps(cells, steps, warmup):
+def e2e_steps(cells, steps, warmup, nstreams=3):
     """End to end through the public API with host buffers: per step, pinned
-    H2D of every cell's inputs, the launches, D2H of every result."""
+    H2D of every cell's inputs, the launches, D2H of every result.  Cells
+    take turns on `nstreams` streams, so one cell's upload, another's kernel
+    and a third's download overlap (the copy engines run both directions at
+    once); a cell's own copy-launch-copy stays ordered on its stream."""
     import torch
     pinned_in, pinned_out, outs = [], [], []
     h2d = d2h = 0
@@ -179,23 +182,32 @@ def e2e_steps(cells, steps, warmup):
         pinned_out.append(po)
         d2h += sum(r.numel() * r.element_size() for r in res)
 
+    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    main = torch.cuda.current_stream()
+
     def one_step():
-        for c, pin, res, po in zip(cells, pinned_in, outs, pinned_out):
-            w = c.work[0]
-            for k, t in pin.items():
-                w[k].copy_(t, non_blocking=True)
-            c.launch(0)
-            for r, p in zip(res, po):
-                p.copy_(r, non_blocking=True)
+        for i, (c, pin, res, po) in enumerate(zip(cells, pinned_in, outs, pinned_out)):
+            s = streams[i % nstreams]
+            with torch.cuda.stream(s):
+                w = c.work[0]
+                for k, t in pin.items():
+                    w[k].copy_(t, non_blocking=True)
+                c.launch(0, stream=s)
+                for r, p in zip(res, po):
+                    p.copy_(r, non_blocking=True)
 
     for _ in range(warmup):
         one_step()
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record()
+    t0.record(main)
+    for s in streams:
+        s.wait_stream(main)
     for _ in range(steps):
         one_step()
-    t1.record()
+    for s in streams:
+        main.wait_stream(s)
+    t1.record(main)
     torch.cuda.synchronize()
     return t0.elapsed_time(t1), h2d, d2h
 
@@ -699,13 +711,65 @@ def extra_robo(peaks, batches=(4096, 1 << 20)):
     return out
 
 
+def extra_blas(peaks):
+    """Batched dot and GEMV, and the block-tridiagonal matvec and solve of
+    trajectory optimization (symmetric, N blocks of nb x nb: N = horizon,
+    nb = state size), table/auto placements, inputs restored untimed."""
+    import numpy as np
+    import torch
+    import paper_2609_28179_gb300 as g
+    out = {}
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1010)
+    for n, batch in ((16, 1 << 20), (64, 1 << 20)):
+        x = torch.randn(batch * n, generator=gen, device="cuda")
+        y = torch.randn(batch * n, generator=gen, device="cuda")
+        o = torch.empty(batch, device="cuda")
+        ms = _graph_time(lambda: g.glass_batched_dot(n, x, n, y, n, o, batch), 8)
+        by = 4 * batch * (2 * n + 1)
+        out[f"dot:n{n}:b{batch}"] = {"us": ms * 1e3, "gbs": by / (ms / 1e3) / 1e9,
+                                     "frac_hbm": by / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    for n, batch in ((16, 1 << 18), (64, 1 << 16)):
+        A = torch.randn(batch * n * n, generator=gen, device="cuda")
+        x = torch.randn(batch * n, generator=gen, device="cuda")
+        y = torch.empty(batch * n, device="cuda")
+        ms = _graph_time(lambda: g.glass_batched_gemv(0, n, n, 1.0, A, n, n * n, x, n, 0.0, y, n, batch), 8)
+        by = 4 * batch * (n * n + 2 * n)
+        out[f"gemv:n{n}:b{batch}"] = {"us": ms * 1e3, "gbs": by / (ms / 1e3) / 1e9,
+                                      "frac_hbm": by / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    for nb, N, batch in ((6, 32, 4096), (12, 32, 4096), (16, 64, 4096)):
+        r = np.random.default_rng(1011)
+        M = r.standard_normal((batch, N, nb, nb)).astype(np.float32)
+        D0 = torch.from_numpy(np.ascontiguousarray(
+            (M @ M.transpose(0, 1, 3, 2) + (2 * nb + 2) * np.eye(nb, dtype=np.float32)).transpose(0, 1, 3, 2))).cuda()
+        O0 = torch.randn(batch * (N - 1) * nb * nb, generator=gen, device="cuda")
+        b0 = torch.randn(batch * N * nb, generator=gen, device="cuda")
+        D, O, b = D0.clone().reshape(-1), O0.clone(), b0.clone()
+        info = torch.empty(batch, dtype=torch.int32, device="cuda")
+        y = torch.empty_like(b0)
+
+        def setup():
+            D.copy_(D0.reshape(-1))
+            O.copy_(O0)
+            b.copy_(b0)
+        ms_mv = _graph_time(lambda: g.glass_batched_btd_matvec(nb, N, D0, O0, b0, y, batch), 8)
+        ms_sv = _graph_time(lambda: g.glass_batched_btd_posv(nb, N, D, O, b, info, batch), 1, setup=setup)
+        by = 4 * batch * ((2 * N - 1) * nb * nb + 2 * N * nb)
+        out[f"btd:nb{nb}:N{N}:b{batch}"] = {
+            "matvec_us": ms_mv * 1e3, "matvec_gbs": by / (ms_mv / 1e3) / 1e9,
+            "posv_us": ms_sv * 1e3, "posv_systems_per_s": batch / (ms_sv / 1e3),
+            "posv_gbs": 2 * by / (ms_sv / 1e3) / 1e9}
+    return out
+
+
 def run_extras(peaks, which):
     out = {}
     for name, fn in (("plain_posv_n6", lambda: extra_plain_posv(peaks)), ("mixed_size", lambda: extra_varsize(peaks)),
                      ("tensor_core_gemm", lambda: extra_tc_gemm(peaks)), ("refined_posv", lambda: extra_refine(peaks)),
                      ("learned_placement", extra_learned), ("latency", extra_latency),
                      ("batch_scaling", lambda: extra_batch_scaling(peaks)),
-                     ("riccati_gain", lambda: extra_riccati(peaks)), ("robotics_ops", lambda: extra_robo(peaks))):
+                     ("riccati_gain", lambda: extra_riccati(peaks)), ("robotics_ops", lambda: extra_robo(peaks)),
+                     ("blas_block_tridiagonal", lambda: extra_blas(peaks))):
         if which != "all" and name not in which.split(","):
             continue
         try:

@@ -403,6 +403,50 @@ glass_status glass_batched_softmax(int n, const void *x, long long sx, void *y, 
 glass_status glass_robo_placement(int op, int n, int batch, glass_placement *out);
 int glass_robo_feasible(int op, int n, glass_placement p);
 
+/* ----------------------------------------- BLAS-1/2, block-tridiagonal */
+
+/* Batched dot product (Sec. III-B reductions, BLAS L1):
+ * out[b] = sum_{i<n} x[b*sx + i] y[b*sy + i], n >= 1.  Placement: thread
+ * (one problem per thread), warp or block (64 threads) with a shuffle
+ * reduction; auto picks by n. */
+glass_status glass_batched_dot(int n, const void *x, long long sx, const void *y, long long sy,
+                               void *out, int batch, const glass_opts *opts, glass_stream_t stream);
+
+/* Batched GEMV (BLAS L2): y = alpha op(A) x + beta y, A m x n column-major
+ * (lda >= m, batch stride sA), op(A) = A (trans 0: x has n entries, y m) or
+ * A^T (trans 1: x m, y n); 1 <= m, n <= 64; beta == 0 does not read y.
+ * Placement: thread or warp (rows over lanes); auto picks by size. */
+glass_status glass_batched_gemv(int trans, int m, int n, float alpha, const void *A, int lda,
+                                long long sA, const void *x, long long sx, float beta, void *y,
+                                long long sy, int batch, const glass_opts *opts,
+                                glass_stream_t stream);
+
+/* Batched triangular solve with one right-hand side (BLAS L2 TRSV: left,
+ * lower, no transpose, non-unit): L x = b, x overwrites b (x[b*sx + i]).
+ * The trsm kernels with nrhs = 1 and the trsm placement table. */
+glass_status glass_batched_trsv(int n, const void *L, int lda, long long sA, void *x, long long sx,
+                                int batch, const glass_opts *opts, glass_stream_t stream);
+
+/* Symmetric block-tridiagonal operators of trajectory optimization (Sec.
+ * III-B structured routines): T has N >= 1 diagonal blocks D_i and N-1
+ * sub-diagonal blocks O_i = T[i+1][i] (the super-diagonal blocks are their
+ * transposes), each nb x nb column-major (1 <= nb <= 32), packed per
+ * problem: D [batch][N][nb*nb], O [batch][N-1][nb*nb], vectors
+ * [batch][N*nb].  One warp per problem (pack warps per CTA).
+ *   btd_matvec: y = T x (every entry of D_i is read).
+ *   btd_posv:   T x = b for SPD T by the block Cholesky recurrence
+ *     L_0 L_0^T = D_0, W_i = O_i L_i^{-T}, L_{i+1} L_{i+1}^T = D_{i+1} -
+ *     W_i W_i^T, then the block forward and backward sweeps; in place:
+ *     D_i <- L_i (lower triangle; the strict upper triangle keeps its
+ *     contents), O_i <- W_i, b <- x.  info[b] = 0, or i*nb + j + 1 when the
+ *     j-th column of block i fails (the global column of the dense
+ *     Cholesky of T). */
+glass_status glass_batched_btd_matvec(int nb, int N, const void *D, const void *O, const void *x,
+                                      void *y, int batch, const glass_opts *opts,
+                                      glass_stream_t stream);
+glass_status glass_batched_btd_posv(int nb, int N, void *D, void *O, void *b, int *info, int batch,
+                                    const glass_opts *opts, glass_stream_t stream);
+
 /* ------------------------------------------------------- measurement aid */
 
 /* Pipe-throughput probe (no counterpart in the paper; it supplies the

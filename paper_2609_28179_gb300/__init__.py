@@ -108,6 +108,12 @@ _SIGS = {
     "glass_batched_closest_rotation": (_i, [_P, _P, _i, _OPTS, _P]),
     "glass_batched_argmax": (_i, [_i, _P, _ll, _P, _i, _OPTS, _P]),
     "glass_batched_softmax": (_i, [_i, _P, _ll, _P, _ll, _i, _OPTS, _P]),
+    "glass_batched_dot": (_i, [_i, _P, _ll, _P, _ll, _P, _i, _OPTS, _P]),
+    "glass_batched_gemv": (_i, [_i, _i, _i, ctypes.c_float, _P, _i, _ll, _P, _ll, ctypes.c_float, _P, _ll, _i,
+                                _OPTS, _P]),
+    "glass_batched_trsv": (_i, [_i, _P, _i, _ll, _P, _ll, _i, _OPTS, _P]),
+    "glass_batched_btd_matvec": (_i, [_i, _i, _P, _P, _P, _P, _i, _OPTS, _P]),
+    "glass_batched_btd_posv": (_i, [_i, _i, _P, _P, _P, _P, _i, _OPTS, _P]),
     "glass_robo_placement": (_i, [_i, _i, _i, ctypes.POINTER(glass_placement)]),
     "glass_robo_feasible": (_i, [_i, _i, glass_placement]),
     "glass_peak_probe": (_i, [_i, _i, _i, _i, _P, ctypes.POINTER(ctypes.c_double), _P]),
@@ -339,6 +345,29 @@ def glass_batched_argmax(n, x, sx, idx, batch, opts=None, stream=None):
 
 def glass_batched_softmax(n, x, sx, y, sy, batch, opts=None, stream=None):
     return lib().glass_batched_softmax(n, _ptr(x), sx, _ptr(y), sy, batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_dot(n, x, sx, y, sy, out, batch, opts=None, stream=None):
+    return lib().glass_batched_dot(n, _ptr(x), sx, _ptr(y), sy, _ptr(out), batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_gemv(trans, m, n, alpha, A, lda, sA, x, sx, beta, y, sy, batch, opts=None, stream=None):
+    return lib().glass_batched_gemv(trans, m, n, alpha, _ptr(A), lda, sA, _ptr(x), sx, beta, _ptr(y), sy, batch,
+                                    _opts(opts), _stream(stream))
+
+
+def glass_batched_trsv(n, L, lda, sA, x, sx, batch, opts=None, stream=None):
+    return lib().glass_batched_trsv(n, _ptr(L), lda, sA, _ptr(x), sx, batch, _opts(opts), _stream(stream))
+
+
+def glass_batched_btd_matvec(nb, N, D, O, x, y, batch, opts=None, stream=None):
+    return lib().glass_batched_btd_matvec(nb, N, _ptr(D), _ptr(O), _ptr(x), _ptr(y), batch, _opts(opts),
+                                          _stream(stream))
+
+
+def glass_batched_btd_posv(nb, N, D, O, b, info, batch, opts=None, stream=None):
+    return lib().glass_batched_btd_posv(nb, N, _ptr(D), _ptr(O), _ptr(b), _ptr(info), batch, _opts(opts),
+                                        _stream(stream))
 
 
 def glass_robo_placement(op, n, batch):

@@ -680,6 +680,95 @@ glass_status glass_batched_softmax(int n, const void *x, long long sx, void *y, 
 }
 #undef GLASS_ROBO_ENTRY
 
+glass_status glass_batched_dot(int n, const void *x, long long sx, const void *y, long long sy, void *out, int batch,
+                               const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if (n < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32 || o.math != GLASS_MATH_FP32 || o.layout != GLASS_LAYOUT_COLMAJOR)
+        return GLASS_ERR_UNSUPPORTED;
+    if (!x || !y || !out || sx < 0 || sy < 0) return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    if (o.placement.scope == GLASS_SCOPE_AUTO) {
+        pl = n <= 8 ? Placement{SCOPE_THREAD, 4} : n <= 512 ? Placement{SCOPE_WARP, 4} : Placement{SCOPE_BLOCK, 2};
+        if (o.placement.pack != 0) pl.pack = o.placement.pack;
+    } else {
+        pl = Placement{o.placement.scope, o.placement.pack == 0 ? 1 : o.placement.pack};
+    }
+    if (pl.scope < SCOPE_THREAD || pl.scope > SCOPE_BLOCK || !valid_pack(pl.pack) ||
+        (pl.scope == SCOPE_BLOCK && pl.pack > 4))
+        return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_dot(n, static_cast<const float *>(x), sx, static_cast<const float *>(y), sy,
+                                static_cast<float *>(out), batch, pl, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_batched_gemv(int trans, int m, int n, float alpha, const void *A, int lda, long long sA,
+                                const void *x, long long sx, float beta, void *y, long long sy, int batch,
+                                const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if ((trans != 0 && trans != 1) || m < 1 || n < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (m > 64 || n > 64) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32 || o.math != GLASS_MATH_FP32 || o.layout != GLASS_LAYOUT_COLMAJOR)
+        return GLASS_ERR_UNSUPPORTED;
+    const int ylen = trans ? n : m;
+    if (!operand_ok(A, lda, sA, m, n, false, o.layout) || !x || !y || sx < 0 || sy < ylen)
+        return GLASS_ERR_INVALID_VALUE;
+    Placement pl;
+    if (o.placement.scope == GLASS_SCOPE_AUTO) {
+        pl = m * n <= 64 ? Placement{SCOPE_THREAD, 2} : Placement{SCOPE_WARP, 4};
+        if (o.placement.pack != 0) pl.pack = o.placement.pack;
+    } else {
+        pl = Placement{o.placement.scope, o.placement.pack == 0 ? 1 : o.placement.pack};
+    }
+    if ((pl.scope != SCOPE_THREAD && pl.scope != SCOPE_WARP) || !valid_pack(pl.pack)) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_gemv(trans, m, n, alpha, make_mat(A, lda, sA, m, n, o.layout),
+                                 static_cast<const float *>(x), sx, beta, static_cast<float *>(y), sy, batch, pl,
+                                 reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_batched_trsv(int n, const void *L, int lda, long long sA, void *x, long long sx, int batch,
+                                const glass_opts *opts, glass_stream_t stream) {
+    return glass_batched_trsm(n, 1, L, lda, sA, x, n, sx, batch, opts, stream);
+}
+
+glass_status glass_batched_btd_matvec(int nb, int N, const void *D, const void *O, const void *x, void *y, int batch,
+                                      const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if (nb < 1 || N < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (nb > 32) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32 || o.math != GLASS_MATH_FP32 || o.layout != GLASS_LAYOUT_COLMAJOR)
+        return GLASS_ERR_UNSUPPORTED;
+    if (!D || (N > 1 && !O) || !x || !y) return GLASS_ERR_INVALID_VALUE;
+    if (o.placement.scope != GLASS_SCOPE_AUTO && o.placement.scope != GLASS_SCOPE_WARP) return GLASS_ERR_INVALID_VALUE;
+    const int pack = o.placement.pack == 0 ? 4 : o.placement.pack;
+    if (!valid_pack(pack)) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_btd_matvec(nb, N, static_cast<const float *>(D), static_cast<const float *>(O),
+                                       static_cast<const float *>(x), static_cast<float *>(y), batch, pack,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glass_status glass_batched_btd_posv(int nb, int N, void *D, void *O, void *b, int *info, int batch,
+                                    const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if (nb < 1 || N < 1 || batch < 0) return GLASS_ERR_INVALID_VALUE;
+    if (nb > 32) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32 || o.math != GLASS_MATH_FP32 || o.layout != GLASS_LAYOUT_COLMAJOR)
+        return GLASS_ERR_UNSUPPORTED;
+    if (!D || (N > 1 && !O) || !b || !info) return GLASS_ERR_INVALID_VALUE;
+    if (o.placement.scope != GLASS_SCOPE_AUTO && o.placement.scope != GLASS_SCOPE_WARP) return GLASS_ERR_INVALID_VALUE;
+    const int pack = o.placement.pack == 0 ? 2 : o.placement.pack;
+    if (!valid_pack(pack)) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_btd_posv(nb, N, static_cast<float *>(D), static_cast<float *>(O), static_cast<float *>(b),
+                                     info, batch, pack, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 glass_status glass_robo_placement(int op, int n, int batch, glass_placement *out) {
     if (out == nullptr || op < 0 || op >= GLASS_ROBO_NUM_OPS || batch < 0) return GLASS_ERR_INVALID_VALUE;
     const Placement pl = robo_resolve(op, n < 1 ? 1 : n, batch);

@@ -305,6 +305,15 @@ enum RoboOp {
 bool feasible_robo(int op, int n, Placement pl);
 cudaError_t launch_robo(int op, int n, const float *a, const float *b, long long sa, float *o1, float *o2, float *o3,
                         long long so, int *idx, int batch, Placement pl, cudaStream_t st);
+// k_blas.cu
+cudaError_t launch_dot(int n, const float *x, long long sx, const float *y, long long sy, float *out, int batch,
+                       Placement pl, cudaStream_t st);
+cudaError_t launch_gemv(int trans, int m, int n, float alpha, Mat A, const float *x, long long sx, float beta, float *y,
+                        long long sy, int batch, Placement pl, cudaStream_t st);
+cudaError_t launch_btd_matvec(int nb, int N, const float *D, const float *O, const float *x, float *y, int batch,
+                              int pack, cudaStream_t st);
+cudaError_t launch_btd_posv(int nb, int N, float *D, float *O, float *bx, int *info, int batch, int pack,
+                            cudaStream_t st);
 // k_mlp.cu
 size_t mlp_workspace(int rows);
 cudaError_t launch_mlp_forward(int din, const float *w, int rows, const float *X, float *Y,

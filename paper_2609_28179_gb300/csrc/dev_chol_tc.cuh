@@ -271,40 +271,49 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, boo
 }
 
 // One right-hand side held like the rows (x[q] = row lane + 32q) against L
-// in shared memory: x <- L^{-1} x down the columns of L, then x <- L^{-T} x
-// down the columns of the mirrored upper triangle (both column-oriented: one
-// broadcast and one fused multiply-add per row and step, no reductions).
+// in shared memory, for 32 < n <= 64: x <- L^{-1} x down the columns of L,
+// then x <- L^{-T} x down the columns of the mirrored upper triangle.  Each
+// half of the rows is a fully unrolled loop (the pivot's lane and slot known
+// at compile time): one shuffle and one fused multiply-add per slot and step,
+// column loads independent of the chain.
 template <int NMAX>
 __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&x)[Shape<NMAX>::R], int n) {
+    static_assert(NMAX == 64, "the tensor-core Cholesky serves orders 33..64");
     constexpr int LD = Shape<NMAX>::LD;
-    constexpr int R = Shape<NMAX>::R;
     const int lane = threadIdx.x & 31;
-    auto get = [&](int i) {
-        float s = x[0];
 #pragma unroll
-        for (int q = 1; q < R; ++q)
-            if ((i >> 5) == q) s = x[q];
-        return __shfl_sync(GLASS_FULL_MASK, s, i & 31);
-    };
-    for (int i = 0; i < n; ++i) {
-        const float yi = get(i) * dv[i];
-        const float *col = As + i * LD;
+    for (int i = 0; i < 32; ++i) {
+        const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+        const float c0 = As[i * LD + lane], c1 = As[i * LD + lane + 32];
+        if (lane == i) x[0] = yi;
+        else if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
+        x[1] = fmaf(-c1, yi, x[1]);  // rows >= n: zero factor rows keep x = 0
+    }
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int row = lane + 32 * q;
-            if (row == i) x[q] = yi;
-            else if (row > i && row < n) x[q] = fmaf(-col[row], yi, x[q]);
+    for (int i = 32; i < 64; ++i) {
+        if (i < n) {
+            const float yi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
+            const float c1 = As[i * LD + lane + 32];
+            if (lane + 32 == i) x[1] = yi;
+            else if (lane + 32 > i) x[1] = fmaf(-c1, yi, x[1]);
         }
     }
-    for (int i = n - 1; i >= 0; --i) {
-        const float xi = get(i) * dv[i];
-        const float *col = As + i * LD;
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int row = lane + 32 * q;
-            if (row == i) x[q] = xi;
-            else if (row < i) x[q] = fmaf(-col[row], xi, x[q]);
+    for (int i = 63; i >= 32; --i) {
+        if (i < n) {
+            const float xi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
+            const float c0 = As[i * LD + lane], c1 = As[i * LD + lane + 32];  // mirror: l_{i,row}
+            if (lane + 32 == i) x[1] = xi;
+            else if (lane + 32 < i) x[1] = fmaf(-c1, xi, x[1]);
+            x[0] = fmaf(-c0, xi, x[0]);
         }
+    }
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+        const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+        const float c0 = As[i * LD + lane];
+        if (lane == i) x[0] = xi;
+        else if (lane < i) x[0] = fmaf(-c0, xi, x[0]);
     }
 }
 

@@ -93,7 +93,7 @@ __device__ __forceinline__ void panel(float *As, int *prow, int n, int c0, int *
             for (int q = QLO + 1; q < R; ++q)
                 if (wq == q) sel = p[q][j];
             const float pv = __shfl_sync(GLASS_FULL_MASK, sel, wl);
-            const float rc = pv != 0.f ? 1.0f / pv : 0.f;
+            const float rc = pv != 0.f ? __frcp_rn(pv) : 0.f;  // the correctly rounded 1 / pv
             if (lane == 0) {
                 ipiv_s[cj] = ppos;
                 dv[cj] = rc;
@@ -251,37 +251,46 @@ __device__ __forceinline__ int getrf(float *As, int n, int *prow, int *ipiv_s, f
 
 // One right-hand side already gathered into logical row order (x[q] = row
 // lane + 32q of P b): unit-lower forward and column-oriented upper backward
-// sweeps against the packed factor.
+// sweeps against the packed factor, for 32 < n <= 64.  Each half of the
+// rows is a fully unrolled loop with the pivot's lane and register slot
+// known at compile time, so a step is one shuffle and one fused
+// multiply-add per slot, and the column loads do not wait on the chain.
 template <int NMAX>
 __device__ __forceinline__ void getrs(const float *As, const float *dv, float (&x)[Shape<NMAX>::R], int n) {
+    static_assert(NMAX == 64, "the tensor-core LU serves orders 33..64");
     constexpr int LD = Shape<NMAX>::LD;
-    constexpr int R = Shape<NMAX>::R;
     const int lane = threadIdx.x & 31;
-    auto get = [&](int i) {
-        float s = x[0];
 #pragma unroll
-        for (int q = 1; q < R; ++q)
-            if ((i >> 5) == q) s = x[q];
-        return __shfl_sync(GLASS_FULL_MASK, s, i & 31);
-    };
-    for (int i = 0; i < n; ++i) {
-        const float yi = get(i);
-        const float *col = As + i * LD;
+    for (int i = 0; i < 32; ++i) {  // rows 0..31 hold the pivots (n > 32)
+        const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i);
+        const float c0 = As[i * LD + lane], c1 = As[i * LD + lane + 32];
+        if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
+        x[1] = fmaf(-c1, yi, x[1]);  // rows >= n: zero factor rows keep x = 0
+    }
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int row = lane + 32 * q;
-            if (row > i && row < n) x[q] = fmaf(-col[row], yi, x[q]);
+    for (int i = 32; i < 64; ++i) {
+        if (i < n) {
+            const float yi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32);
+            const float c1 = As[i * LD + lane + 32];
+            if (lane + 32 > i) x[1] = fmaf(-c1, yi, x[1]);
         }
     }
-    for (int i = n - 1; i >= 0; --i) {
-        const float xi = get(i) * dv[i];
-        const float *col = As + i * LD;
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int row = lane + 32 * q;
-            if (row == i) x[q] = xi;
-            else if (row < i) x[q] = fmaf(-col[row], xi, x[q]);
+    for (int i = 63; i >= 32; --i) {
+        if (i < n) {
+            const float xi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
+            const float c0 = As[i * LD + lane], c1 = As[i * LD + lane + 32];
+            if (lane + 32 == i) x[1] = xi;
+            else if (lane + 32 < i) x[1] = fmaf(-c1, xi, x[1]);
+            x[0] = fmaf(-c0, xi, x[0]);
         }
+    }
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+        const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+        const float c0 = As[i * LD + lane];
+        if (lane == i) x[0] = xi;
+        else if (lane < i) x[0] = fmaf(-c0, xi, x[0]);
     }
 }
 

@@ -1,0 +1,139 @@
+"""Batched dot, GEMV, TRSV and the block-tridiagonal matvec and solve on the
+GPU, through the C ABI, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2609_28179_gb300 as g
+from paper_2609_28179_gb300 import workloads as W
+from tests.helpers import U32
+
+pytestmark = pytest.mark.gpu
+
+BATCH = 333
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2609_28179_gb300 import _build
+    _build.build()
+    g.lib()
+
+
+def _dev(x, dtype=np.float32):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=dtype)).cuda()
+
+
+def _host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.float64) if t.dtype != torch.int32 else t.cpu().numpy()
+
+
+def _nan(n):
+    import torch
+    return torch.full((max(1, n),), float("nan"), device="cuda")
+
+
+@pytest.mark.parametrize("n", [1, 7, 16, 33, 100, 1000])
+def test_dot_every_placement(n):
+    r = W.rng(300 + n)
+    sx, sy = n + 1, n + 3
+    x = r.standard_normal(BATCH * sx).astype(np.float32)
+    y = r.standard_normal(BATCH * sy).astype(np.float32)
+    ref = oracle.dot(n, x.astype(np.float64), y.astype(np.float64), BATCH, sx=sx, sy=sy)
+    absd = oracle.dot(n, np.abs(x).astype(np.float64), np.abs(y).astype(np.float64), BATCH, sx=sx, sy=sy)
+    for s, p in [(0, 1), (0, 4), (1, 1), (1, 8), (2, 1), (2, 4), (-1, 0)]:
+        out = _nan(BATCH)
+        g.check(g.glass_batched_dot(n, _dev(x), sx, _dev(y), sy, out, BATCH, g.make_opts(scope=s, pack=p)))
+        assert (np.abs(_host(out)[:BATCH] - ref) <= n * U32 * 2 * absd + 1e-30).all(), (n, s, p)
+
+
+@pytest.mark.parametrize("trans", [0, 1])
+@pytest.mark.parametrize("m,n", [(1, 1), (6, 6), (12, 5), (33, 64), (64, 40)])
+def test_gemv_every_placement(trans, m, n):
+    r = W.rng(310 + m + n + trans)
+    lda = m + 2
+    A = r.standard_normal(BATCH * lda * n).astype(np.float32)
+    xl, yl = (m, n) if trans else (n, m)
+    x = r.standard_normal(BATCH * xl).astype(np.float32)
+    y0 = r.standard_normal(BATCH * (yl + 1)).astype(np.float32)
+    ref = oracle.gemv(trans, m, n, 0.5, A.astype(np.float64), lda, lda * n, x.astype(np.float64), xl, 2.0,
+                      y0.astype(np.float64), yl + 1, BATCH)
+    absr = oracle.gemv(trans, m, n, 0.5, np.abs(A).astype(np.float64), lda, lda * n, np.abs(x).astype(np.float64),
+                       xl, 2.0, np.abs(y0).astype(np.float64), yl + 1, BATCH)
+    for s, p in [(0, 1), (0, 2), (1, 1), (1, 4), (-1, 0)]:
+        dy = _dev(y0)
+        g.check(g.glass_batched_gemv(trans, m, n, 0.5, _dev(A), lda, lda * n, _dev(x), xl, 2.0, dy, yl + 1, BATCH,
+                                     g.make_opts(scope=s, pack=p)))
+        got = _host(dy)
+        assert (np.abs(got - ref) <= (max(m, n) + 2) * 2 * U32 * absr + 1e-30).all(), (trans, m, n, s, p)
+        gaps = got.reshape(BATCH, yl + 1)[:, yl]
+        assert np.array_equal(gaps, y0.reshape(BATCH, yl + 1)[:, yl].astype(np.float64))
+
+
+@pytest.mark.parametrize("n", [3, 17, 64])
+def test_trsv_integer_exact(n):
+    L = W.int_lower_pow2_diag(n, 40, 320 + n)
+    X0 = W.int_matrix(n, 1, 40, 321 + n, -3, 3)
+    b = W.colmajor(L @ X0)
+    dx = _dev(b)
+    g.check(g.glass_batched_trsv(n, _dev(W.colmajor(L)), n, n * n, dx, n, 40))
+    assert np.array_equal(_host(dx).reshape(40, n), X0.reshape(40, n))
+
+
+def _btd(nb, N, batch, seed):
+    r = W.rng(seed)
+    D = r.standard_normal((batch, N, nb, nb))
+    D = D @ D.transpose(0, 1, 3, 2) + (2.0 * nb + 2.0) * np.eye(nb)
+    O = r.standard_normal((batch, max(N - 1, 0), nb, nb))
+    flat = lambda X: np.ascontiguousarray(X.transpose(0, 1, 3, 2)).reshape(-1).astype(np.float32)
+    return flat(D), flat(O) if N > 1 else np.zeros(1, np.float32)
+
+
+@pytest.mark.parametrize("nb,N", [(1, 1), (1, 9), (3, 5), (6, 16), (12, 8), (16, 3), (32, 2), (7, 33)])
+def test_btd_matvec_and_posv(nb, N):
+    batch = 67
+    D, O = _btd(nb, N, batch, 330 + nb + N)
+    r = W.rng(331)
+    x = r.standard_normal(batch * N * nb).astype(np.float32)
+    yref = oracle.btd_matvec(nb, N, D.astype(np.float64), O.astype(np.float64), x.astype(np.float64), batch)
+    yabs = oracle.btd_matvec(nb, N, np.abs(D).astype(np.float64), np.abs(O).astype(np.float64),
+                             np.abs(x).astype(np.float64), batch)
+    for pack in (1, 4):
+        y = _nan(batch * N * nb)
+        g.check(g.glass_batched_btd_matvec(nb, N, _dev(D), _dev(O), _dev(x), y, batch, g.make_opts(pack=pack)))
+        assert (np.abs(_host(y) - yref) <= 3 * nb * 2 * U32 * yabs + 1e-30).all(), (nb, N, pack)
+    b = r.standard_normal(batch * N * nb).astype(np.float32)
+    Xref, info = oracle.btd_posv(nb, N, D.astype(np.float64), O.astype(np.float64), b.astype(np.float64), batch)
+    assert (info == 0).all()
+    for pack in (1, 2, 8):
+        dD, dO, db = _dev(D), _dev(O), _dev(b)
+        dinfo = _dev(np.full(batch, -5, np.int32), np.int32)
+        g.check(g.glass_batched_btd_posv(nb, N, dD, dO, db, dinfo, batch, g.make_opts(pack=pack)))
+        assert (_host(dinfo) == 0).all()
+        X = _host(db)
+        assert np.abs(X - Xref).max() <= 1e-4 * np.abs(Xref).max(), (nb, N, pack)
+        # the factor in place: T = L L^T blockwise (check the diagonal blocks' recurrence on one problem)
+        Lb = _host(dD).reshape(batch, N, nb, nb).transpose(0, 1, 3, 2)
+        Wb = _host(dO).reshape(batch, max(N - 1, 0), nb, nb).transpose(0, 1, 3, 2) if N > 1 else None
+        Dm = D.astype(np.float64).reshape(batch, N, nb, nb).transpose(0, 1, 3, 2)
+        L0 = np.tril(Lb[0, 0])
+        assert np.abs(L0 @ L0.T - Dm[0, 0]).max() <= 1e-5 * np.abs(Dm[0, 0]).max()
+        if N > 1:
+            Om = O.astype(np.float64).reshape(batch, N - 1, nb, nb).transpose(0, 1, 3, 2)
+            assert np.abs(Wb[0, 0] @ L0.T - Om[0, 0]).max() <= 1e-5 * max(1.0, np.abs(Om[0, 0]).max())
+
+
+def test_btd_posv_reports_the_failing_global_column():
+    nb, N, batch = 2, 3, 4
+    D, O = _btd(nb, N, batch, 340)
+    Dm = D.reshape(batch, N, nb, nb)
+    Dm[1::2, 1] = -np.eye(2, dtype=np.float32)        # odd problems: block 1 indefinite
+    Om = O.reshape(batch, N - 1, nb, nb)
+    Om[1::2] = 0.0
+    _, info_ref = oracle.btd_posv(nb, N, D.astype(np.float64), O.astype(np.float64), np.zeros(batch * N * nb), batch)
+    dinfo = _dev(np.zeros(batch, np.int32), np.int32)
+    g.check(g.glass_batched_btd_posv(nb, N, _dev(D), _dev(O), _dev(np.zeros(batch * N * nb)), dinfo, batch))
+    assert np.array_equal(_host(dinfo), info_ref) and (info_ref[1::2] == 3).all()

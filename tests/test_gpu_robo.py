@@ -76,9 +76,10 @@ def test_quat_small_angles_and_identity():
 
 def test_se3_retract():
     T = W.se3_transforms(BATCH, 204).astype(np.float32)
-    xi = W.twists(BATCH, 205)
+    xi = W.twists(BATCH, 205).reshape(BATCH, 6)
     xi[:40] *= 1e-6                                     # small-angle branch
     xi[40:60, 3:] = 0.0                                 # pure translation
+    xi = xi.reshape(-1)
     ref = oracle.se3_retract(T.astype(np.float64), xi.astype(np.float64), BATCH)
     for s, p in PLACEMENTS:
         out = _empty(16 * BATCH)
