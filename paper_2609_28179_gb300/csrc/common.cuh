@@ -221,7 +221,7 @@ __device__ __forceinline__ void chol_diag(float d, bool fp64, float &l, float &r
         r = (float)(1.0 / s);
     } else {
         l = sqrtf(d);
-        r = 1.0f / l;
+        r = __frcp_rn(l);  // the correctly rounded 1 / l
     }
 }
 

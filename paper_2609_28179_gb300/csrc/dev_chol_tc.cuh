@@ -142,20 +142,26 @@ __device__ __forceinline__ void panel(float *As, int n, int c0, float *dv, float
     for (int q = QLO; q < R; ++q)
 #pragma unroll
         for (int k = 0; k < 16; ++k) p[q][k] = As[(c0 + k) * LD + lane + 32 * q];
+    // rows c0..c0+15 of column j go to segment j & 1
+    auto publish = [&](int j) {
+        float *buf = bc + 16 * (j & 1);
+#pragma unroll
+        for (int q = QLO; q < R; ++q) {
+            const int i = lane + 32 * q;
+            if (i >= c0 && i < c0 + 16) buf[i - c0] = p[q][j];
+        }
+    };
+    // Software pipeline: column j+1 is updated and published before the
+    // rest of column j's update, which hides the publish latency.
+    publish(0);
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         const int cj = c0 + j;
         if (cj < n) {
-            float *buf = bc + 16 * (j & 1);
-#pragma unroll
-            for (int q = QLO; q < R; ++q) {
-                const int i = lane + 32 * q;
-                if (i >= c0 && i < c0 + 16) buf[i - c0] = p[q][j];
-            }
             __syncwarp();
             float s[16];
             {
-                const float4 *b4 = reinterpret_cast<const float4 *>(buf);
+                const float4 *b4 = reinterpret_cast<const float4 *>(bc + 16 * (j & 1));
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const float4 v = b4[m];
@@ -172,9 +178,15 @@ __device__ __forceinline__ void panel(float *As, int n, int c0, float *dv, float
             if (lane == 0) dv[cj] = r;
 #pragma unroll
             for (int q = QLO; q < R; ++q) p[q][j] = (lane + 32 * q == cj) ? l : p[q][j] * r;
+            if (j + 1 < 16) {
+                const float l1 = s[j + 1] * r;
+#pragma unroll
+                for (int q = QLO; q < R; ++q) p[q][j + 1] = fmaf(-p[q][j], l1, p[q][j + 1]);
+                publish(j + 1);
+            }
 #pragma unroll
             for (int k = 0; k < 16; ++k) {  // fixed range: keeps p[][] in registers
-                if (k > j) {
+                if (k > j + 1) {
                     const float lkj = s[k] * r;
 #pragma unroll
                     for (int q = QLO; q < R; ++q) p[q][k] = fmaf(-p[q][j], lkj, p[q][k]);

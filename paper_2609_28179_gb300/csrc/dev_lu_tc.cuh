@@ -53,25 +53,33 @@ __device__ __forceinline__ void panel(float *As, int *prow, int n, int c0, int *
 #pragma unroll
         for (int k = 0; k < 16; ++k) p[q][k] = As[(c0 + k) * LD + row];
     }
+    // this lane's candidate for column j: largest |a|, then smallest position
+    auto candidate = [&](int j, unsigned &key, unsigned &kpos, int &kq) {
+        key = 0;
+        kpos = 0xffffffffu;
+        kq = QLO;
+#pragma unroll
+        for (int q = QLO; q < R; ++q) {
+            if (!done[q]) {
+                const unsigned kk = __float_as_uint(fabsf(p[q][j])) + 1u;
+                if (kk > key || (kk == key && (unsigned)pos[q] < kpos)) {
+                    key = kk;
+                    kpos = pos[q];
+                    kq = q;
+                }
+            }
+        }
+    };
+    // Software pipeline: column j+1 is updated first and its reduction is
+    // issued before the rest of column j's update, which hides its latency.
+    unsigned key, kpos, kmax;
+    int kq;
+    candidate(0, key, kpos, kq);
+    kmax = __reduce_max_sync(GLASS_FULL_MASK, key);
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         const int cj = c0 + j;
         if (cj < n) {
-            // this lane's candidate: largest |a|, then smallest position
-            unsigned key = 0, kpos = 0xffffffffu;
-            int kq = QLO;
-#pragma unroll
-            for (int q = QLO; q < R; ++q) {
-                if (!done[q]) {
-                    const unsigned kk = __float_as_uint(fabsf(p[q][j])) + 1u;
-                    if (kk > key || (kk == key && (unsigned)pos[q] < kpos)) {
-                        key = kk;
-                        kpos = pos[q];
-                        kq = q;
-                    }
-                }
-            }
-            const unsigned kmax = __reduce_max_sync(GLASS_FULL_MASK, key);
             unsigned tie = __ballot_sync(GLASS_FULL_MASK, key == kmax);
             if (__popc(tie) > 1) {
                 const unsigned pmin = __reduce_min_sync(GLASS_FULL_MASK, key == kmax ? kpos : 0xffffffffu);
@@ -93,34 +101,40 @@ __device__ __forceinline__ void panel(float *As, int *prow, int n, int c0, int *
             for (int q = QLO + 1; q < R; ++q)
                 if (wq == q) sel = p[q][j];
             const float pv = __shfl_sync(GLASS_FULL_MASK, sel, wl);
+            // a zero pivot (every candidate is zero) records info and eliminates
+            // nothing: rc = 0 makes the multipliers and the update vanish
             const float rc = pv != 0.f ? __frcp_rn(pv) : 0.f;  // the correctly rounded 1 / pv
             if (lane == 0) {
                 ipiv_s[cj] = ppos;
                 dv[cj] = rc;
             }
-            if (pv == 0.f) {
-                if (info == 0) info = cj + 1;
-                continue;
-            }
+            if (pv == 0.f && info == 0) info = cj + 1;
             float m[R];
 #pragma unroll
             for (int q = QLO; q < R; ++q) {
                 m[q] = p[q][j] * rc;
                 if (!done[q]) p[q][j] = m[q];
             }
+            auto update = [&](int k) {
+                float s = p[QLO][k];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {  // fixed range: keeps p[][] in registers
-                if (k > j) {
-                    float s = p[QLO][k];
+                for (int q = QLO + 1; q < R; ++q)
+                    if (wq == q) s = p[q][k];
+                const float pk = __shfl_sync(GLASS_FULL_MASK, s, wl);
 #pragma unroll
-                    for (int q = QLO + 1; q < R; ++q)
-                        if (wq == q) s = p[q][k];
-                    const float pk = __shfl_sync(GLASS_FULL_MASK, s, wl);
-#pragma unroll
-                    for (int q = QLO; q < R; ++q)
-                        if (!done[q]) p[q][k] = fmaf(-m[q], pk, p[q][k]);
+                for (int q = QLO; q < R; ++q)
+                    if (!done[q]) p[q][k] = fmaf(-m[q], pk, p[q][k]);
+            };
+            if (j + 1 < 16) {
+                update(j + 1);
+                if (cj + 1 < n) {
+                    candidate(j + 1, key, kpos, kq);
+                    kmax = __reduce_max_sync(GLASS_FULL_MASK, key);
                 }
             }
+#pragma unroll
+            for (int k = 0; k < 16; ++k)  // fixed range: keeps p[][] in registers
+                if (k > j + 1) update(k);
         }
     }
     // ---- 2. panel to its logical rows; permute the other columns and prow
