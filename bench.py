@@ -762,6 +762,30 @@ def extra_blas(peaks):
     return out
 
 
+def extra_fp64(peaks, sizes=(6, 32, 64), batch=16384):
+    """FP64 storage variants at the table's placement: time, GB/s and the
+    fraction of the measured FP64 FMA peak (glass_peak_probe kind 1)."""
+    from paper_2609_28179_gb300.cells import bytes_flops
+    from paper_2609_28179_gb300.tune import F64_OPS, F64Cell
+    pk = measure_peaks()["fp64_dfma"]["tflops"]
+    out = {"fp64_peak_tflops": pk}
+    for op in F64_OPS:
+        for n in sizes:
+            cell = F64Cell(op, n, batch, sets=4)
+            k = [0]
+
+            def fn():
+                cell.launch(k[0] % 4)
+                k[0] += 1
+            ms = _graph_time(fn, 4, setup=cell.restore)
+            fl = bytes_flops(op, n)[1] * batch
+            out[f"{op}:n{n}:b{batch}"] = {"us": round(ms * 1e3, 2), "gbs": cell.bytes / (ms / 1e3) / 1e9,
+                                          "frac_hbm": cell.bytes / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                          "gflops": fl / (ms / 1e3) / 1e9, "frac_fp64": fl / (ms / 1e3) / 1e12 / pk}
+            del cell
+    return out
+
+
 def run_extras(peaks, which):
     out = {}
     for name, fn in (("plain_posv_n6", lambda: extra_plain_posv(peaks)), ("mixed_size", lambda: extra_varsize(peaks)),
@@ -769,7 +793,7 @@ def run_extras(peaks, which):
                      ("learned_placement", extra_learned), ("latency", extra_latency),
                      ("batch_scaling", lambda: extra_batch_scaling(peaks)),
                      ("riccati_gain", lambda: extra_riccati(peaks)), ("robotics_ops", lambda: extra_robo(peaks)),
-                     ("blas_block_tridiagonal", lambda: extra_blas(peaks))):
+                     ("blas_block_tridiagonal", lambda: extra_blas(peaks)), ("fp64_storage", lambda: extra_fp64(peaks))):
         if which != "all" and name not in which.split(","):
             continue
         try:

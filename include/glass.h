@@ -99,7 +99,14 @@ typedef struct {
 } glass_placement;
 
 typedef struct {
-    int dtype;        /* glass_dtype of the stored operands (A/B of a GEMM) */
+    int dtype;        /* glass_dtype of the stored operands: GLASS_F32; GLASS_BF16
+                         for the A/B of a BF16 tensor-core GEMM; GLASS_F64 (the
+                         paper's fp64 sweep variants) for gemm, potrf, potrs,
+                         posv, trsm and getrf_getrs -- every operand, the
+                         strides in doubles, thread scope (n <= 8) or warp
+                         scope (n <= 64 while the packed problems fit shared
+                         memory), no refinement, FP64 divisions and square
+                         roots; its own measured placement table */
     int math;         /* glass_math */
     int layout;       /* glass_layout */
     glass_placement placement;

@@ -12,6 +12,7 @@
 #include "placement_table.h"
 #include "riccati_table.h"
 #include "robo_table.h"
+#include "fp64_table.h"
 
 namespace glass {
 
@@ -225,6 +226,39 @@ glass_status check_order(int n) {
     return GLASS_OK;
 }
 
+// ------------------------------------------------------ FP64 storage
+int f64_row(int op) {
+    switch (op) {
+        case GLASS_OP_GEMM: return 0;
+        case GLASS_OP_POSV:
+        case GLASS_OP_POTRF:
+        case GLASS_OP_POTRS: return 1;
+        case GLASS_OP_TRSM: return 2;
+        default: return 3;
+    }
+}
+
+glass_status f64_placement_of(int op, int n, int batch, const glass_opts &o, Placement &pl) {
+    if (o.math != GLASS_MATH_FP32 || o.layout != GLASS_LAYOUT_COLMAJOR) return GLASS_ERR_UNSUPPORTED;
+    if (o.placement.scope == GLASS_SCOPE_AUTO) {
+        const int ni = nearest_index(kF64N, kF64NumN, n);
+        const int bi = nearest_index(kF64B, kF64NumB, batch > 0 ? batch : 1);
+        pl = decode(kF64Table[f64_row(op)][ni][bi]);
+        if (o.placement.pack != 0) {
+            if (!valid_pack(o.placement.pack)) return GLASS_ERR_INVALID_VALUE;
+            pl.pack = o.placement.pack;
+        }
+        if (!feasible_f64(op, n, pl)) {
+            pl.scope = SCOPE_WARP;
+            while (!feasible_f64(op, n, pl) && pl.pack > 1) pl.pack >>= 1;
+        }
+    } else {
+        pl = Placement{o.placement.scope, o.placement.pack == 0 ? 1 : o.placement.pack};
+        if (!valid_pack(pl.pack)) return GLASS_ERR_INVALID_VALUE;
+    }
+    return feasible_f64(op, n, pl) ? GLASS_OK : GLASS_ERR_INVALID_VALUE;
+}
+
 // ------------------------------------------------- robotics operations
 Placement robo_resolve(int op, int n, int batch) {
     const int bi = nearest_index(kRoboB, kRoboNumB, batch > 0 ? batch : 1);
@@ -316,6 +350,17 @@ glass_status glass_batched_gemm(int m, int n, int k, const void *A, int lda, lon
             return GLASS_ERR_UNSUPPORTED;
         return from_cuda(launch_gemm_tc(n, o.math, A, B, static_cast<float *>(C), batch, st));
     }
+    if (o.dtype == GLASS_F64) {
+        if (!operand_ok(A, lda, sA, m, k, false, o.layout) || !operand_ok(B, ldb, sB, k, n, false, o.layout) ||
+            !operand_ok(C, ldc, sC, m, n, true, o.layout))
+            return GLASS_ERR_INVALID_VALUE;
+        const int mx = m > n ? (m > k ? m : k) : (n > k ? n : k);
+        Placement pl;
+        GLASS_TRY(f64_placement_of(GLASS_OP_GEMM, mx, batch, o, pl));
+        return from_cuda(launch_gemm_f64(m, n, k, static_cast<const double *>(A), lda, sA,
+                                         static_cast<const double *>(B), ldb, sB, static_cast<double *>(C), ldc, sC,
+                                         batch, pl, st));
+    }
     if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
     if (!operand_ok(A, lda, sA, m, k, false, o.layout) || !operand_ok(B, ldb, sB, k, n, false, o.layout) ||
         !operand_ok(C, ldc, sC, m, n, true, o.layout))
@@ -345,6 +390,13 @@ glass_status glass_batched_potrf(int n, void *A, int lda, long long sA, int *inf
     GLASS_TRY(check_order(n));
     if (batch < 0) return GLASS_ERR_INVALID_VALUE;
     if (batch == 0) return GLASS_OK;
+    if (o.dtype == GLASS_F64) {
+        if (!operand_ok(A, lda, sA, n, n, true, o.layout) || info == nullptr) return GLASS_ERR_INVALID_VALUE;
+        Placement pl;
+        GLASS_TRY(f64_placement_of(GLASS_OP_POTRF, n, batch, o, pl));
+        return from_cuda(launch_chol_f64(GLASS_OP_POTRF, n, 0, static_cast<double *>(A), lda, sA, nullptr, 1, 0, info,
+                                         batch, pl, reinterpret_cast<cudaStream_t>(stream)));
+    }
     if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
     if (!operand_ok(A, lda, sA, n, n, true, o.layout) || info == nullptr) return GLASS_ERR_INVALID_VALUE;
     Placement pl;
@@ -360,6 +412,15 @@ glass_status glass_batched_potrs(int n, int nrhs, const void *L, int lda, long l
     GLASS_TRY(check_order(n));
     if (nrhs < 0 || batch < 0) return GLASS_ERR_INVALID_VALUE;
     if (batch == 0 || nrhs == 0) return GLASS_OK;
+    if (o.dtype == GLASS_F64) {
+        if (!operand_ok(L, lda, sA, n, n, false, o.layout) || !operand_ok(B, ldb, sB, n, nrhs, true, o.layout))
+            return GLASS_ERR_INVALID_VALUE;
+        Placement pl;
+        GLASS_TRY(f64_placement_of(GLASS_OP_POTRS, n, batch, o, pl));
+        return from_cuda(launch_chol_f64(GLASS_OP_POTRS, n, nrhs, static_cast<double *>(const_cast<void *>(L)), lda,
+                                         sA, static_cast<double *>(B), ldb, sB, nullptr, batch, pl,
+                                         reinterpret_cast<cudaStream_t>(stream)));
+    }
     if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
     if (!operand_ok(L, lda, sA, n, n, false, o.layout) || !operand_ok(B, ldb, sB, n, nrhs, true, o.layout))
         return GLASS_ERR_INVALID_VALUE;
@@ -378,6 +439,16 @@ glass_status glass_batched_posv(int n, int nrhs, void *A, int lda, long long sA,
     if (nrhs < 0 || batch < 0) return GLASS_ERR_INVALID_VALUE;
     if (o.refine_steps < 0 || o.refine_steps > 1) return GLASS_ERR_UNSUPPORTED;
     if (batch == 0) return GLASS_OK;
+    if (o.dtype == GLASS_F64) {
+        if (o.refine_steps != 0) return GLASS_ERR_UNSUPPORTED;
+        if (!operand_ok(A, lda, sA, n, n, true, o.layout) || info == nullptr) return GLASS_ERR_INVALID_VALUE;
+        if (nrhs > 0 && !operand_ok(B, ldb, sB, n, nrhs, true, o.layout)) return GLASS_ERR_INVALID_VALUE;
+        Placement pl;
+        GLASS_TRY(f64_placement_of(GLASS_OP_POSV, n, batch, o, pl));
+        return from_cuda(launch_chol_f64(nrhs > 0 ? GLASS_OP_POSV : GLASS_OP_POTRF, n, nrhs, static_cast<double *>(A),
+                                         lda, sA, static_cast<double *>(B), ldb, sB, info, batch, pl,
+                                         reinterpret_cast<cudaStream_t>(stream)));
+    }
     if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
     if (!operand_ok(A, lda, sA, n, n, true, o.layout) || info == nullptr) return GLASS_ERR_INVALID_VALUE;
     if (nrhs > 0 && !operand_ok(B, ldb, sB, n, nrhs, true, o.layout)) return GLASS_ERR_INVALID_VALUE;
@@ -398,6 +469,15 @@ glass_status glass_batched_trsm(int n, int nrhs, const void *L, int lda, long lo
     if (nrhs < 0 || batch < 0) return GLASS_ERR_INVALID_VALUE;
     if (nrhs > 4096) return GLASS_ERR_UNSUPPORTED;
     if (batch == 0 || nrhs == 0) return GLASS_OK;
+    if (o.dtype == GLASS_F64) {
+        if (!operand_ok(L, lda, sA, n, n, false, o.layout) || !operand_ok(B, ldb, sB, n, nrhs, true, o.layout))
+            return GLASS_ERR_INVALID_VALUE;
+        Placement pl;
+        GLASS_TRY(f64_placement_of(GLASS_OP_TRSM, n, batch, o, pl));
+        return from_cuda(launch_chol_f64(GLASS_OP_TRSM, n, nrhs, static_cast<double *>(const_cast<void *>(L)), lda,
+                                         sA, static_cast<double *>(B), ldb, sB, nullptr, batch, pl,
+                                         reinterpret_cast<cudaStream_t>(stream)));
+    }
     if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
     if (!operand_ok(L, lda, sA, n, n, false, o.layout) || !operand_ok(B, ldb, sB, n, nrhs, true, o.layout))
         return GLASS_ERR_INVALID_VALUE;
@@ -416,6 +496,15 @@ glass_status glass_batched_getrf_getrs(int n, int nrhs, void *A, int lda, long l
     GLASS_TRY(check_order(n));
     if (nrhs < 0 || batch < 0) return GLASS_ERR_INVALID_VALUE;
     if (batch == 0) return GLASS_OK;
+    if (o.dtype == GLASS_F64) {
+        if (!operand_ok(A, lda, sA, n, n, true, o.layout) || ipiv == nullptr || info == nullptr)
+            return GLASS_ERR_INVALID_VALUE;
+        if (nrhs > 0 && !operand_ok(B, ldb, sB, n, nrhs, true, o.layout)) return GLASS_ERR_INVALID_VALUE;
+        Placement pl;
+        GLASS_TRY(f64_placement_of(GLASS_OP_GETRF_GETRS, n, batch, o, pl));
+        return from_cuda(launch_lu_f64(n, nrhs, static_cast<double *>(A), lda, sA, ipiv, static_cast<double *>(B),
+                                       ldb, sB, info, batch, pl, reinterpret_cast<cudaStream_t>(stream)));
+    }
     if (o.dtype != GLASS_F32) return GLASS_ERR_UNSUPPORTED;
     if (!operand_ok(A, lda, sA, n, n, true, o.layout) || ipiv == nullptr || info == nullptr)
         return GLASS_ERR_INVALID_VALUE;

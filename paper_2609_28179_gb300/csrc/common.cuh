@@ -314,6 +314,14 @@ cudaError_t launch_btd_matvec(int nb, int N, const float *D, const float *O, con
                               int pack, cudaStream_t st);
 cudaError_t launch_btd_posv(int nb, int N, float *D, float *O, float *bx, int *info, int batch, int pack,
                             cudaStream_t st);
+// k_fp64.cu (op = glass_op)
+bool feasible_f64(int op, int n, Placement pl);
+cudaError_t launch_gemm_f64(int m, int n, int k, const double *A, int lda, long long sA, const double *B, int ldb,
+                            long long sB, double *C, int ldc, long long sC, int batch, Placement pl, cudaStream_t st);
+cudaError_t launch_chol_f64(int op, int n, int nrhs, double *A, int lda, long long sA, double *B, int ldb, long long sB,
+                            int *info, int batch, Placement pl, cudaStream_t st);
+cudaError_t launch_lu_f64(int n, int nrhs, double *A, int lda, long long sA, int *ipiv, double *B, int ldb, long long sB,
+                          int *info, int batch, Placement pl, cudaStream_t st);
 // k_mlp.cu
 size_t mlp_workspace(int rows);
 cudaError_t launch_mlp_forward(int din, const float *w, int rows, const float *X, float *Y,

@@ -25,6 +25,8 @@ Usage (on the GPU):
   python -m paper_2609_28179_gb300.tune riccati-codegen        # -> csrc/riccati_table.h
   python -m paper_2609_28179_gb300.tune robo [--out FILE]      # robotics ops (Table II)
   python -m paper_2609_28179_gb300.tune robo-codegen           # -> csrc/robo_table.h
+  python -m paper_2609_28179_gb300.tune fp64 [--out FILE]      # FP64 storage variants
+  python -m paper_2609_28179_gb300.tune fp64-codegen           # -> csrc/fp64_table.h
 """
 from __future__ import annotations
 
@@ -490,6 +492,151 @@ static const unsigned char kRoboTable[{len(g.ROBO_OPS)}][{len(SWEEP_B)}] = {{
     return out
 
 
+F64_FILE = os.path.join(TUNING, "sm103_fp64.jsonl")
+F64_H = os.path.join(HERE, "csrc", "fp64_table.h")
+F64_OPS = ["gemm", "posv", "trsm", "getrf_getrs"]
+
+
+class F64Cell:
+    """FP64 device inputs of one (op, n, batch) cell; destructive operations
+    get `sets` copies restored (untimed) between replays."""
+
+    def __init__(self, op, n, batch, sets=1, seed=6000):
+        import torch
+        self.op, self.n, self.batch = op, n, batch
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed + n)
+        dd = dict(dtype=torch.float64, device="cuda")
+        eye = torch.eye(n, **dd)
+        if op == "gemm":
+            A, B = torch.randn(batch, n, n, generator=gen, **dd), torch.randn(batch, n, n, generator=gen, **dd)
+        elif op == "posv":
+            M = torch.randn(batch, n, n, generator=gen, **dd)
+            A, B = M @ M.transpose(1, 2) + n * eye, torch.randn(batch, n, 1, generator=gen, **dd)
+        elif op == "trsm":
+            A, B = torch.tril(torch.randn(batch, n, n, generator=gen, **dd)) + n * eye, \
+                torch.randn(batch, n, n, generator=gen, **dd)
+        else:
+            A, B = torch.randn(batch, n, n, generator=gen, **dd) + n * eye, torch.randn(batch, n, 1, generator=gen, **dd)
+        self.pristine = {"A": A.transpose(1, 2).contiguous().reshape(-1), "B": B.transpose(1, 2).contiguous().reshape(-1)}
+        self.k = n if op in ("gemm", "trsm") else 1
+        self.sets = sets if op != "gemm" else 1
+        self.work = [{k: v.clone() for k, v in self.pristine.items()} for _ in range(self.sets)] if op != "gemm" \
+            else [self.pristine]
+        self.out = torch.empty(batch * n * n, **dd) if op == "gemm" else None
+        self.info = torch.zeros(max(1, batch), dtype=torch.int32, device="cuda")
+        self.ipiv = torch.zeros(max(1, batch * n), dtype=torch.int32, device="cuda")
+        from paper_2609_28179_gb300.cells import bytes_flops
+        self.bytes = 2 * bytes_flops(op, n)[0] * batch  # FP64: twice the FP32 bytes
+
+    def restore(self):
+        if self.op != "gemm":
+            for w in self.work:
+                for key, v in w.items():
+                    v.copy_(self.pristine[key])
+
+    def launch(self, i=0, scope=-1, pack=0):
+        import paper_2609_28179_gb300 as g
+        w, n, B = self.work[i % len(self.work)], self.n, self.batch
+        o = g.make_opts(dtype=g.GLASS_F64, scope=scope, pack=pack)
+        if self.op == "gemm":
+            return g.glass_batched_gemm(n, n, n, w["A"], n, n * n, w["B"], n, n * n, self.out, n, n * n, B, o)
+        if self.op == "posv":
+            return g.glass_batched_posv(n, 1, w["A"], n, n * n, w["B"], n, n, self.info, B, o)
+        if self.op == "trsm":
+            return g.glass_batched_trsm(n, n, w["A"], n, n * n, w["B"], n, n * n, B, o)
+        return g.glass_batched_getrf_getrs(n, 1, w["A"], n, n * n, self.ipiv, w["B"], n, n, self.info, B, o)
+
+
+def fp64_sweep(out_path: str = F64_FILE, iters: int = 5, seed: int = 23):
+    """Thread and warp placements of the FP64 storage variants over the
+    sweep grid (n <= 8 for thread scope)."""
+    import torch
+    import paper_2609_28179_gb300 as g
+    from paper_2609_28179_gb300.cells import SWEEP_B, SWEEP_N
+    g.lib()
+    rng = random.Random(seed)
+    stream = torch.cuda.Stream()
+    with open(out_path, "w") as f:
+        for op in F64_OPS:
+            for n in SWEEP_N:
+                for batch in SWEEP_B:
+                    probe = F64Cell(op, n, 1)
+                    R = int(min(32, max(8, math.ceil(2 * L2_BYTES / max(1, probe.bytes * batch)))))
+                    cell = F64Cell(op, n, batch, sets=R)
+                    order = [(s, p) for s in (0, 1) for p in (1, 2, 4, 8) if not (s == 0 and n > 8)]
+                    rng.shuffle(order)
+                    meas = {}
+                    for scope, pack in order:
+                        st = cell.launch(0, scope, pack)
+                        if st != g.GLASS_OK:
+                            continue
+                        cell.restore()
+                        torch.cuda.synchronize()
+                        graph = torch.cuda.CUDAGraph()
+                        with torch.cuda.graph(graph, stream=stream):
+                            for r in range(R):
+                                cell.launch(r, scope, pack)
+                        samples = []
+                        for _ in range(iters):
+                            cell.restore()
+                            torch.cuda.synchronize()
+                            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            a.record()
+                            graph.replay()
+                            b.record()
+                            torch.cuda.synchronize()
+                            samples.append(a.elapsed_time(b) * 1e3 / R)
+                        del graph
+                        meas[(scope, pack)] = {"us": statistics.median(samples)}
+                        f.write(json.dumps({"op": op, "n": n, "batch": batch, "scope": scope, "pack": pack,
+                                            "us": meas[(scope, pack)]["us"], "samples": samples, "reps": R}) + "\n")
+                    f.flush()
+                    best = choose(meas)
+                    print(f"fp64 {op:12s} n={n:3d} B={batch:6d} best={g.SCOPE_NAMES[best[0]]}x{best[1]} "
+                          f"{meas[best]['us']:.2f}us", flush=True)
+                    del cell
+                    torch.cuda.empty_cache()
+
+
+def fp64_codegen(inp: str = F64_FILE, out: str = F64_H):
+    from paper_2609_28179_gb300.cells import SWEEP_B, SWEEP_N
+    cells = {}
+    with open(inp) as f:
+        for line in f:
+            r = json.loads(line)
+            cells.setdefault((r["op"], r["n"], r["batch"]), {})[(r["scope"], r["pack"])] = r
+    rows = []
+    for op in F64_OPS:
+        per_n = []
+        for n in SWEEP_N:
+            codes = []
+            for b in SWEEP_B:
+                s, p = choose(cells[(op, n, b)])
+                codes.append(str(s * 4 + int(math.log2(p))))
+            per_n.append("{" + ", ".join(codes) + "}")
+        rows.append(f"    /* {op} */ {{" + ", ".join(per_n) + "},")
+    text = f"""// fp64_table.h -- GENERATED by paper_2609_28179_gb300/tune.py; do not edit.
+// Placement of the FP64 storage variants per (op row, n, batch) cell: rows
+// gemm, posv (potrf/potrs), trsm, getrf_getrs; code = scope * 4 + log2(pack)
+// (Sec. IV-A: the fp64 half of the sweep).
+// source: {os.path.relpath(inp, os.path.dirname(HERE))} (GB300 measurements, 5 % dispatch margin)
+#pragma once
+namespace glass {{
+static const int kF64NumN = {len(SWEEP_N)};
+static const int kF64N[{len(SWEEP_N)}] = {{{", ".join(map(str, SWEEP_N))}}};
+static const int kF64NumB = {len(SWEEP_B)};
+static const int kF64B[{len(SWEEP_B)}] = {{{", ".join(map(str, SWEEP_B))}}};
+static const unsigned char kF64Table[{len(F64_OPS)}][{len(SWEEP_N)}][{len(SWEEP_B)}] = {{
+{chr(10).join(rows)}
+}};
+}}  // namespace glass
+"""
+    with open(out, "w") as f:
+        f.write(text)
+    return out
+
+
 def launch_cells(specs):
     """One launch of each cell 'op:n:batch[:scope:pack]' (device inputs)."""
     import torch
@@ -511,7 +658,7 @@ def launch_cells(specs):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("cmd", choices=["sweep", "random", "codegen", "launch", "riccati", "riccati-codegen", "robo",
-                                    "robo-codegen"])
+                                    "robo-codegen", "fp64", "fp64-codegen"])
     ap.add_argument("--cells", nargs="+", default=[])
     ap.add_argument("--out", default=None)
     ap.add_argument("--inp", default=GRID_FILE)
@@ -527,6 +674,10 @@ def main():
         launch_cells(args.cells)
     elif args.cmd == "riccati":
         riccati_sweep(args.out or RICCATI_FILE)
+    elif args.cmd == "fp64":
+        fp64_sweep(args.out or F64_FILE)
+    elif args.cmd == "fp64-codegen":
+        print(fp64_codegen(args.inp if args.inp != GRID_FILE else F64_FILE))
     elif args.cmd == "robo":
         robo_sweep(args.out or ROBO_FILE)
     elif args.cmd == "robo-codegen":

@@ -159,3 +159,14 @@ def test_riccati_placement_queries(L):
     assert not g.glass_riccati_feasible(64, 64, g.GLASS_SCOPE_WARP, 8)   # shared memory
     assert not g.glass_riccati_feasible(8, 8, g.GLASS_SCOPE_BLOCK, 4)    # 512 threads
     assert not g.glass_riccati_feasible(8, 8, g.GLASS_SCOPE_THREAD, 1)
+
+
+def test_fp64_storage_argument_rules(L):
+    o = g.make_opts(dtype=g.GLASS_F64, refine_steps=1)
+    assert g.glass_batched_posv(6, 1, BAD, 6, 36, BAD, 6, 6, BAD, 4, o, 0) == g.GLASS_ERR_UNSUPPORTED
+    o = g.make_opts(dtype=g.GLASS_F64, scope=g.GLASS_SCOPE_THREAD, pack=1)
+    assert g.glass_batched_getrf_getrs(9, 1, BAD, 9, 81, BAD, BAD, 9, 9, BAD, 4, o, 0) == g.GLASS_ERR_INVALID_VALUE
+    o = g.make_opts(dtype=g.GLASS_F64, scope=g.GLASS_SCOPE_BLOCK, pack=1)
+    assert g.glass_batched_trsm(6, 2, BAD, 6, 36, BAD, 6, 12, 4, o, 0) == g.GLASS_ERR_INVALID_VALUE
+    o = g.make_opts(dtype=g.GLASS_F64, layout=g.GLASS_LAYOUT_INTERLEAVED32)
+    assert g.glass_batched_gemm(4, 4, 4, BAD, 4, 16, BAD, 4, 16, BAD, 4, 16, 4, o, 0) == g.GLASS_ERR_UNSUPPORTED
