@@ -1,5 +1,5 @@
 // dev_chol_tc.cuh -- warp-scope blocked Cholesky with tensor-core trailing
-// updates, for orders 33..64 (below that the register form is faster).
+// updates, for orders 17..64 (NMAX 32 or 64).
 //
 // One warp owns one problem held in its shared memory, column-major with
 // pitch LD = NMAX + 8 (LD = 8 mod 32: every TF32 fragment load of the MMA
@@ -224,8 +224,12 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, boo
     int info = 0;
     for (int c0 = 0; c0 < n; c0 += 16) {
         // ---- 1. panel on the SIMT pipe
-        if (c0 < 32) panel<NMAX, 0>(As, n, c0, dv, bc, fp64diag, info);
-        else panel<NMAX, 1>(As, n, c0, dv, bc, fp64diag, info);
+        if constexpr (NMAX > 32) {
+            if (c0 < 32) panel<NMAX, 0>(As, n, c0, dv, bc, fp64diag, info);
+            else panel<NMAX, 1>(As, n, c0, dv, bc, fp64diag, info);
+        } else {
+            panel<NMAX, 0>(As, n, c0, dv, bc, fp64diag, info);
+        }
         // ---- 2. trailing update on the tensor cores, 16 x 16 per step
         float *wp = opaque(As);
         const int r0 = c0 + 16;
@@ -283,16 +287,37 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, boo
 }
 
 // One right-hand side held like the rows (x[q] = row lane + 32q) against L
-// in shared memory, for 32 < n <= 64: x <- L^{-1} x down the columns of L,
+// in shared memory, for 16 < n <= NMAX: x <- L^{-1} x down the columns of L,
 // then x <- L^{-T} x down the columns of the mirrored upper triangle.  Each
 // half of the rows is a fully unrolled loop (the pivot's lane and slot known
 // at compile time): one shuffle and one fused multiply-add per slot and step,
 // column loads independent of the chain.
 template <int NMAX>
 __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&x)[Shape<NMAX>::R], int n) {
-    static_assert(NMAX == 64, "the tensor-core Cholesky serves orders 33..64");
+    static_assert(NMAX == 32 || NMAX == 64, "orders 17..32 or 33..64");
     constexpr int LD = Shape<NMAX>::LD;
     const int lane = threadIdx.x & 31;
+    if constexpr (NMAX == 32) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (i < n) {
+                const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+                const float c0 = As[i * LD + lane];
+                if (lane == i) x[0] = yi;
+                else if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
+            }
+        }
+#pragma unroll
+        for (int i = 31; i >= 0; --i) {
+            if (i < n) {
+                const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+                const float c0 = As[i * LD + lane];
+                if (lane == i) x[0] = xi;
+                else if (lane < i) x[0] = fmaf(-c0, xi, x[0]);
+            }
+        }
+        return;
+    } else {
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
         const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
@@ -326,6 +351,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
         const float c0 = As[i * LD + lane];
         if (lane == i) x[0] = xi;
         else if (lane < i) x[0] = fmaf(-c0, xi, x[0]);
+    }
     }
 }
 

@@ -1,5 +1,5 @@
 // dev_lu_tc.cuh -- warp-scope blocked LU with partial pivoting and
-// tensor-core trailing updates, for orders 33..64.
+// tensor-core trailing updates, for orders 17..64 (NMAX 32 or 64).
 //
 // One warp owns one problem in its shared memory (column-major, pitch
 // LD = NMAX + 8, rows and columns beyond n zero).  Per 16-column panel:
@@ -180,8 +180,12 @@ __device__ __forceinline__ int getrf(float *As, int n, int *prow, int *ipiv_s, f
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     int info = 0;
     for (int c0 = 0; c0 < n; c0 += 16) {
-        if (c0 < 32) panel<NMAX, 0>(As, prow, n, c0, ipiv_s, dv, info);
-        else panel<NMAX, 1>(As, prow, n, c0, ipiv_s, dv, info);
+        if constexpr (NMAX > 32) {
+            if (c0 < 32) panel<NMAX, 0>(As, prow, n, c0, ipiv_s, dv, info);
+            else panel<NMAX, 1>(As, prow, n, c0, ipiv_s, dv, info);
+        } else {
+            panel<NMAX, 0>(As, prow, n, c0, ipiv_s, dv, info);
+        }
         float *wp = opaque(As);
         // ---- 3. U12 = L11^{-1} A12, one column per lane
         for (int c = c0 + 16 + lane; c < n; c += 32) {
@@ -265,15 +269,35 @@ __device__ __forceinline__ int getrf(float *As, int n, int *prow, int *ipiv_s, f
 
 // One right-hand side already gathered into logical row order (x[q] = row
 // lane + 32q of P b): unit-lower forward and column-oriented upper backward
-// sweeps against the packed factor, for 32 < n <= 64.  Each half of the
+// sweeps against the packed factor, for 16 < n <= NMAX.  Each half of the
 // rows is a fully unrolled loop with the pivot's lane and register slot
 // known at compile time, so a step is one shuffle and one fused
 // multiply-add per slot, and the column loads do not wait on the chain.
 template <int NMAX>
 __device__ __forceinline__ void getrs(const float *As, const float *dv, float (&x)[Shape<NMAX>::R], int n) {
-    static_assert(NMAX == 64, "the tensor-core LU serves orders 33..64");
+    static_assert(NMAX == 32 || NMAX == 64, "orders 17..32 or 33..64");
     constexpr int LD = Shape<NMAX>::LD;
     const int lane = threadIdx.x & 31;
+    if constexpr (NMAX == 32) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (i < n) {
+                const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i);
+                const float c0 = As[i * LD + lane];
+                if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
+            }
+        }
+#pragma unroll
+        for (int i = 31; i >= 0; --i) {
+            if (i < n) {
+                const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+                const float c0 = As[i * LD + lane];
+                if (lane == i) x[0] = xi;
+                else if (lane < i) x[0] = fmaf(-c0, xi, x[0]);
+            }
+        }
+        return;
+    } else {
 #pragma unroll
     for (int i = 0; i < 32; ++i) {  // rows 0..31 hold the pivots (n > 32)
         const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i);
@@ -305,6 +329,7 @@ __device__ __forceinline__ void getrs(const float *As, const float *dv, float (&
         const float c0 = As[i * LD + lane];
         if (lane == i) x[0] = xi;
         else if (lane < i) x[0] = fmaf(-c0, xi, x[0]);
+    }
     }
 }
 

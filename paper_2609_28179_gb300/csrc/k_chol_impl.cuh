@@ -514,7 +514,7 @@ cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *in
 }
 
 // Shared memory of the blocked tensor-core Cholesky, per warp (bytes).
-inline size_t tc_smem(int) { return (size_t)tc_floats<64>() * 4; }
+inline size_t tc_smem(int n) { return (size_t)(n > 32 ? tc_floats<64>() : tc_floats<32>()) * 4; }
 
 // Shared memory of the many-right-hand-side solve kernels, per problem
 // (bytes), for a team of T threads: column-per-thread up to order 32,
@@ -560,9 +560,12 @@ cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info
         return solve_cols_dispatch<32, false>(n, nrhs, A, B, batch, pack, st);
     } else {
         if constexpr (has_factor(OP) && !RF) {
-            if (n > 32) {
+            if (n > 16) {
                 const int grid = ceil_div(batch, pack);
-                return launch_k(k_chol_tc<OP, 64>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info, batch,
+                if (n > 32)
+                    return launch_k(k_chol_tc<OP, 64>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info,
+                                    batch, fp64diag);
+                return launch_k(k_chol_tc<OP, 32>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info, batch,
                                 fp64diag);
             }
         }
@@ -620,7 +623,7 @@ size_t smem_of(int n, int nrhs, Placement pl, int refine) {
             return (size_t)32 * pl.pack * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4;
         case SCOPE_WARP: {
             if (OP == C_TRSM) return solve_cols_per(n, nrhs, 32) * pl.pack;
-            if (has_factor(OP) && !refine && n > 32) return tc_smem(n) * pl.pack;
+            if (has_factor(OP) && !refine && n > 16) return tc_smem(n) * pl.pack;
             const int N = nmax_bucket(n);
             return (size_t)pl.pack * (N + (refine ? N * (N + 1) : 0)) * 4;
         }

@@ -216,7 +216,9 @@ size_t smem_lu(int n, int nrhs, Placement pl) {
     switch (pl.scope) {
         case SCOPE_THREAD: return (size_t)32 * pl.pack * (odd_stride(n * n) + (nrhs > 0 ? odd_stride(n * nrhs) : 0)) * 4;
         case SCOPE_WARP:
-            return n > 32 ? (size_t)pl.pack * lu_tc_floats<64>() * 4 : (size_t)pl.pack * 2 * 32 * 4;
+            return n > 32   ? (size_t)pl.pack * lu_tc_floats<64>() * 4
+                   : n > 16 ? (size_t)pl.pack * lu_tc_floats<32>() * 4
+                            : (size_t)pl.pack * 2 * 16 * 4;
         default: {
             const int N = n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64;
             const int f = N == 8 ? lu_team_floats<8>() : N == 16 ? lu_team_floats<16>()
@@ -262,11 +264,11 @@ cudaError_t launch_getrf_getrs(int n, int nrhs, Mat A, int *ipiv, Mat B, int *in
     if (pl.scope == SCOPE_WARP) {
         const int th = 32 * pl.pack;
         if (n > 32) return go(k_lu_tc<64>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
-        const int N = n <= 8 ? 8 : n <= 16 ? 16 : 32;
+        if (n > 16) return go(k_lu_tc<32>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
+        const int N = n <= 8 ? 8 : 16;
         const size_t sw = (size_t)pl.pack * 2 * N * 4;
         if (N == 8) return go(k_lu_warp<8>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
-        if (N == 16) return go(k_lu_warp<16>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
-        return go(k_lu_warp<32>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
+        return go(k_lu_warp<16>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
     }
     const int th = rows::T * pl.pack;
     if (n <= 8) return go(k_lu_rows<8>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
