@@ -239,10 +239,14 @@ constexpr int tc_floats() {
     return NMAX * tcwarp::Shape<NMAX>::LD + NMAX + 32;
 }
 
-// Warp scope, orders 33..64, no refinement: blocked Cholesky with
-// tensor-core trailing updates (dev_chol_tc.cuh) on the problem held in the
-// warp's shared memory; the solves run against L in shared memory.
-template <int OP, int NMAX>
+// Warp scope, orders 17..64: blocked Cholesky with tensor-core trailing
+// updates (dev_chol_tc.cuh) on the problem held in the warp's shared memory;
+// the solves run against L in shared memory.  RF: one refinement step per
+// right-hand side -- r = b - A x0 in FP64 from the original A (still intact
+// in global memory: the factor is written back last), dx = A^{-1} r with
+// the factor, x1 = x0 + dx.  (A shared-memory copy of A halves the resident
+// warps and measured slower: the residual is bound by the FP64 pipe.)
+template <int OP, int NMAX, bool RF>
 __global__ void __launch_bounds__(256, 1) k_chol_tc(int n, int nrhs, Mat A, Mat B, int *info, int batch, int fp64diag) {
     constexpr int LD = tcwarp::Shape<NMAX>::LD;
     constexpr int R = tcwarp::Shape<NMAX>::R;
@@ -265,6 +269,39 @@ __global__ void __launch_bounds__(256, 1) k_chol_tc(int n, int nrhs, Mat A, Mat 
                 x[q] = (i < n) ? B.cget(b, i, c) : 0.f;
             }
             tcwarp::potrs<NMAX>(As, dv, x, n);
+            if constexpr (RF) {
+                const float *ga = A.p + (long long)b * A.s;
+                double acc[R][2];  // two partial sums per row hide the FP64 latency
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int i = lane + 32 * q;
+                    acc[q][0] = (i < n) ? (double)B.cget(b, i, c) : 0.0;
+                    acc[q][1] = 0.0;
+                }
+#pragma unroll 2
+                for (int k = 0; k < n; ++k) {
+                    float xk = 0.f;
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        const float v = __shfl_sync(GLASS_FULL_MASK, x[q], k & 31);
+                        if ((k >> 5) == q) xk = v;
+                    }
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        const int i = lane + 32 * q;
+                        if (i < n) {  // the lower triangle holds a_ik = a_ki
+                            const float aik = i >= k ? ga[(long long)k * A.ld + i] : ga[(long long)i * A.ld + k];
+                            acc[q][k & 1] = fma(-(double)aik, (double)xk, acc[q][k & 1]);
+                        }
+                    }
+                }
+                float r[R];
+#pragma unroll
+                for (int q = 0; q < R; ++q) r[q] = (float)(acc[q][0] + acc[q][1]);
+                tcwarp::potrs<NMAX>(As, dv, r, n);
+#pragma unroll
+                for (int q = 0; q < R; ++q) x[q] += r[q];
+            }
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int i = lane + 32 * q;
@@ -559,14 +596,14 @@ cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info
     if constexpr (OP == C_TRSM) {
         return solve_cols_dispatch<32, false>(n, nrhs, A, B, batch, pack, st);
     } else {
-        if constexpr (has_factor(OP) && !RF) {
+        if constexpr (has_factor(OP)) {
             if (n > 16) {
                 const int grid = ceil_div(batch, pack);
                 if (n > 32)
-                    return launch_k(k_chol_tc<OP, 64>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info,
-                                    batch, fp64diag);
-                return launch_k(k_chol_tc<OP, 32>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info, batch,
-                                fp64diag);
+                    return launch_k(k_chol_tc<OP, 64, RF>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B,
+                                    info, batch, fp64diag);
+                return launch_k(k_chol_tc<OP, 32, RF>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info,
+                                batch, fp64diag);
             }
         }
         const int threads = 32 * pack;
@@ -623,7 +660,7 @@ size_t smem_of(int n, int nrhs, Placement pl, int refine) {
             return (size_t)32 * pl.pack * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4;
         case SCOPE_WARP: {
             if (OP == C_TRSM) return solve_cols_per(n, nrhs, 32) * pl.pack;
-            if (has_factor(OP) && !refine && n > 16) return tc_smem(n) * pl.pack;
+            if (has_factor(OP) && n > 16) return tc_smem(n) * pl.pack;
             const int N = nmax_bucket(n);
             return (size_t)pl.pack * (N + (refine ? N * (N + 1) : 0)) * 4;
         }

@@ -233,6 +233,75 @@ __global__ void __launch_bounds__(T) k_gemm_async(int n, Mat A, Mat B, Mat C, in
     }
 }
 
+// Block scope at order 64: the same staging with a 64-thread team, each
+// thread an 8 x 8 tile made of two 4-row and two 4-column halves 32 apart
+// (rows 4g..4g+3 and 32+4g..32+4g+3), so the 8 lanes of a quarter-warp
+// read 8 distinct 16-byte bank groups of A and share B (broadcast): per
+// four k, 16 16-byte reads feed 256 fused multiply-adds.
+template <int NMAX>
+__global__ void __launch_bounds__(64) k_gemm_async8(int n, Mat A, Mat B, Mat C, int batch) {
+    static_assert(NMAX == 64, "the 8x8 tiling covers a 64x64 product with 64 threads");
+    constexpr int LD = NMAX + 4;
+    extern __shared__ __align__(16) float smem[];
+    float *As = smem, *Bs = smem + NMAX * LD;
+    const int b = blockIdx.x;
+    const int rank = threadIdx.x;
+    const int q4 = n >> 2;
+    const float *ga = A.p + (long long)b * A.s, *gb = B.p + (long long)b * B.s;
+    for (int e = rank; e < n * q4; e += 64) {
+        const int c = e / q4, q = e - c * q4;
+        cp_async16(As + c * LD + 4 * q, ga + c * n + 4 * q);
+        cp_async16(Bs + c * LD + 4 * q, gb + c * n + 4 * q);
+    }
+    for (int e = rank; e < NMAX * NMAX; e += 64) {  // zero padding when n < NMAX
+        const int c = e / NMAX, r = e - c * NMAX;
+        if (r >= n || c >= n) { As[c * LD + r] = 0.f; Bs[c * LD + r] = 0.f; }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int rg = rank & 7, cg = rank >> 3;
+    const int i0 = 4 * rg, j0 = 4 * cg;  // halves at +0 and +32
+    float acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+#pragma unroll 1
+    for (int l = 0; l < NMAX; l += 4) {
+        float bq[8][4];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int j = j0 + (c & 3) + 32 * (c >> 2);
+            const float4 v = *reinterpret_cast<const float4 *>(Bs + j * LD + l);
+            bq[c][0] = v.x; bq[c][1] = v.y; bq[c][2] = v.z; bq[c][3] = v.w;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(As + (l + u) * LD + i0);
+            const float4 a1 = *reinterpret_cast<const float4 *>(As + (l + u) * LD + i0 + 32);
+            const float af[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(af[r], bq[c][u], acc[r][c]);
+        }
+    }
+    __syncthreads();
+    float *Cs = As;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int j = j0 + (c & 3) + 32 * (c >> 2);
+        *reinterpret_cast<float4 *>(Cs + j * LD + i0) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+        *reinterpret_cast<float4 *>(Cs + j * LD + i0 + 32) = make_float4(acc[4][c], acc[5][c], acc[6][c], acc[7][c]);
+    }
+    __syncthreads();
+    float *gc = C.p + (long long)b * C.s;
+    for (int e = rank; e < n * q4; e += 64) {
+        const int c = e / q4, q = e - c * q4;
+        __stcs(reinterpret_cast<float4 *>(gc + c * n + 4 * q), *reinterpret_cast<const float4 *>(Cs + c * LD + 4 * q));
+    }
+}
+
 template <typename K>
 cudaError_t go(K kern, int grid, int threads, size_t smem, cudaStream_t st, int m, int n, int k, const Mat &A,
                const Mat &B, const Mat &C, int batch) {
@@ -306,8 +375,8 @@ cudaError_t launch_gemm(int m, int n, int k, Mat A, Mat B, Mat C, int batch, Pla
             if ((e = prepare(k_gemm_async<32, 64>, sm)) != cudaSuccess) return e;
             k_gemm_async<32, 64><<<batch, 64, sm, st>>>(n, A, B, C, batch);
         } else {
-            if ((e = prepare(k_gemm_async<64, 256>, sm)) != cudaSuccess) return e;
-            k_gemm_async<64, 256><<<batch, 256, sm, st>>>(n, A, B, C, batch);
+            if ((e = prepare(k_gemm_async8<64>, sm)) != cudaSuccess) return e;
+            k_gemm_async8<64><<<batch, 64, sm, st>>>(n, A, B, C, batch);
         }
         return cudaPeekAtLastError();
     }

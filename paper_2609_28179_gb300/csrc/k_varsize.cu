@@ -12,12 +12,15 @@
 //    first, grid = resident CTAs of that instantiation): every warp takes
 //    the next ticket of its bucket with one atomic, solves instance
 //    order[start + ticket] with the warp primitive specialised for the
-//    bucket, and repeats.  One instantiation per bucket keeps each launch at
+//    bucket (the register-resident factorization up to order 16, the
+//    blocked tensor-core one in the warp's shared memory above), and
+//    repeats.  One instantiation per bucket keeps each launch at
 //    the register count of its own order.  No CTA ever waits on another.
 //
 // Everything the launch needs lives in the caller's workspace, so the pair
 // of kernels can be recorded in a CUDA graph and replayed.
 #include "dev_chol.cuh"
+#include "dev_chol_tc.cuh"
 
 namespace glass {
 namespace {
@@ -117,13 +120,48 @@ __device__ __forceinline__ int warp_posv_one(float *A, float *B, int n, int nrhs
     return info;
 }
 
+// The same with the blocked tensor-core Cholesky (orders 17..NMAX, NMAX 32
+// or 64) on the instance staged in the warp's shared memory As.
+template <int NMAX>
+__device__ __forceinline__ int warp_posv_tc(float *A, float *B, int n, int nrhs, float *As) {
+    constexpr int LD = tcwarp::Shape<NMAX>::LD;
+    constexpr int R = tcwarp::Shape<NMAX>::R;
+    float *dv = As + NMAX * LD, *bc = dv + NMAX;
+    const int lane = threadIdx.x & 31;
+    __syncwarp();  // the previous instance is done with As
+    tcwarp::stage<NMAX, true>(As, A, n, n);
+    const int info = tcwarp::potrf<NMAX>(As, n, dv, bc, false);
+    for (int c = 0; c < nrhs; ++c) {
+        float x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = lane + 32 * q;
+            x[q] = (i < n) ? __ldcs(B + c * n + i) : 0.f;
+        }
+        tcwarp::potrs<NMAX>(As, dv, x, n);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = lane + 32 * q;
+            if (i < n) __stcs(B + c * n + i, x[q]);
+        }
+    }
+    tcwarp::unstage<NMAX, true>(A, n, As, n);
+    return info;
+}
+
+// Shared-memory floats per warp of a bucket.
+template <int NMAX>
+constexpr int bucket_floats() {
+    return NMAX >= 32 ? NMAX * (NMAX + 8) + NMAX + 32 : NMAX;
+}
+
 template <int NMAX>
 __global__ void __launch_bounds__(256) k_varsize_posv(const int *__restrict__ n_dev, const long long *__restrict__ offA,
                                                       const long long *__restrict__ offB, int nrhs, float *A, float *B,
                                                       int *__restrict__ info, VarWs *ws, int bucket) {
     extern __shared__ __align__(16) float vsm[];
     const int lane = threadIdx.x & 31;
-    float *col = vsm + (threadIdx.x >> 5) * NMAX;
+    float *col = vsm + (threadIdx.x >> 5) * bucket_floats<NMAX>();
     const int *order = reinterpret_cast<const int *>(ws + 1);
     const int start = ws->bstart[bucket], count = ws->bcount[bucket];
     // software pipeline: lane 0 takes the next ticket and fetches that
@@ -147,7 +185,9 @@ __global__ void __launch_bounds__(256) k_varsize_posv(const int *__restrict__ n_
                 ob2 = offB[i2];
             }
         }
-        const int inf = warp_posv_one<NMAX>(A + oa, B + ob, n, nrhs, col);
+        int inf;
+        if constexpr (NMAX >= 32) inf = warp_posv_tc<NMAX>(A + oa, B + ob, n, nrhs, col);
+        else inf = warp_posv_one<NMAX>(A + oa, B + ob, n, nrhs, col);
         if (lane == 0) info[i] = inf;
         t = __shfl_sync(GLASS_FULL_MASK, t2, 0);
         i = __shfl_sync(GLASS_FULL_MASK, i2, 0);
@@ -161,7 +201,9 @@ template <int NMAX>
 cudaError_t launch_bucket(int batch, const int *n_dev, const long long *offA, const long long *offB, int nrhs, float *A,
                           float *B, int *info, VarWs *w, int warps_per_cta, int bucket, int sms, cudaStream_t st) {
     const int threads = 32 * warps_per_cta;
-    const size_t sm = (size_t)warps_per_cta * NMAX * 4;
+    const size_t sm = (size_t)warps_per_cta * bucket_floats<NMAX>() * 4;
+    cudaError_t pe = prepare_kernel(reinterpret_cast<const void *>(k_varsize_posv<NMAX>), sm);
+    if (pe != cudaSuccess) return pe;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_varsize_posv<NMAX>, threads, sm);
     if (e != cudaSuccess) return e;
