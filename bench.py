@@ -9,7 +9,9 @@ placement (one thread per problem where feasible, else one warp: "plain") is
 timed beside it.
 
 Reported (one JSON line):
-  value       batched matrices/s of the tuned step, inputs resident in HBM;
+  value       batched matrices/s of the tuned step, inputs resident in HBM,
+              the K timed steps replayed as one CUDA graph (the library's
+              calls are capture-safe; per-cell times likewise);
   e2e         the same through host buffers (pinned H2D of every input and
               D2H of every result inside the timed region);
   roofline    of the dominant kernel (largest share of the step), from CUDA
@@ -129,28 +131,60 @@ def resolved_placement(cell):
     return pl
 
 
-def time_steps(cells, placements, steps, warmup, stream_events=True):
-    """Run warmup + steps passes; returns (total_ms, per-cell mean ms)."""
+def time_steps(cells, placements, steps, warmup, barrier=None):
+    """Warm up with `warmup` eager passes, then time `steps` passes of the
+    step captured in one CUDA graph (the library's calls never allocate,
+    synchronise or read device memory on the host, so a step records as a
+    graph and replays without host launch gaps).  Every destructive cell
+    reads its own fresh input copy in each pass; the copies are restored,
+    untimed, before the replay.  Per-cell times come the same way from a
+    graph of that cell's `steps` launches.  Returns (total_ms, per-cell ms)."""
     import torch
     import paper_2609_28179_gb300 as g
-    nc = len(cells)
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-          for _ in range(nc)]
     for w in range(warmup):
         for c, (s, p) in zip(cells, placements):
             g.check(c.launch(w, s, p), f"{c.op} n={c.n}")
     torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for st in range(steps):
-        for ci, (c, (s, p)) in enumerate(zip(cells, placements)):
-            ev[ci][st][0].record()
-            c.launch(warmup + st, s, p)
-            ev[ci][st][1].record()
-    t1.record()
+
+    def restore_all():
+        for c in cells:
+            c.restore()
+        torch.cuda.synchronize()
+
+    def replay_ms(graph):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    cap = torch.cuda.Stream()
+    per = []
+    for c, (s, p) in zip(cells, placements):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=cap):
+            for st in range(steps):
+                c.launch(warmup + st, s, p)
+        c.restore()
+        torch.cuda.synchronize()
+        per.append(replay_ms(gr) / steps)
+        del gr
+    step = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(step, stream=cap):
+        for st in range(steps):
+            for c, (s, p) in zip(cells, placements):
+                c.launch(warmup + st, s, p)
+    restore_all()
+    replay_ms(step)          # first replay uploads the graph; not timed
+    restore_all()
+    if barrier:
+        barrier()
     torch.cuda.synchronize()
-    total = t0.elapsed_time(t1)
-    per = [statistics.mean(a.elapsed_time(b) for a, b in ev[ci]) for ci in range(nc)]
+    total = replay_ms(step)  # ends with a synchronize
+    if barrier:
+        barrier()
+    del step
     return total, per
 
 
@@ -856,13 +890,13 @@ def main():
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as cs:
-        t_tuned, per_tuned = time_steps(cells, tuned, args.steps, args.warmup)
+        t_tuned, per_tuned = time_steps(cells, tuned, args.steps, args.warmup, barrier)
     clocks = cs.summary()
     barrier()
     for c in cells:
         c.restore()
     torch.cuda.synchronize()
-    t_plain, per_plain = time_steps(cells, plain, args.steps, args.warmup)
+    t_plain, per_plain = time_steps(cells, plain, args.steps, args.warmup, barrier)
     t_e2e = h2d = d2h = None
     if not args.no_e2e:
         t_e2e, h2d, d2h = e2e_steps(cells, args.steps, args.warmup)
