@@ -49,15 +49,14 @@ struct Shape {
 };
 
 // Stage the column-major n x n operand at ga (leading dimension lda) into As
-// (pitch LD) with cp.async copies, every copy of the lane in flight at once:
+// (pitch LD, a multiple of 4) with cp.async copies, every copy of the lane in flight at once:
 // 16-byte copies when n and lda are multiples of 4 and ga is 16-byte aligned,
 // 4-byte copies otherwise.  Everything outside the operand is zero; LOWER
 // skips what lies above the diagonal (16-byte groups wholly above it in the
 // vector form) and leaves it zero or as read -- it is never used.  Ends with
 // the copies complete and visible to the warp.
-template <int NMAX, bool LOWER>
+template <int NMAX, bool LOWER, int LD = Shape<NMAX>::LD>
 __device__ __forceinline__ void stage(float *As, const float *ga, long long lda, int n) {
-    constexpr int LD = Shape<NMAX>::LD;
     constexpr int R = Shape<NMAX>::R;
     const int lane = threadIdx.x & 31;
     const bool vec = (n & 3) == 0 && (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(ga) & 15) == 0;
@@ -87,9 +86,8 @@ __device__ __forceinline__ void stage(float *As, const float *ga, long long lda,
 // Write the n x n result in As back to ga (LOWER: the lower triangle only,
 // the rest of ga keeps its contents), 16-byte stores where whole 16-byte
 // groups are written and the operand is aligned as for stage().
-template <int NMAX, bool LOWER>
+template <int NMAX, bool LOWER, int LD = Shape<NMAX>::LD>
 __device__ __forceinline__ void unstage(float *ga, long long lda, const float *As, int n) {
-    constexpr int LD = Shape<NMAX>::LD;
     constexpr int R = Shape<NMAX>::R;
     const int lane = threadIdx.x & 31;
     const bool vec = (n & 3) == 0 && (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(ga) & 15) == 0;
@@ -298,7 +296,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
     constexpr int LD = Shape<NMAX>::LD;
     const int lane = threadIdx.x & 31;
     if constexpr (NMAX == 32) {
-#pragma unroll
+#pragma unroll 4
         for (int i = 0; i < 32; ++i) {
             if (i < n) {
                 const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
@@ -307,7 +305,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
                 else if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
             }
         }
-#pragma unroll
+#pragma unroll 4
         for (int i = 31; i >= 0; --i) {
             if (i < n) {
                 const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
@@ -318,7 +316,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
         }
         return;
     } else {
-#pragma unroll
+#pragma unroll 4
     for (int i = 0; i < 32; ++i) {
         const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
         const float c0 = As[i * LD + lane], c1 = As[i * LD + lane + 32];
@@ -326,7 +324,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
         else if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
         x[1] = fmaf(-c1, yi, x[1]);  // rows >= n: zero factor rows keep x = 0
     }
-#pragma unroll
+#pragma unroll 4
     for (int i = 32; i < 64; ++i) {
         if (i < n) {
             const float yi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
@@ -335,7 +333,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
             else if (lane + 32 > i) x[1] = fmaf(-c1, yi, x[1]);
         }
     }
-#pragma unroll
+#pragma unroll 4
     for (int i = 63; i >= 32; --i) {
         if (i < n) {
             const float xi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
@@ -345,7 +343,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
             x[0] = fmaf(-c0, xi, x[0]);
         }
     }
-#pragma unroll
+#pragma unroll 4
     for (int i = 31; i >= 0; --i) {
         const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
         const float c0 = As[i * LD + lane];

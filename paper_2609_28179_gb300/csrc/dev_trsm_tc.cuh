@@ -4,7 +4,7 @@
 //
 // A team of T threads owns one problem: L (lower triangle, pitch LD) and
 // 1/l_ii in shared memory, shared by the team; each warp solves chunks of 32
-// right-hand sides held in its own shared-memory buffer (pitch LD).  Per
+// right-hand sides held in its own shared-memory buffer (pitch LDB).  Per
 // 16-row block p of the forward sweep:
 //   1. X_p = L_pp^{-1} B_p on the SIMT pipe, one right-hand side per lane,
 //      the 16 values in registers and L_pp read as 16-byte broadcasts;
@@ -26,27 +26,28 @@ using tcwarp::mma_tf32;
 using tcwarp::split;
 
 constexpr int NMAX = 64;
-constexpr int LD = NMAX + 8;
+constexpr int LD = NMAX + 8;   // L: 8 mod 32, conflict-free A fragments
+constexpr int LDB = NMAX + 4;  // B chunks: 4 mod 32, conflict-free C/B fragments and column loads
 constexpr int CW = 32;  // right-hand sides per warp chunk
 
 // Shared-memory floats of one problem for a team of T threads.
 template <int T>
 constexpr int floats() {
-    return NMAX * LD + NMAX + (T / 32) * CW * LD;
+    return NMAX * LD + NMAX + (T / 32) * CW * LDB;
 }
 
 // Copy rows 0..n-1 of the first `cols` of `ncols` columns of a column-major
-// operand (leading dimension ld) into dst (pitch LD) with cp.async; zero
+// operand (leading dimension ld) into dst (pitch P) with cp.async; zero
 // the rest of the ncols x NMAX block.  `vec`: 16-byte copies (n, ld multiples
 // of 4 and a 16-byte aligned base).  LOWER: skip the 16-byte groups that lie
 // wholly above the diagonal (they are never read).  The caller waits.
 template <bool LOWER>
-__device__ __forceinline__ void stage_cols(float *dst, const float *src, long long ld, int n, int cols, int ncols,
-                                           bool vec, int rank, int T) {
+__device__ __forceinline__ void stage_cols(float *dst, int P, const float *src, long long ld, int n, int cols,
+                                           int ncols, bool vec, int rank, int T) {
     if (vec) {
         for (int e = rank; e < ncols * (NMAX / 4); e += T) {
             const int j = e >> 4, r = 4 * (e & 15);
-            float *d = dst + j * LD + r;
+            float *d = dst + j * P + r;
             if (j < cols && r < n) {
                 if (!LOWER || r + 3 >= j) cp_async16(d, src + (long long)j * ld + r);
             } else {
@@ -56,7 +57,7 @@ __device__ __forceinline__ void stage_cols(float *dst, const float *src, long lo
     } else {
         for (int e = rank; e < ncols * NMAX; e += T) {
             const int j = e >> 6, i = e & 63;
-            float *d = dst + j * LD + i;
+            float *d = dst + j * P + i;
             if (j < cols && i < n) {
                 if (!LOWER || i >= j) cp_async4(d, src + (long long)j * ld + i);
             } else {
@@ -73,12 +74,12 @@ __device__ __forceinline__ void store_cols(float *dst, long long ld, const float
         for (int e = lane; e < cols * (NMAX / 4); e += 32) {
             const int j = e >> 4, r = 4 * (e & 15);
             if (r < n) __stcs(reinterpret_cast<float4 *>(dst + (long long)j * ld + r),
-                              *reinterpret_cast<const float4 *>(src + j * LD + r));
+                              *reinterpret_cast<const float4 *>(src + j * LDB + r));
         }
     } else {
         for (int e = lane; e < cols * NMAX; e += 32) {
             const int j = e >> 6, i = e & 63;
-            if (i < n) dst[(long long)j * ld + i] = src[j * LD + i];
+            if (i < n) dst[(long long)j * ld + i] = src[j * LDB + i];
         }
     }
 }
@@ -128,18 +129,18 @@ __device__ __forceinline__ void update(const float *Ls, float *Bs, int p, int q)
     float acc[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
-        const float *c = Bs + (8 * nt + 2 * t) * LD + 16 * q + g;
+        const float *c = Bs + (8 * nt + 2 * t) * LDB + 16 * q + g;
         acc[nt][0] = c[0];
-        acc[nt][1] = c[LD];
+        acc[nt][1] = c[LDB];
         acc[nt][2] = c[8];
-        acc[nt][3] = c[LD + 8];
+        acc[nt][3] = c[LDB + 8];
     }
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
         unsigned bh[4][2], bl[4][2];
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
-            const float *x = Bs + (8 * nt + g) * LD + 16 * p + 8 * kk + t;
+            const float *x = Bs + (8 * nt + g) * LDB + 16 * p + 8 * kk + t;
             split(x[0], bh[nt][0], bl[nt][0]);
             split(x[4], bh[nt][1], bl[nt][1]);
         }
@@ -153,11 +154,11 @@ __device__ __forceinline__ void update(const float *Ls, float *Bs, int p, int q)
     float *wb = opaque(Bs);
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
-        float *c = wb + (8 * nt + 2 * t) * LD + 16 * q + g;
+        float *c = wb + (8 * nt + 2 * t) * LDB + 16 * q + g;
         c[0] = acc[nt][0];
-        c[LD] = acc[nt][1];
+        c[LDB] = acc[nt][1];
         c[8] = acc[nt][2];
-        c[LD + 8] = acc[nt][3];
+        c[LDB + 8] = acc[nt][3];
     }
 }
 
@@ -167,7 +168,7 @@ __device__ __forceinline__ void forward(const float *Ls, const float *dv, float 
     const int nb = (n + 15) >> 4;
     for (int p = 0; p < nb; ++p) {
         float x[16];
-        load16(Bs + lane * LD + 16 * p, x);
+        load16(Bs + lane * LDB + 16 * p, x);
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             float l[16];
@@ -177,7 +178,7 @@ __device__ __forceinline__ void forward(const float *Ls, const float *dv, float 
             for (int s = 0; s < 16; ++s)
                 if (s > r) x[s] = fmaf(-l[s], x[r], x[s]);
         }
-        store16(opaque(Bs) + lane * LD + 16 * p, x);
+        store16(opaque(Bs) + lane * LDB + 16 * p, x);
         __syncwarp();
         for (int q = p + 1; q < nb; ++q) update<false>(Ls, Bs, p, q);
         __syncwarp();
@@ -190,7 +191,7 @@ __device__ __forceinline__ void backward_t(const float *Ls, const float *dv, flo
     const int nb = (n + 15) >> 4;
     for (int p = nb - 1; p >= 0; --p) {
         float x[16];
-        load16(Bs + lane * LD + 16 * p, x);
+        load16(Bs + lane * LDB + 16 * p, x);
 #pragma unroll
         for (int r = 15; r >= 0; --r) {
             float l[16];
@@ -201,7 +202,7 @@ __device__ __forceinline__ void backward_t(const float *Ls, const float *dv, flo
                 if (k > r) s = fmaf(-l[k], x[k], s);
             x[r] = s * dv[16 * p + r];
         }
-        store16(opaque(Bs) + lane * LD + 16 * p, x);
+        store16(opaque(Bs) + lane * LDB + 16 * p, x);
         __syncwarp();
         for (int q = 0; q < p; ++q) update<true>(Ls, Bs, p, q);
         __syncwarp();

@@ -326,15 +326,16 @@ __global__ void __launch_bounds__(256, 1) k_solve_tc(int n, int nrhs, Mat L, Mat
     const int bar = 1 + team;
     float *Ls = smem + team * floats<T>();
     float *dv = Ls + NMAX * LD;
-    float *Bs = dv + NMAX + w * CW * LD;
+    float *Bs = dv + NMAX + w * CW * LDB;
     if (b >= batch || nrhs <= 0) return;  // whole team
     const float *gl = L.p + (long long)b * L.s;
     float *gb = B.p + (long long)b * B.s;
     const bool vec = (n & 3) == 0 && (L.ld & 3) == 0 && (B.ld & 3) == 0 &&
                      ((reinterpret_cast<uintptr_t>(gl) | reinterpret_cast<uintptr_t>(gb)) & 15) == 0;
-    stage_cols<true>(Ls, gl, L.ld, n, n, NMAX, vec, rank, T);
+    stage_cols<true>(Ls, LD, gl, L.ld, n, n, NMAX, vec, rank, T);
     int c0 = w * CW;
-    if (c0 < nrhs) stage_cols<false>(Bs, gb + (long long)c0 * B.ld, B.ld, n, min(CW, nrhs - c0), CW, vec, rank & 31, 32);
+    if (c0 < nrhs)
+        stage_cols<false>(Bs, LDB, gb + (long long)c0 * B.ld, B.ld, n, min(CW, nrhs - c0), CW, vec, rank & 31, 32);
     cp_async_wait_all();
     team_sync<T>(bar);
     for (int i = rank; i < NMAX; i += T) dv[i] = i < n ? 1.0f / Ls[i * LD + i] : 0.f;
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(256, 1) k_solve_tc(int n, int nrhs, Mat L, Mat
     for (bool first = true; c0 < nrhs; c0 += W * CW, first = false) {
         const int cols = min(CW, nrhs - c0);
         if (!first) {
-            stage_cols<false>(Bs, gb + (long long)c0 * B.ld, B.ld, n, cols, CW, vec, rank & 31, 32);
+            stage_cols<false>(Bs, LDB, gb + (long long)c0 * B.ld, B.ld, n, cols, CW, vec, rank & 31, 32);
             cp_async_wait_all();
             __syncwarp();
         }

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256, 1) k_lu_tc(int n, int nrhs, Mat A, int *i
     if (b >= batch) return;  // whole warp
 #pragma unroll
     for (int q = 0; q < R; ++q) prow[lane + 32 * q] = lane + 32 * q;
-    tcwarp::stage<NMAX, false>(As, A.p + (long long)b * A.s, A.ld, n);
+    tcwarp::stage<NMAX, false, LD>(As, A.p + (long long)b * A.s, A.ld, n);
     const int inf = tclu::getrf<NMAX>(As, n, prow, ps, dv);
     if (lane == 0) info[b] = inf;
     int *gp = ipiv + (long long)b * n;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256, 1) k_lu_tc(int n, int nrhs, Mat A, int *i
             if (i < n) B.cset(b, i, c, x[q]);
         }
     }
-    tcwarp::unstage<NMAX, false>(A.p + (long long)b * A.s, A.ld, As, n);
+    tcwarp::unstage<NMAX, false, LD>(A.p + (long long)b * A.s, A.ld, As, n);
 }
 
 constexpr int kRS = 4;
