@@ -296,7 +296,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
     constexpr int LD = Shape<NMAX>::LD;
     const int lane = threadIdx.x & 31;
     if constexpr (NMAX == 32) {
-#pragma unroll 4
+#pragma unroll
         for (int i = 0; i < 32; ++i) {
             if (i < n) {
                 const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
@@ -305,7 +305,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
                 else if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
             }
         }
-#pragma unroll 4
+#pragma unroll
         for (int i = 31; i >= 0; --i) {
             if (i < n) {
                 const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
@@ -316,7 +316,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
         }
         return;
     } else {
-#pragma unroll 4
+#pragma unroll
     for (int i = 0; i < 32; ++i) {
         const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
         const float c0 = As[i * LD + lane], c1 = As[i * LD + lane + 32];
@@ -324,7 +324,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
         else if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
         x[1] = fmaf(-c1, yi, x[1]);  // rows >= n: zero factor rows keep x = 0
     }
-#pragma unroll 4
+#pragma unroll
     for (int i = 32; i < 64; ++i) {
         if (i < n) {
             const float yi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
@@ -333,7 +333,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
             else if (lane + 32 > i) x[1] = fmaf(-c1, yi, x[1]);
         }
     }
-#pragma unroll 4
+#pragma unroll
     for (int i = 63; i >= 32; --i) {
         if (i < n) {
             const float xi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
@@ -343,7 +343,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
             x[0] = fmaf(-c0, xi, x[0]);
         }
     }
-#pragma unroll 4
+#pragma unroll
     for (int i = 31; i >= 0; --i) {
         const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
         const float c0 = As[i * LD + lane];

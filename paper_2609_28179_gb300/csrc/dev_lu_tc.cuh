@@ -282,7 +282,7 @@ __device__ __forceinline__ void getrs(const float *As, const float *dv, float (&
     constexpr int LD = Shape<NMAX>::LD;
     const int lane = threadIdx.x & 31;
     if constexpr (NMAX == 32) {
-#pragma unroll 4
+#pragma unroll
         for (int i = 0; i < 32; ++i) {
             if (i < n) {
                 const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i);
@@ -290,7 +290,7 @@ __device__ __forceinline__ void getrs(const float *As, const float *dv, float (&
                 if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
             }
         }
-#pragma unroll 4
+#pragma unroll
         for (int i = 31; i >= 0; --i) {
             if (i < n) {
                 const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
@@ -301,14 +301,14 @@ __device__ __forceinline__ void getrs(const float *As, const float *dv, float (&
         }
         return;
     } else {
-#pragma unroll 4
+#pragma unroll
     for (int i = 0; i < 32; ++i) {  // rows 0..31 hold the pivots (n > 32)
         const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i);
         const float c0 = As[i * LD + lane], c1 = As[i * LD + lane + 32];
         if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
         x[1] = fmaf(-c1, yi, x[1]);  // rows >= n: zero factor rows keep x = 0
     }
-#pragma unroll 4
+#pragma unroll
     for (int i = 32; i < 64; ++i) {
         if (i < n) {
             const float yi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32);
@@ -316,7 +316,7 @@ __device__ __forceinline__ void getrs(const float *As, const float *dv, float (&
             if (lane + 32 > i) x[1] = fmaf(-c1, yi, x[1]);
         }
     }
-#pragma unroll 4
+#pragma unroll
     for (int i = 63; i >= 32; --i) {
         if (i < n) {
             const float xi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
@@ -326,7 +326,7 @@ __device__ __forceinline__ void getrs(const float *As, const float *dv, float (&
             x[0] = fmaf(-c0, xi, x[0]);
         }
     }
-#pragma unroll 4
+#pragma unroll
     for (int i = 31; i >= 0; --i) {
         const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
         const float c0 = As[i * LD + lane];
