@@ -780,7 +780,7 @@ glass_status glass_batched_dot(int n, const void *x, long long sx, const void *y
     if (!x || !y || !out || sx < 0 || sy < 0) return GLASS_ERR_INVALID_VALUE;
     Placement pl;
     if (o.placement.scope == GLASS_SCOPE_AUTO) {
-        pl = n <= 8 ? Placement{SCOPE_THREAD, 4} : n <= 512 ? Placement{SCOPE_WARP, 4} : Placement{SCOPE_BLOCK, 2};
+        pl = n <= 32 ? Placement{SCOPE_THREAD, 4} : n <= 512 ? Placement{SCOPE_WARP, 4} : Placement{SCOPE_BLOCK, 2};
         if (o.placement.pack != 0) pl.pack = o.placement.pack;
     } else {
         pl = Placement{o.placement.scope, o.placement.pack == 0 ? 1 : o.placement.pack};

@@ -231,7 +231,10 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, boo
         // ---- 2. trailing update on the tensor cores, 16 x 16 per step
         float *wp = opaque(As);
         const int r0 = c0 + 16;
-        for (int R0 = r0; R0 < n; R0 += 16) {
+#pragma unroll
+        for (int rt = 0; rt < NMAX / 16 - 1; ++rt) {  // fixed trip counts: the tiles interleave
+            const int R0 = r0 + 16 * rt;
+            if (R0 >= n) break;
             unsigned ah[2][4], al[2][4];
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
@@ -241,7 +244,9 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, boo
                 split(-col[4 * LD + R0 + g], ah[kk][2], al[kk][2]);
                 split(-col[4 * LD + R0 + g + 8], ah[kk][3], al[kk][3]);
             }
-            for (int C0 = r0; C0 <= R0; C0 += 16) {
+#pragma unroll
+            for (int ct = 0; ct <= rt; ++ct) {
+                const int C0 = r0 + 16 * ct;
                 const bool two = C0 + 8 < n;
                 float *c = wp + (C0 + 2 * t) * LD + R0 + g;
                 float a0[4] = {c[0], c[LD], c[8], c[LD + 8]};

@@ -26,7 +26,19 @@ __global__ void __launch_bounds__(256) k_dot(int n, const float *x, long long sx
     if (b >= batch) return;  // whole team
     const float *xb = x + b * sx, *yb = y + b * sy;
     float s = 0.f;
-    for (int i = rank; i < n; i += T) s = fmaf(xb[i], yb[i], s);
+    if (T == 1 && (n & 3) == 0 && ((reinterpret_cast<uintptr_t>(xb) | reinterpret_cast<uintptr_t>(yb)) & 15) == 0) {
+        // one problem per thread: 16-byte loads (L1 keeps the rest of each line)
+        const float4 *x4 = reinterpret_cast<const float4 *>(xb), *y4 = reinterpret_cast<const float4 *>(yb);
+        for (int i = 0; i < (n >> 2); ++i) {
+            const float4 a = x4[i], c = y4[i];
+            s = fmaf(a.x, c.x, s);
+            s = fmaf(a.y, c.y, s);
+            s = fmaf(a.z, c.z, s);
+            s = fmaf(a.w, c.w, s);
+        }
+    } else {
+        for (int i = rank; i < n; i += T) s = fmaf(xb[i], yb[i], s);
+    }
     if constexpr (T > 1) s = warp_sum(s);
     if constexpr (T > 32) {
         const int w = threadIdx.x >> 5;
