@@ -36,10 +36,11 @@ def _nan(n):
     return torch.full((max(1, n),), float("nan"), device="cuda")
 
 
-@pytest.mark.parametrize("n", [1, 7, 16, 33, 100, 1000])
-def test_dot_every_placement(n):
+@pytest.mark.parametrize("n,packed", [(1, False), (7, False), (16, False), (33, False), (100, False),
+                                      (1000, False), (16, True), (32, True)])
+def test_dot_every_placement(n, packed):
     r = W.rng(300 + n)
-    sx, sy = n + 1, n + 3
+    sx, sy = (n, n) if packed else (n + 1, n + 3)   # packed: the 16-byte thread-scope path
     x = r.standard_normal(BATCH * sx).astype(np.float32)
     y = r.standard_normal(BATCH * sy).astype(np.float32)
     ref = oracle.dot(n, x.astype(np.float64), y.astype(np.float64), BATCH, sx=sx, sy=sy)
