@@ -243,3 +243,47 @@ def test_mlp_adam_matches_oracle_step():
     sync()
     assert np.abs(host(dw) - wr).max() <= 1e-6
     assert np.abs(host(dm) - mr).max() <= 1e-6 and np.abs(host(dv) - vr).max() <= 1e-6
+
+
+@pytest.mark.parametrize("n", [24, 40, 64])
+def test_tensor_core_paths_with_padded_leading_dimensions(n):
+    """The blocked tensor-core kernels on operands that are not packed
+    (lda > n, batch strides with slack: the 4-byte staging path) against
+    the oracle on the same padded buffers; the padding stays untouched."""
+    import torch
+    batch, lda, ldb, nrhs = 70, n + 3, n + 1, 3
+    sA, sB = lda * n + 5, ldb * nrhs + 2
+
+    def pack(M, ld, s):
+        out = np.full(batch * s, 7.0, dtype=np.float32)
+        for b in range(batch):
+            for j in range(M.shape[2]):
+                out[b * s + j * ld: b * s + j * ld + M.shape[1]] = M[b, :, j]
+        return out
+    A = pack(W.from_colmajor(W.spd(n, batch, 1500 + n), batch, n, n), lda, sA)
+    G = pack(W.from_colmajor(W.general(n, batch, 1501 + n), batch, n, n), lda, sA)
+    B = pack(W.rng(1502 + n).standard_normal((batch, n, nrhs)), ldb, sB)
+    f64 = lambda x: x.astype(np.float64)
+    kw = dict(lda=lda, sA=sA, ldb=ldb, sB=sB)
+    info = torch.zeros(batch, dtype=torch.int32, device="cuda")
+
+    _, Xr, ir = oracle.posv(n, nrhs, f64(A), f64(B), batch, **kw)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    g.check(g.glass_batched_posv(n, nrhs, dA, lda, sA, dB, ldb, sB, info, batch,
+                                 g.make_opts(scope=g.GLASS_SCOPE_WARP, pack=2)))
+    assert (info.cpu().numpy() == 0).all() and (ir == 0).all()
+    assert np.abs(dB.cpu().numpy() - Xr).max() <= 1e-4 * np.abs(Xr).max()      # padding: 7 on both sides
+
+    _, _, Xr, _ = oracle.getrf_getrs(n, nrhs, f64(G), f64(B), batch, **kw)
+    dA, dB = torch.from_numpy(G).cuda(), torch.from_numpy(B).cuda()
+    ipiv = torch.zeros(batch * n, dtype=torch.int32, device="cuda")
+    g.check(g.glass_batched_getrf_getrs(n, nrhs, dA, lda, sA, ipiv, dB, ldb, sB, info, batch,
+                                        g.make_opts(scope=g.GLASS_SCOPE_WARP, pack=2)))
+    assert np.abs(dB.cpu().numpy() - Xr).max() <= 1e-4 * np.abs(Xr).max()
+
+    Lp = pack(np.tril(W.from_colmajor(W.general(n, batch, 1503 + n), batch, n, n)) + n * np.eye(n), lda, sA)
+    Xr = oracle.trsm(n, nrhs, f64(Lp), f64(B), batch, **kw)
+    dB = torch.from_numpy(B).cuda()
+    g.check(g.glass_batched_trsm(n, nrhs, torch.from_numpy(Lp).cuda(), lda, sA, dB, ldb, sB, batch,
+                                 g.make_opts(scope=g.GLASS_SCOPE_BLOCK, pack=2)))
+    assert np.abs(dB.cpu().numpy() - Xr).max() <= 1e-4 * np.abs(Xr).max()
