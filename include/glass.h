@@ -124,7 +124,13 @@ typedef struct {
  * 1 <= m, n, k <= 64.  With opts->math != FP32 the contraction runs on the
  * tensor cores: GLASS_MATH_BF16_TC requires opts->dtype == GLASS_BF16 (A and
  * B stored as bfloat16, C as FP32); the TF32 modes read FP32 A and B.
- * Tensor-core modes require m = n = k in {16, 32, 64}, packed colmajor. */
+ * Tensor-core modes require m = n = k in {16, 32, 64}, packed colmajor.
+ * Order 64 in 3xTF32 mode, and the FP32 block-scope placement (pack 1) of
+ * order 64 with packed, 16-byte aligned operands, run on the fifth-
+ * generation tensor cores (tcgen05, operands in shared memory, accumulator
+ * in tensor memory; each error within the FP32 bound 2 k u |A||B|).  That
+ * kernel's waits are bounded: one that gives up records GLASS_ERR_TIMEOUT
+ * for glass_last_device_status. */
 glass_status glass_batched_gemm(int m, int n, int k,
                                 const void *A, int lda, long long sA,
                                 const void *B, int ldb, long long sB,

@@ -34,6 +34,11 @@ cudaError_t prepare_kernel(const void *fn, size_t bytes) {
 // Device status word (bounded waits that gave up, ...), one per device.
 __device__ unsigned g_device_status;
 
+unsigned *device_status_word() {
+    unsigned *p = nullptr;
+    return cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_device_status) == cudaSuccess ? p : nullptr;
+}
+
 namespace {
 
 const glass_opts kDefaultOpts = {GLASS_F32, GLASS_MATH_FP32, GLASS_LAYOUT_COLMAJOR, {GLASS_SCOPE_AUTO, 0}, 0, 0, 0};

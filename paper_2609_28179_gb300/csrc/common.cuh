@@ -267,6 +267,12 @@ bool feasible_gemm(int m, int n, int k, Placement pl);
 // k_gemm_tc.cu
 cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float *C, int batch,
                            cudaStream_t st);
+// Order-64 products on the fifth-generation tensor cores (3xTF32 split),
+// contiguous 16-byte aligned batches only.
+cudaError_t launch_gemm_umma64(const float *A, const float *B, float *C, int batch, cudaStream_t st);
+// capi.cu: the device status word of the current device (bounded device-side
+// waits that gave up record GLASS_ERR_TIMEOUT there), or null.
+unsigned *device_status_word();
 // k_geom.cu
 cudaError_t launch_rot3(int chain, Mat Rs, Mat R, int batch, Placement pl, cudaStream_t st);
 cudaError_t launch_se3(int chain, Mat T, int npts, Mat P, Mat Q, int batch, Placement pl,

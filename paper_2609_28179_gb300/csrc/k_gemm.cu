@@ -9,6 +9,8 @@
 // TM x TN register tile of C from 16-byte shared-memory fragments (the
 // warp's lanes share rows and columns, so fragments are mostly broadcasts);
 // C goes back through shared memory for fully coalesced streaming stores.
+// Block scope, pack 1, order 64 on packed 16-byte aligned operands goes to
+// the fifth-generation tensor cores instead (3xTF32, k_gemm_tc.cu).
 #include "common.cuh"
 
 namespace glass {
@@ -368,6 +370,7 @@ cudaError_t launch_gemm(int m, int n, int k, Mat A, Mat B, Mat C, int batch, Pla
                           A.packed() && B.packed() && C.packed() &&
                           ((reinterpret_cast<uintptr_t>(A.p) | reinterpret_cast<uintptr_t>(B.p) |
                             reinterpret_cast<uintptr_t>(C.p)) & 15) == 0;
+    if (async_ok && m == 64) return launch_gemm_umma64(A.p, B.p, C.p, batch, st);
     if (async_ok) {
         const size_t sm = (size_t)2 * N * (N + 4) * 4;
         cudaError_t e;

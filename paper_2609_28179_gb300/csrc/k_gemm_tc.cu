@@ -2,7 +2,9 @@
 // with FP32 accumulation: BF16 operands, TF32 operands, or 3xTF32 split
 // products (a = a_hi + a_lo with a_hi = tf32(a), a_lo = tf32(a - a_hi);
 // C += a_lo b_hi + a_hi b_lo + a_hi b_hi), the precision path the paper
-// lists as future work (Sec. V).
+// lists as future work (Sec. V).  The 3xTF32 product of order 64 runs on the
+// fifth-generation tensor cores (dev_umma.cuh), which also serve the FP32
+// block-scope GEMM of order 64; the others use warp-level mma.sync.
 //
 // Work split: n/16 warps per product, warp w owns rows 16w .. 16w+15 of C
 // and every 8-column block, so one A fragment serves n/8 MMAs.  A CTA holds
@@ -13,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "dev_umma.cuh"
 
 namespace glass {
 namespace {
@@ -214,6 +217,22 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16 *__restri
 
 }  // namespace
 
+cudaError_t launch_gemm_umma64(const float *A, const float *B, float *C, int batch, cudaStream_t st) {
+    if (batch <= 0) return cudaSuccess;
+    if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) != 0)
+        return cudaErrorInvalidConfiguration;
+    unsigned *status = device_status_word();
+    if (status == nullptr) return cudaErrorInvalidDeviceFunction;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    auto kern = umma::k_gemm_umma64<4, 2>;
+    if ((e = prepare(kern, umma::SMEM_BYTES)) != cudaSuccess) return e;
+    kern<<<batch < sms ? batch : sms, 32 * 9, umma::SMEM_BYTES, st>>>(A, B, C, batch, status);
+    return cudaPeekAtLastError();
+}
+
 cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float *C, int batch, cudaStream_t st) {
     // 16-byte staging needs 16-byte aligned operands
     if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) != 0)
@@ -242,7 +261,7 @@ cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float 
     }
     if (n == 16) TF(16, true);
     if (n == 32) TF(32, true);
-    TF(64, true);
+    return launch_gemm_umma64(a, b, C, batch, st);
 #undef TF
 }
 

@@ -94,6 +94,49 @@ def test_tc_gemm_gaussian_errors(n):
             assert rel.max() <= 1e-4
 
 
+# ------------------------------------------ fifth-generation tensor cores
+@pytest.mark.parametrize("batch", [1, 2, 151, 152, 153, 457])
+def test_umma_gemm64_batches_and_routes(batch):
+    """Order 64: the FP32 block-scope placement (packed, aligned operands)
+    and the 3xTF32 mode both run the persistent tcgen05 kernel -- one CTA
+    per SM, problems strided by the grid, so batches around the SM count
+    leave CTAs with 0, 1 or 2+ problems.  Both must meet the FP32 bound and
+    agree bit for bit; no bounded wait may have given up."""
+    n = 64
+    A = W.gaussian(batch * n * n, 2500 + batch)
+    B = W.gaussian(batch * n * n, 2600 + batch)
+    ref = oracle.gemm(n, n, n, A.astype(np.float64), B.astype(np.float64), batch)
+    bound = n * 2 * U32 * (np.abs(mats(A, batch, n, n)) @ np.abs(mats(B, batch, n, n))) + 1e-30
+    dA, dB = to_dev(A), to_dev(B)
+    out = []
+    for o in (g.make_opts(scope=2, pack=1), g.make_opts(math=g.GLASS_MATH_3XTF32_TC)):
+        dC = to_dev(np.full(batch * n * n, np.nan, np.float32))
+        g.check(g.glass_batched_gemm(n, n, n, dA, n, n * n, dB, n, n * n, dC, n, n * n, batch, o))
+        assert g.glass_last_device_status() == g.GLASS_OK
+        C = host(dC)
+        assert (np.abs(mats(C.astype(np.float64) - ref, batch, n, n)) <= bound).all()
+        out.append(C)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_umma_gemm64_unaligned_operands_take_the_simt_kernel():
+    """A 4-byte-offset operand cannot feed the bulk copies; the block-scope
+    call still returns the FP32-accurate product (through the SIMT kernel)."""
+    import torch
+    n, batch = 64, 40
+    A = W.gaussian(batch * n * n, 2700)
+    B = W.gaussian(batch * n * n, 2701)
+    ref = oracle.gemm(n, n, n, A.astype(np.float64), B.astype(np.float64), batch)
+    bound = n * 2 * U32 * (np.abs(mats(A, batch, n, n)) @ np.abs(mats(B, batch, n, n))) + 1e-30
+    bufA = torch.zeros(batch * n * n + 1, device="cuda")
+    bufA[1:] = torch.from_numpy(A).cuda()
+    dC = to_dev(np.zeros(batch * n * n, np.float32))
+    g.check(g.glass_batched_gemm(n, n, n, bufA[1:], n, n * n, to_dev(B), n, n * n, dC, n, n * n, batch,
+                                 g.make_opts(scope=2, pack=1)))
+    assert g.glass_last_device_status() == g.GLASS_OK
+    assert (np.abs(mats(host(dC).astype(np.float64) - ref, batch, n, n)) <= bound).all()
+
+
 # -------------------------------------------------------------- refinement
 @pytest.mark.parametrize("n", [8, 32, 64])
 @pytest.mark.parametrize("kappa", [1e1, 1e3])
