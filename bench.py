@@ -493,7 +493,9 @@ def extra_varsize(peaks, wpcs=(0, 2, 4, 8)):
 
 
 def extra_tc_gemm(peaks, batch=65536):
-    """Tensor-core batched GEMM, n in {16, 32, 64}, batch 65536, inputs N(0,1)."""
+    """Tensor-core batched GEMM, n in {16, 32, 64}, batch 65536, inputs N(0,1);
+    fp32_table is the FP32 call at the table's placement (SIMT kernels for
+    n = 16, 32; the tcgen05 3xTF32 kernel for n = 64)."""
     import torch
     import paper_2609_28179_gb300 as g
     out = {}
@@ -507,7 +509,7 @@ def extra_tc_gemm(peaks, batch=65536):
         for name, math_, dt, a, b, bpe in (("bf16", g.GLASS_MATH_BF16_TC, g.GLASS_BF16, Ab, Bb, 2),
                                            ("tf32", g.GLASS_MATH_TF32_TC, g.GLASS_F32, A, B, 4),
                                            ("3xtf32", g.GLASS_MATH_3XTF32_TC, g.GLASS_F32, A, B, 4),
-                                           ("fp32_simt", g.GLASS_MATH_FP32, g.GLASS_F32, A, B, 4)):
+                                           ("fp32_table", g.GLASS_MATH_FP32, g.GLASS_F32, A, B, 4)):
             o = g.make_opts(dtype=dt, math=math_)
             fn = lambda: g.glass_batched_gemm(n, n, n, a, n, n * n, b, n, n * n, C, n, n * n, batch, o)
             g.check(fn(), f"tc gemm {name}")
