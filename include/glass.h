@@ -128,7 +128,8 @@ typedef struct {
  * Order 64 in 3xTF32 mode, and the FP32 block-scope placement (pack 1) of
  * order 64 with packed, 16-byte aligned operands, run on the fifth-
  * generation tensor cores (tcgen05, operands in shared memory, accumulator
- * in tensor memory; each error within the FP32 bound 2 k u |A||B|).  That
+ * in tensor memory; that kernel also adds the lo*lo product; each error
+ * within the FP32 bound 2 k u |A||B|).  That
  * kernel's waits are bounded: one that gives up records GLASS_ERR_TIMEOUT
  * for glass_last_device_status. */
 glass_status glass_batched_gemm(int m, int n, int k,

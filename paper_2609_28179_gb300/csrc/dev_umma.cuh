@@ -1,16 +1,17 @@
 // dev_umma.cuh -- fifth-generation tensor cores (tcgen05 "UMMA") for the
-// batched order-64 GEMM: C = A B with FP32 operands through a 3xTF32 split
-// (a = a_hi + a_lo, a_hi = tf32(a), a_lo = tf32(a - a_hi); the product keeps
-// a_lo b_hi + a_hi b_lo + a_hi b_hi), FP32 accumulation in tensor memory.
+// batched order-64 GEMM: C = A B with FP32 operands through a TF32 split
+// (a = a_hi + a_lo, a_hi = tf32(a), a_lo = tf32(a - a_hi); the product sums
+// a_x b_y over x, y in {hi, lo}), FP32 accumulation in tensor memory.
 //
 // One persistent CTA per SM walks problems p = blockIdx.x,
 // blockIdx.x + gridDim.x, ... through a pipeline of three warp roles:
 //   - the issue warp has the bulk-copy engine (cp.async.bulk, completion on
 //     an mbarrier) bring problem i + 2's A and B (16 KB each, contiguous)
-//     into raw[i % 2], and issues problem i's 8 k-steps x 3 tcgen05.mma
-//     (M = N = 64, K = 8) into one of the tensor-memory accumulators;
-//   - the split warps turn problem i's raw operands into hi / lo tiles in
-//     the K-major 128-byte-swizzled layout in op[i % 2];
+//     into raw[i % 2], and issues problem i's 8 tcgen05.mma (one per K = 8
+//     step, M = N = 128 over the stacked hi / lo operands) into one of the
+//     tensor-memory accumulators;
+//   - the split warps turn problem i's raw operands into stacked hi / lo
+//     tiles in the K-major 128-byte-swizzled layout in op[i % 2];
 //   - the drain warps move finished accumulators (tcgen05.ld) to HBM.
 // Every wait is bounded (about a second of clock cycles); on a timeout the
 // CTA records the failure in a device status word, stops issuing work,
@@ -172,20 +173,23 @@ __device__ __forceinline__ void split4(const float (&x)[4], float4 &hi, float4 &
     lo = make_float4(l[0], l[1], l[2], l[3]);
 }
 
-// Tile geometry (64 x 64 FP32, K-major, 128-byte swizzle): element (r, k) of
-// an operand (r = row of A or column of B; c4 = k / 4 its 16-byte chunk) in
-// K-half k / 32 (8 KB each), row r at 128 r bytes, chunk c4 % 8 stored at
-// chunk position (c4 % 8) ^ (r % 8).  8-row groups are 1024 B apart (SBO);
-// the K = 8 step s starts 32 (s % 4) bytes into the rows of half s / 4, and
-// the hardware applies the same XOR to the addresses it forms (the tiles sit
-// on 1 KB boundaries).
-constexpr int TILE_FLOATS = 64 * 64;
+// Operand tiles: K-major with the 128-byte swizzle, hi and lo stacked into
+// one 128-row operand per matrix (rows 0-63 the hi parts, 64-127 the lo
+// parts of rows / columns 0-63).  Element (r, k) of the stacked operand
+// (r = row of A or column of B, c4 = k / 4 its 16-byte chunk) lies in K-half
+// k / 32 (16 KB each), row r at 128 r bytes, chunk c4 % 8 at chunk position
+// (c4 % 8) ^ (r % 8).  8-row groups are 1024 B apart (SBO); the K = 8 step s
+// starts 32 (s % 4) bytes into the rows of half s / 4, and the hardware
+// applies the same XOR to the addresses it forms (the tiles sit on 1 KB
+// boundaries).
+constexpr int TILE_FLOATS = 64 * 64;     // one raw 64 x 64 operand
+constexpr int PAIR_FLOATS = 2 * TILE_FLOATS;  // one stacked hi / lo operand
 
-__device__ __forceinline__ int kmajor_off(int r, int c4) {
-    return (c4 >> 3) * 2048 + r * 32 + (((c4 & 7) ^ (r & 7)) << 2);
+__device__ __forceinline__ int pair_off(int r, int c4) {  // r < 64: the hi part; + 2048 floats: the lo part
+    return (c4 >> 3) * 4096 + r * 32 + (((c4 & 7) ^ (r & 7)) << 2);
 }
-__device__ __forceinline__ uint64_t kstep_desc(uint32_t tile, int s) {
-    return desc_kmajor(tile + (s >> 2) * 8192 + (s & 3) * 32, 16, 1024) | (2ull << 61);
+__device__ __forceinline__ uint64_t kstep_desc(uint32_t pair, int s) {
+    return desc_kmajor(pair + (s >> 2) * 16384 + (s & 3) * 32, 16, 1024) | (2ull << 61);
 }
 
 // A (column-major, pitch 64), T threads: thread t splits row
@@ -193,7 +197,7 @@ __device__ __forceinline__ uint64_t kstep_desc(uint32_t tile, int s) {
 // scalar loads per chunk (consecutive m across a warp), and the eight rows
 // of a quarter-warp store to eight distinct chunk positions.
 template <int T>
-__device__ __forceinline__ void split_a(const float *raw, float *hi, float *lo, int t) {
+__device__ __forceinline__ void split_a(const float *raw, float *pair, int t) {
     const int w = t >> 5, m = (t & 31) + 32 * (w & 1);
 #pragma unroll
     for (int it = 0; it < 1024 / T; ++it) {
@@ -203,9 +207,9 @@ __device__ __forceinline__ void split_a(const float *raw, float *hi, float *lo, 
         for (int u = 0; u < 4; ++u) x[u] = raw[(4 * c4 + u) * 64 + m];
         float4 h, l;
         split4(x, h, l);
-        const int o = kmajor_off(m, c4);
-        *reinterpret_cast<float4 *>(hi + o) = h;
-        *reinterpret_cast<float4 *>(lo + o) = l;
+        const int o = pair_off(m, c4);
+        *reinterpret_cast<float4 *>(pair + o) = h;
+        *reinterpret_cast<float4 *>(pair + o + 2048) = l;
     }
 }
 
@@ -218,7 +222,7 @@ __device__ __forceinline__ void split_a(const float *raw, float *hi, float *lo, 
 __device__ __forceinline__ int gf8_alpha(int q) { return ((q << 1) & 7) ^ ((q & 4) ? 3 : 0); }
 
 template <int T>
-__device__ __forceinline__ void split_b(const float *raw, float *hi, float *lo, int t) {
+__device__ __forceinline__ void split_b(const float *raw, float *pair, int t) {
     const int q = t & 7, grp = t >> 3;
 #pragma unroll
     for (int it = 0; it < 1024 / T; ++it) {
@@ -228,59 +232,58 @@ __device__ __forceinline__ void split_b(const float *raw, float *hi, float *lo, 
         const float x[4] = {v.x, v.y, v.z, v.w};
         float4 h, l;
         split4(x, h, l);
-        const int o = kmajor_off(n, c4);
-        *reinterpret_cast<float4 *>(hi + o) = h;
-        *reinterpret_cast<float4 *>(lo + o) = l;
+        const int o = pair_off(n, c4);
+        *reinterpret_cast<float4 *>(pair + o) = h;
+        *reinterpret_cast<float4 *>(pair + o + 2048) = l;
     }
 }
 
-// The 24 MMAs of one product (8 k-steps x {a_lo b_hi, a_hi b_lo, a_hi b_hi})
-// into tensor-memory columns d .. d + 63.
-__device__ __forceinline__ void issue_3xtf32(uint32_t d, const float *ahi, const float *alo, const float *bhi,
-                                             const float *blo) {
-    constexpr uint32_t ID = idesc_tf32(64, 64);
-    const uint32_t a_h = smem_u32(ahi), a_l = smem_u32(alo), b_h = smem_u32(bhi), b_l = smem_u32(blo);
+// One product: per k-step a single M = N = 128 MMA of the stacked operands
+// forms all four products a_x b_y (x, y in {hi, lo}) in the quadrants of the
+// accumulator -- lane = row of the stacked A, columns d .. d + 127 = the
+// columns of the stacked B -- so C is the sum of the four quadrants (the
+// lo * lo quadrant comes at no extra cost).
+__device__ __forceinline__ void issue_split_product(uint32_t d, const float *ap, const float *bp) {
+    constexpr uint32_t ID = idesc_tf32(128, 128);
+    const uint32_t a = smem_u32(ap), b = smem_u32(bp);
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        mma_tf32(d, kstep_desc(a_l, s), kstep_desc(b_h, s), ID, s > 0 ? 1u : 0u);
-        mma_tf32(d, kstep_desc(a_h, s), kstep_desc(b_l, s), ID, 1u);
-        mma_tf32(d, kstep_desc(a_h, s), kstep_desc(b_h, s), ID, 1u);
-    }
+    for (int s = 0; s < 8; ++s) mma_tf32(d, kstep_desc(a, s), kstep_desc(b, s), ID, s > 0 ? 1u : 0u);
 }
 
 // ------------------------------------------------------- pipelined kernel
 constexpr int RAW_BYTES = 2 * TILE_FLOATS * 4;  // A and B of one problem
-constexpr int OP_BYTES = 4 * TILE_FLOATS * 4;   // A_hi, A_lo, B_hi, B_lo
+constexpr int OP_BYTES = 2 * PAIR_FLOATS * 4;   // stacked A and B of one problem
 constexpr int BAR_OFF = 2 * RAW_BYTES + 2 * OP_BYTES;
-// Two raw stages, two operand stages (1 KB aligned), then the mbarriers, the
-// tensor-memory slot and the failure flag.
-constexpr int SMEM_BYTES = BAR_OFF + 256;
+// The drain warps exchange half sums through two 64 x 65 buffers (pitch 65:
+// conflict-free along rows and columns).
+constexpr int XCH_OFF = BAR_OFF + 256, XCH_FLOATS = 64 * 65;
+// Two raw stages, two operand stages (1 KB aligned), the mbarriers, the
+// tensor-memory slot and the failure flag, the exchange buffers.
+constexpr int SMEM_BYTES = XCH_OFF + 2 * XCH_FLOATS * 4;
 constexpr long long WAIT_CYCLES = 2000000000LL;  // about a second
-
-// Accumulator row held by lane `l` of tensor memory for M = 64 (cta_group::1):
-// rows 16 q .. 16 q + 15 in lanes 32 q .. 32 q + 15 of lane quarter q; -1 for
-// the lanes that hold none.
-__device__ __forceinline__ int acc_row(int lane_quarter, int l) { return l < 16 ? 16 * lane_quarter + l : -1; }
 
 // C[p] = A[p] B[p] for p = blockIdx.x, blockIdx.x + gridDim.x, ... < batch;
 // every operand 64 x 64, contiguous (batch stride 4096 floats), 16-byte
 // aligned.  Warp-specialised: SW split warps (4 or 8), four drain warps
 // (drain warp w reads lane quarter w % 4), one issue warp (bulk copies and
-// MMAs, lane 0); AS accumulator stages (2 or 4) in tensor memory.  The roles
-// meet only on mbarriers (problem i of the CTA; s = i % 2, a = i % AS):
+// MMAs, lane 0); AS accumulators of 128 columns in tensor memory (2 or 4).
+// The roles meet only on mbarriers (problem i of the CTA; s = i % 2,
+// a = i % AS):
 //   raw_full[s]  bulk copy of problem i landed in raw[s]      (tx bytes)
 //   op_full[s]   split of problem i written to op[s]          (SW * 32 arrivals)
 //   mma_done[a]  MMAs of problem i complete: op[s] reusable, accumulator a readable
 //   acc_free[a]  accumulator a drained                        (128 arrivals)
-// each waited on with the parity of its use count (i / 2 or i / AS).  *status
-// gets GLASS_ERR_TIMEOUT if a wait timed out; from then on every wait is skipped and nothing
-// new is issued, so every role still reaches the final barrier.
+// each waited on with the parity of its use count (i / 2 or i / AS), and the
+// drain warps meet on named barrier 1 for the half-sum exchange.  *status
+// gets GLASS_ERR_TIMEOUT if a wait timed out; from then on every wait is
+// skipped and nothing new is issued, so every role still reaches its
+// barriers.
 template <int SW, int AS>
 __global__ void __launch_bounds__(32 * (SW + 5), 1)
     k_gemm_umma64(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C, int batch,
                   unsigned *status) {
     static_assert((SW == 4 || SW == 8) && (AS == 2 || AS == 4), "warp roles, accumulator stages");
-    constexpr int TCOLS = 256;  // AS x 64 columns, a power of two
+    constexpr int TCOLS = AS * 128;  // a power of two
     extern __shared__ __align__(1024) unsigned char smem[];
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     float *raw = reinterpret_cast<float *>(smem);
@@ -327,31 +330,44 @@ __global__ void __launch_bounds__(32 * (SW + 5), 1)
             wait(&raw_full[s], i >> 1);
             if (i >= 2) wait(&mma_done[(i - 2) % AS], (i - 2) / AS);  // problem i - 2 has left op[s]
             const float *r = raw + s * 2 * TILE_FLOATS;
-            float *o = op + s * 4 * TILE_FLOATS;
-            split_a<SW * 32>(r, o, o + TILE_FLOATS, t);
-            split_b<SW * 32>(r + TILE_FLOATS, o + 2 * TILE_FLOATS, o + 3 * TILE_FLOATS, t);
+            float *o = op + s * 2 * PAIR_FLOATS;
+            split_a<SW * 32>(r, o, t);
+            split_b<SW * 32>(r + TILE_FLOATS, o + PAIR_FLOATS, t);
             fence_async_smem();
             mbar_arrive(&op_full[s]);
         }
     } else if (w < SW + 4) {
-        // ---- drain warps: accumulator -> C, 16 rows per warp, 64 B per store
-        const int q = w & 3, row = acc_row(q, lane);
+        // ---- drain warps: lane quarter q holds rows 32 (q % 2) + lane of the
+        // a_hi (q < 2) or a_lo (q >= 2) half; each sums its two column halves,
+        // quarters 2, 3 hand theirs to 0, 1, which store whole 128-byte
+        // column segments of C
+        const int q = w & 3, r = 32 * (q & 1) + lane;
+        float *xch = reinterpret_cast<float *>(smem + XCH_OFF);
         for (int i = 0; i < count; ++i) {
             const int a = i % AS;
             wait(&mma_done[a], i / AS);
             fence_after_sync();
-            const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + 64 * a;
-            float *c = C + prob(i);
+            const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + 128 * a;
+            float hold[64];
 #pragma unroll
             for (int cc = 0; cc < 64; cc += 32) {
-                float v[32];
+                float v[32], v2[32];
                 tmem_ld32(ta + cc, v);
-                if (row >= 0)
+                tmem_ld32(ta + 64 + cc, v2);
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) __stcs(c + (cc + u) * 64 + row, v[u]);
+                for (int u = 0; u < 32; ++u) hold[cc + u] = v[u] + v2[u];
             }
             fence_before_sync();
             mbar_arrive(&acc_free[a]);
+            float *xb = xch + (i & 1) * XCH_FLOATS;
+            if (q >= 2)
+#pragma unroll
+                for (int u = 0; u < 64; ++u) xb[r * 65 + u] = hold[u];
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            float *c = C + prob(i);
+            if (q < 2)
+#pragma unroll
+                for (int u = 0; u < 64; ++u) __stcs(c + u * 64 + r, hold[u] + xb[r * 65 + u]);
         }
     } else if (lane == 0) {
         // ---- issue warp
@@ -372,8 +388,8 @@ __global__ void __launch_bounds__(32 * (SW + 5), 1)
             if (i >= AS) wait(&acc_free[a], i / AS - 1);  // problem i - AS drained from accumulator a
             if (*failed) break;
             fence_after_sync();
-            const float *o = op + s * 4 * TILE_FLOATS;
-            issue_3xtf32(tbase + 64 * a, o, o + TILE_FLOATS, o + 2 * TILE_FLOATS, o + 3 * TILE_FLOATS);
+            const float *o = op + s * 2 * PAIR_FLOATS;
+            issue_split_product(tbase + 128 * a, o, o + PAIR_FLOATS);
             mma_commit(&mma_done[a]);
             issued = i + 1;
         }

@@ -227,9 +227,10 @@ cudaError_t launch_gemm_umma64(const float *A, const float *B, float *C, int bat
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    auto kern = umma::k_gemm_umma64<4, 2>;
+    constexpr int kSplitWarps = 8, kAccumulators = 2;  // measured best of {4, 8} x {2, 4}
+    auto kern = umma::k_gemm_umma64<kSplitWarps, kAccumulators>;
     if ((e = prepare(kern, umma::SMEM_BYTES)) != cudaSuccess) return e;
-    kern<<<batch < sms ? batch : sms, 32 * 9, umma::SMEM_BYTES, st>>>(A, B, C, batch, status);
+    kern<<<batch < sms ? batch : sms, 32 * (kSplitWarps + 5), umma::SMEM_BYTES, st>>>(A, B, C, batch, status);
     return cudaPeekAtLastError();
 }
 
