@@ -92,23 +92,47 @@ __device__ __forceinline__ void apply_point(const Aff &T, float x, float y, floa
     qz = fmaf(T.m[2], x, fmaf(T.m[5], y, fmaf(T.m[8], z, T.m[11])));
 }
 
-// Stream npts points of one problem with `nthr` cooperating threads.
-__device__ __forceinline__ void stream_points(const Aff &T, const float *P, float *Q, int npts, int rank, int nthr) {
-    const bool vec = ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(Q)) & 15) == 0;
-    const int ng = vec ? npts / 4 : 0;
-    for (int g = rank; g < ng; g += nthr) {
-        const float4 *src = reinterpret_cast<const float4 *>(P) + 3 * g;
-        const float4 v0 = __ldcs(src), v1 = __ldcs(src + 1), v2 = __ldcs(src + 2);
-        float4 o0, o1, o2;
-        apply_point(T, v0.x, v0.y, v0.z, o0.x, o0.y, o0.z);
-        apply_point(T, v0.w, v1.x, v1.y, o0.w, o1.x, o1.y);
-        apply_point(T, v1.z, v1.w, v2.x, o1.z, o1.w, o2.x);
-        apply_point(T, v2.y, v2.z, v2.w, o2.y, o2.z, o2.w);
-        float4 *dst = reinterpret_cast<float4 *>(Q) + 3 * g;
-        __stcs(dst, o0);
-        __stcs(dst + 1, o1);
-        __stcs(dst + 2, o2);
+// Four points as 3 float4 (x0 y0 z0 x1 | y1 z1 x2 y2 | z2 x3 y3 z3).
+struct Quad {
+    float4 a, b, c;
+};
+
+__device__ __forceinline__ Quad load_quad(const float *P, int g) {
+    const float4 *src = reinterpret_cast<const float4 *>(P) + 3 * g;
+    return Quad{__ldcs(src), __ldcs(src + 1), __ldcs(src + 2)};
+}
+
+__device__ __forceinline__ void apply_quad(const Aff &T, const Quad &v, float *Q, int g) {
+    float4 o0, o1, o2;
+    apply_point(T, v.a.x, v.a.y, v.a.z, o0.x, o0.y, o0.z);
+    apply_point(T, v.a.w, v.b.x, v.b.y, o0.w, o1.x, o1.y);
+    apply_point(T, v.b.z, v.b.w, v.c.x, o1.z, o1.w, o2.x);
+    apply_point(T, v.c.y, v.c.z, v.c.w, o2.y, o2.z, o2.w);
+    float4 *dst = reinterpret_cast<float4 *>(Q) + 3 * g;
+    __stcs(dst, o0);
+    __stcs(dst + 1, o1);
+    __stcs(dst + 2, o2);
+}
+
+__device__ __forceinline__ bool quads_ok(const float *P, const float *Q) {
+    return ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(Q)) & 15) == 0;
+}
+
+// Stream npts points of one problem with `nthr` cooperating threads, from
+// group g0 (of four points) on: four groups per step, all their loads
+// issued before any is transformed; a ragged tail point by point.
+__device__ __forceinline__ void stream_points(const Aff &T, const float *P, float *Q, int npts, int rank, int nthr,
+                                              int g0 = -1) {
+    const int ng = quads_ok(P, Q) ? npts / 4 : 0;
+    int g = g0 < 0 ? rank : g0;
+    for (; g + 3 * nthr < ng; g += 4 * nthr) {
+        Quad v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = load_quad(P, g + k * nthr);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) apply_quad(T, v[k], Q, g + k * nthr);
     }
+    for (; g < ng; g += nthr) apply_quad(T, load_quad(P, g), Q, g);
     for (int i = 4 * ng + rank; i < npts; i += nthr) {
         float qx, qy, qz;
         apply_point(T, P[3 * i], P[3 * i + 1], P[3 * i + 2], qx, qy, qz);
@@ -148,6 +172,16 @@ __global__ void __launch_bounds__(256) k_geom_warp(int chain, Mat T, int npts, M
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= batch) return;
     constexpr bool ROT = OP == 0;
+    // SE(3): this lane's first two groups of points are already on their way
+    // while the warp composes the chain
+    const float *pb = OP == 1 ? P.p + (long long)b * P.s : nullptr;
+    float *qb = OP == 1 ? Q.p + (long long)b * Q.s : nullptr;
+    const bool pre = OP == 1 && quads_ok(pb, qb) && lane + 32 < npts / 4;
+    Quad first{}, second{};
+    if (pre) {
+        first = load_quad(pb, lane);
+        second = load_quad(pb, lane + 32);
+    }
     Aff acc = warp_compose<ROT>(T.p + (long long)b * T.s, chain);
 #pragma unroll
     for (int u = 0; u < 12; ++u) acc.m[u] = __shfl_sync(GLASS_FULL_MASK, acc.m[u], 0);
@@ -158,7 +192,11 @@ __global__ void __launch_bounds__(256) k_geom_warp(int chain, Mat T, int npts, M
             for (int u = 0; u < 9; ++u) r[u] = acc.m[u];
         }
     } else {
-        stream_points(acc, P.p + (long long)b * P.s, Q.p + (long long)b * Q.s, npts, lane, 32);
+        if (pre) {
+            apply_quad(acc, first, qb, lane);
+            apply_quad(acc, second, qb, lane + 32);
+        }
+        stream_points(acc, pb, qb, npts, lane, 32, pre ? lane + 64 : lane);
     }
 }
 

@@ -293,7 +293,11 @@ def test_rot3_compose_all_placements(chain):
         assert np.abs(np.transpose(Rm, (0, 2, 1)) @ Rm - np.eye(3)).max() < 1e-4
 
 
-@pytest.mark.parametrize("chain,npts", [(1, 1024), (3, 1024), (64, 1024), (2, 7), (5, 1)])
+# npts 200 and 131: 50 and 32 groups of four points, so the warp scope's two
+# prefetched groups per lane exist for some lanes only (or for none) and the
+# four-group streaming steps meet ragged ends
+@pytest.mark.parametrize("chain,npts", [(1, 1024), (3, 1024), (64, 1024), (2, 7), (5, 1), (7, 200), (33, 131),
+                                        (64, 517)])
 def test_se3_apply_all_placements(chain, npts):
     batch = 97
     T = W.se3_transforms(batch * chain, 1300 + chain)
@@ -306,6 +310,25 @@ def test_se3_apply_all_placements(chain, npts):
         sync()
         Q = host(dQ).astype(np.float64)
         assert np.abs(Q - ref).max() <= 1e-5 * max(1, chain / 4) * np.abs(ref).max(), (chain, npts, scope, pack)
+
+
+def test_se3_apply_unaligned_points_take_the_scalar_path():
+    """Point arrays 4 bytes off a 16-byte boundary: no 16-byte streaming, the
+    same result."""
+    import torch
+    chain, npts, batch = 9, 256, 41
+    T = W.se3_transforms(batch * chain, 1320)
+    P = W.gaussian(batch * 3 * npts, 1321)
+    ref = oracle.se3_apply(chain, T.astype(np.float64), npts, P.astype(np.float64), batch)
+    bufP = torch.zeros(batch * 3 * npts + 1, device="cuda")
+    bufP[1:] = torch.from_numpy(P).cuda()
+    for scope, pack in placements(g.GLASS_OP_SE3, 4, chain):
+        bufQ = torch.zeros(batch * 3 * npts + 1, device="cuda")
+        g.check(g.glass_batched_se3_apply(chain, to_dev(T), 16 * chain, npts, bufP[1:], 3 * npts, bufQ[1:], 3 * npts,
+                                          batch, opts_for(scope, pack)))
+        sync()
+        Q = bufQ[1:].cpu().numpy().astype(np.float64)
+        assert np.abs(Q - ref).max() <= 1e-5 * max(1, chain / 4) * np.abs(ref).max(), (scope, pack)
 
 
 # ---------------------------------------------------------------- layouts
