@@ -188,12 +188,13 @@ def time_steps(cells, placements, steps, warmup, barrier=None):
     return total, per
 
 
-def e2e_steps(cells, steps, warmup, nstreams=3):
+def e2e_steps(cells, steps, warmup):
     """End to end through the public API with host buffers: per step, pinned
-    H2D of every cell's inputs, the launches, D2H of every result.  Cells
-    take turns on `nstreams` streams, so one cell's upload, another's kernel
-    and a third's download overlap (the copy engines run both directions at
-    once); a cell's own copy-launch-copy stays ordered on its stream."""
+    H2D of every cell's inputs, the launches, D2H of every result.  Three
+    streams by role -- uploads, launches, downloads -- so the two copy
+    engines and the SMs stay busy at once: a cell's launch waits for its
+    upload, its download for its launch, and its next upload (the buffers
+    are reused in place) for its download."""
     import torch
     pinned_in, pinned_out, outs = [], [], []
     h2d = d2h = 0
@@ -216,30 +217,44 @@ def e2e_steps(cells, steps, warmup, nstreams=3):
         pinned_out.append(po)
         d2h += sum(r.numel() * r.element_size() for r in res)
 
-    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    up, run, down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     main = torch.cuda.current_stream()
+    ev_in = [torch.cuda.Event() for _ in cells]
+    ev_run = [torch.cuda.Event() for _ in cells]
+    ev_out = [None] * len(cells)
 
     def one_step():
-        for i, (c, pin, res, po) in enumerate(zip(cells, pinned_in, outs, pinned_out)):
-            s = streams[i % nstreams]
-            with torch.cuda.stream(s):
+        for i, (c, pin) in enumerate(zip(cells, pinned_in)):
+            with torch.cuda.stream(up):
+                if ev_out[i] is not None:
+                    up.wait_event(ev_out[i])
                 w = c.work[0]
                 for k, t in pin.items():
                     w[k].copy_(t, non_blocking=True)
-                c.launch(0, stream=s)
+                ev_in[i].record(up)
+        for i, c in enumerate(cells):
+            run.wait_event(ev_in[i])
+            c.launch(0, stream=run)
+            ev_run[i].record(run)
+        for i, (res, po) in enumerate(zip(outs, pinned_out)):
+            with torch.cuda.stream(down):
+                down.wait_event(ev_run[i])
                 for r, p in zip(res, po):
                     p.copy_(r, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(down)
+                ev_out[i] = ev
 
     for _ in range(warmup):
         one_step()
     torch.cuda.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(main)
-    for s in streams:
+    for s in (up, run, down):
         s.wait_stream(main)
     for _ in range(steps):
         one_step()
-    for s in streams:
+    for s in (up, run, down):
         main.wait_stream(s)
     t1.record(main)
     torch.cuda.synchronize()
