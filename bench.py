@@ -11,7 +11,9 @@ timed beside it.
 Reported (one JSON line):
   value       batched matrices/s of the tuned step, inputs resident in HBM,
               the K timed steps replayed as one CUDA graph (the library's
-              calls are capture-safe; per-cell times likewise);
+              calls are capture-safe) that forks into --streams streams, the
+              independent cells spread over them; per-cell times from a
+              graph of each cell alone;
   e2e         the same through host buffers (pinned H2D of every input and
               D2H of every result inside the timed region);
   roofline    of the dominant kernel (largest share of the step), from CUDA
@@ -131,14 +133,29 @@ def resolved_placement(cell):
     return pl
 
 
-def time_steps(cells, placements, steps, warmup, barrier=None):
+def stream_assignment(per_ms, nstreams):
+    """Longest-processing-time-first assignment of cells to streams by their
+    measured times: cell index -> stream index."""
+    load = [0.0] * nstreams
+    out = [0] * len(per_ms)
+    for i in sorted(range(len(per_ms)), key=lambda i: -per_ms[i]):
+        j = min(range(nstreams), key=lambda j: load[j])
+        out[i] = j
+        load[j] += per_ms[i]
+    return out
+
+
+def time_steps(cells, placements, steps, warmup, barrier=None, nstreams=1):
     """Warm up with `warmup` eager passes, then time `steps` passes of the
     step captured in one CUDA graph (the library's calls never allocate,
     synchronise or read device memory on the host, so a step records as a
-    graph and replays without host launch gaps).  Every destructive cell
-    reads its own fresh input copy in each pass; the copies are restored,
-    untimed, before the replay.  Per-cell times come the same way from a
-    graph of that cell's `steps` launches.  Returns (total_ms, per-cell ms)."""
+    graph and replays without host launch gaps).  The cells are independent
+    problems: with nstreams > 1 the graph forks into that many streams, each
+    cell's launches on one of them (assigned by measured time), so that
+    latency-bound cells overlap others.  Every destructive cell reads its
+    own fresh input copy in each pass; the copies are restored, untimed,
+    before the replay.  Per-cell times come from a graph of that cell's
+    `steps` launches alone.  Returns (total_ms, per-cell ms)."""
     import torch
     import paper_2609_28179_gb300 as g
     for w in range(warmup):
@@ -171,10 +188,22 @@ def time_steps(cells, placements, steps, warmup, barrier=None):
         per.append(replay_ms(gr) / steps)
         del gr
     step = torch.cuda.CUDAGraph()
+    branches = [torch.cuda.Stream() for _ in range(nstreams)] if nstreams > 1 else [cap]
+    owner = stream_assignment(per, nstreams) if nstreams > 1 else [0] * len(cells)
     with torch.cuda.graph(step, stream=cap):
+        if nstreams > 1:
+            fork = torch.cuda.Event()
+            fork.record(cap)
+            for b in branches:
+                b.wait_event(fork)
         for st in range(steps):
-            for c, (s, p) in zip(cells, placements):
-                c.launch(warmup + st, s, p)
+            for i, (c, (s, p)) in enumerate(zip(cells, placements)):
+                c.launch(warmup + st, s, p, stream=branches[owner[i]])
+        if nstreams > 1:
+            for b in branches:
+                join = torch.cuda.Event()
+                join.record(b)
+                cap.wait_event(join)
     restore_all()
     replay_ms(step)          # first replay uploads the graph; not timed
     restore_all()
@@ -357,7 +386,8 @@ def config_of(args, sample_note=None):
                      f"1024 points for se3), batch {args.batch} per cell, tuned placements",
          "ops": args.ops, "sizes": args.sizes, "batch": args.batch,
          "rhs": "posv/getrs 1, trsm n, gemm square n x n x n",
-         "l2": "step working set > 1 GB >> 129 MB L2; destructive cells read a fresh input copy every step"}
+         "l2": "step working set > 1 GB >> 129 MB L2; destructive cells read a fresh input copy every step",
+         "streams": getattr(args, "streams", 1)}
     if sample_note:
         c["sample"] = sample_note
     return c
@@ -868,6 +898,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sample-div", type=int, default=64)
     ap.add_argument("--extras", default="all", help="comma list of extra configs, 'all' or 'none'")
+    ap.add_argument("--streams", type=int, default=3,
+                    help="streams the step graph forks into (the cells are independent; 3 measured best of 1-8)")
     args = ap.parse_args()
     from paper_2609_28179_gb300.cells import OPS, SWEEP_N
     args.ops = args.ops or OPS
@@ -907,13 +939,13 @@ def main():
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as cs:
-        t_tuned, per_tuned = time_steps(cells, tuned, args.steps, args.warmup, barrier)
+        t_tuned, per_tuned = time_steps(cells, tuned, args.steps, args.warmup, barrier, args.streams)
     clocks = cs.summary()
     barrier()
     for c in cells:
         c.restore()
     torch.cuda.synchronize()
-    t_plain, per_plain = time_steps(cells, plain, args.steps, args.warmup, barrier)
+    t_plain, per_plain = time_steps(cells, plain, args.steps, args.warmup, barrier, args.streams)
     t_e2e = h2d = d2h = None
     if not args.no_e2e:
         t_e2e, h2d, d2h = e2e_steps(cells, args.steps, args.warmup)
