@@ -53,6 +53,18 @@ __device__ __forceinline__ float chain_elem(const float *p, int c, int u) {
 
 template <bool ROT>
 __device__ __forceinline__ void load_aff(Aff &a, const float *p, int c) {
+    if (!ROT && (reinterpret_cast<uintptr_t>(p + c * 16) & 15) == 0) {
+        // a 4 x 4 transform is four 16-byte columns; the bottom row is not used
+        const float4 *q = reinterpret_cast<const float4 *>(p + c * 16);
+#pragma unroll
+        for (int col = 0; col < 4; ++col) {
+            const float4 v = __ldg(q + col);
+            a.m[3 * col] = v.x;
+            a.m[3 * col + 1] = v.y;
+            a.m[3 * col + 2] = v.z;
+        }
+        return;
+    }
 #pragma unroll
     for (int u = 0; u < 12; ++u) a.m[u] = chain_elem<ROT>(p, c, u);
 }
