@@ -48,3 +48,4 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.replica_value(10, 1, 2, 1.0) == pytest.approx(20000.0)
+
