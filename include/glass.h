@@ -125,7 +125,7 @@ typedef struct {
  * tensor cores: GLASS_MATH_BF16_TC requires opts->dtype == GLASS_BF16 (A and
  * B stored as bfloat16, C as FP32); the TF32 modes read FP32 A and B.
  * Tensor-core modes require m = n = k in {16, 32, 64}, packed colmajor.
- * Order 64 in 3xTF32 mode, and the FP32 block-scope placement (pack 1) of
+ * Order 64 in BF16 and 3xTF32 modes, and the FP32 block-scope placement (pack 1) of
  * order 64 with packed, 16-byte aligned operands, run on the fifth-
  * generation tensor cores (tcgen05, operands in shared memory, accumulator
  * in tensor memory; that kernel also adds the lo*lo product; each error

@@ -411,5 +411,192 @@ __global__ void __launch_bounds__(32 * (SW + 5), 1)
     }
 }
 
+// ------------------------------------------------------------- BF16 mode
+// C = A B with BF16 operands (stored as bf16, column-major 64 x 64) and FP32
+// accumulation: no split; one K-major 128-byte-swizzled 64-row tile per
+// operand (a row is one 128-byte swizzle atom: element (r, k) at byte
+// 128 r + 16 ((k / 8) ^ (r % 8)) + 2 (k % 8)) and four tcgen05.mma of
+// kind::f16 (M = N = 64, K = 16) per product.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+constexpr int BF_TILE_BYTES = 64 * 128;  // one 64 x 64 bf16 operand
+
+__device__ __forceinline__ int bf_off(int r, int c) {  // bytes; c = k / 8, the 16-byte chunk
+    return r * 128 + ((c ^ (r & 7)) << 4);
+}
+
+// A (column-major bf16, pitch 64): thread t builds row m = t % 64, chunks
+// c = t / 64 + (T / 64) it from eight 2-byte loads (consecutive m across a
+// warp); a quarter-warp's eight rows store to eight distinct chunk positions.
+template <int T>
+__device__ __forceinline__ void bf16_tile_a(const unsigned short *raw, unsigned char *tile, int t) {
+    const int m = t & 63;
+#pragma unroll
+    for (int it = 0; it < 512 / T; ++it) {
+        const int c = (t >> 6) + (T / 64) * it;
+        unsigned short h[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) h[u] = raw[(8 * c + u) * 64 + m];
+        uint4 v;
+        v.x = h[0] | ((unsigned)h[1] << 16);
+        v.y = h[2] | ((unsigned)h[3] << 16);
+        v.z = h[4] | ((unsigned)h[5] << 16);
+        v.w = h[6] | ((unsigned)h[7] << 16);
+        *reinterpret_cast<uint4 *>(tile + bf_off(m, c)) = v;
+    }
+}
+
+// B (column-major K x N bf16: a column is one 128-byte row of the K-major
+// tile): each 16-byte chunk moves to its swizzled position; chunk choice
+// alpha(q) ^ j as in split_b keeps loads and stores conflict free.
+template <int T>
+__device__ __forceinline__ void bf16_tile_b(const unsigned char *raw, unsigned char *tile, int t) {
+    const int q = t & 7, grp = t >> 3;
+#pragma unroll
+    for (int it = 0; it < 512 / T; ++it) {
+        const int lin = grp + (T / 8) * it, rg = lin & 7, j = lin >> 3;  // j < 8
+        const int c = gf8_alpha(q) ^ j, n = 8 * rg + q;
+        *reinterpret_cast<uint4 *>(tile + bf_off(n, c)) = *reinterpret_cast<const uint4 *>(raw + n * 128 + c * 16);
+    }
+}
+
+constexpr int BF_RAW_BYTES = 2 * BF_TILE_BYTES;  // A and B of one problem, as stored
+constexpr int BF_OP_BYTES = 2 * BF_TILE_BYTES;   // the two swizzled tiles
+constexpr int BF_BAR_OFF = 2 * BF_RAW_BYTES + 2 * BF_OP_BYTES;
+constexpr int BF_SMEM_BYTES = BF_BAR_OFF + 256;
+
+// Same pipeline and failure handling as k_gemm_umma64 (two raw and two tile
+// stages, AS = 2 accumulators of 64 columns; four tile warps, four drain
+// warps -- lanes 0-15 of each lane quarter hold rows 16 q .. 16 q + 15 of an
+// M = 64 accumulator -- and one issue warp); small enough for two CTAs per
+// SM.
+__global__ void __launch_bounds__(288, 2)
+    k_gemm_umma64_bf16(const unsigned short *__restrict__ A, const unsigned short *__restrict__ B,
+                       float *__restrict__ C, int batch, unsigned *status) {
+    constexpr int SW = 4, AS = 2, TCOLS = 128;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    unsigned char *raw = smem;
+    unsigned char *op = smem + 2 * BF_RAW_BYTES;
+    uint64_t *raw_full = reinterpret_cast<uint64_t *>(smem + BF_BAR_OFF);
+    uint64_t *op_full = raw_full + 2, *mma_done = op_full + 2, *acc_free = mma_done + AS;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(acc_free + AS);
+    volatile int *failed = reinterpret_cast<volatile int *>(slot + 1);
+
+    const int G = gridDim.x, first = blockIdx.x;
+    const int count = first < batch ? (batch - first + G - 1) / G : 0;
+    if (t == 0) {
+        *failed = (smem_u32(op) & 1023u) != 0;
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&raw_full[k], 1);
+            mbar_init(&op_full[k], SW * 32);
+        }
+        for (int k = 0; k < AS; ++k) {
+            mbar_init(&mma_done[k], 1);
+            mbar_init(&acc_free[k], 128);
+        }
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (w == 0) {
+        tmem_alloc<TCOLS>(slot);
+        tmem_relinquish();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = *slot;
+
+    auto wait = [&](uint64_t *bar, int use) {
+        if (*failed) return;
+        if (!mbar_wait(bar, use & 1, WAIT_CYCLES)) *failed = 1;
+    };
+    auto prob = [&](int i) { return (first + (long long)i * G) * TILE_FLOATS; };  // elements
+
+    if (w < SW) {
+        for (int i = 0; i < count; ++i) {
+            const int s = i & 1;
+            wait(&raw_full[s], i >> 1);
+            if (i >= 2) wait(&mma_done[(i - 2) % AS], (i - 2) / AS);
+            const unsigned char *r = raw + s * BF_RAW_BYTES;
+            unsigned char *o = op + s * BF_OP_BYTES;
+            bf16_tile_a<SW * 32>(reinterpret_cast<const unsigned short *>(r), o, t);
+            bf16_tile_b<SW * 32>(r + BF_TILE_BYTES, o + BF_TILE_BYTES, t);
+            fence_async_smem();
+            mbar_arrive(&op_full[s]);
+        }
+    } else if (w < SW + 4) {
+        const int q = w & 3, row = lane < 16 ? 16 * q + lane : -1;
+        for (int i = 0; i < count; ++i) {
+            const int a = i % AS;
+            wait(&mma_done[a], i / AS);
+            fence_after_sync();
+            const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + 64 * a;
+            float *c = C + prob(i);
+#pragma unroll
+            for (int cc = 0; cc < 64; cc += 32) {
+                float v[32];
+                tmem_ld32(ta + cc, v);
+                if (row >= 0)
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) __stcs(c + (cc + u) * 64 + row, v[u]);
+            }
+            fence_before_sync();
+            mbar_arrive(&acc_free[a]);
+        }
+    } else if (lane == 0) {
+        int issued = 0, loaded = 0;
+        auto load = [&](int i) {
+            unsigned char *dst = raw + (i & 1) * BF_RAW_BYTES;
+            mbar_expect_tx(&raw_full[i & 1], BF_RAW_BYTES);
+            bulk_g2s(dst, A + prob(i), BF_TILE_BYTES, &raw_full[i & 1]);
+            bulk_g2s(dst + BF_TILE_BYTES, B + prob(i), BF_TILE_BYTES, &raw_full[i & 1]);
+            loaded = i + 1;
+        };
+        for (int i = 0; i < 2 && i < count && !*failed; ++i) load(i);
+        for (int i = 0; i < count; ++i) {
+            const int s = i & 1, a = i % AS;
+            wait(&op_full[s], i >> 1);
+            if (*failed) break;
+            if (i + 2 < count) load(i + 2);
+            if (i >= AS) wait(&acc_free[a], i / AS - 1);
+            if (*failed) break;
+            fence_after_sync();
+            const uint32_t ta = smem_u32(op + s * BF_OP_BYTES), tb = ta + BF_TILE_BYTES;
+            constexpr uint32_t ID = idesc_bf16(64, 64);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                mma_f16(tbase + 64 * a, desc_kmajor(ta + 32 * k, 16, 1024) | (2ull << 61),
+                        desc_kmajor(tb + 32 * k, 16, 1024) | (2ull << 61), ID, k > 0 ? 1u : 0u);
+            mma_commit(&mma_done[a]);
+            issued = i + 1;
+        }
+        if (*failed) {
+            for (int k = issued - 1; k >= 0 && k >= issued - 2; --k)
+                mbar_wait(&mma_done[k % AS], (k / AS) & 1, WAIT_CYCLES);
+            for (int k = loaded - 1; k >= 0 && k >= loaded - 2; --k)
+                mbar_wait(&raw_full[k & 1], (k >> 1) & 1, WAIT_CYCLES);
+            atomicExch(status, (unsigned)GLASS_ERR_TIMEOUT);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (w == 0) {
+        fence_after_sync();
+        tmem_dealloc<TCOLS>(tbase);
+    }
+}
+
 }  // namespace umma
 }  // namespace glass

@@ -2,9 +2,9 @@
 // with FP32 accumulation: BF16 operands, TF32 operands, or 3xTF32 split
 // products (a = a_hi + a_lo with a_hi = tf32(a), a_lo = tf32(a - a_hi);
 // C += a_lo b_hi + a_hi b_lo + a_hi b_hi), the precision path the paper
-// lists as future work (Sec. V).  The 3xTF32 product of order 64 runs on the
-// fifth-generation tensor cores (dev_umma.cuh), which also serve the FP32
-// block-scope GEMM of order 64; the others use warp-level mma.sync.
+// lists as future work (Sec. V).  The BF16 and 3xTF32 products of order 64
+// run on the fifth-generation tensor cores (dev_umma.cuh), which also serve
+// the FP32 block-scope GEMM of order 64; the others use warp-level mma.sync.
 //
 // Work split: n/16 warps per product, warp w owns rows 16w .. 16w+15 of C
 // and every 8-column block, so one A fragment serves n/8 MMAs.  A CTA holds
@@ -234,6 +234,23 @@ cudaError_t launch_gemm_umma64(const float *A, const float *B, float *C, int bat
     return cudaPeekAtLastError();
 }
 
+// BF16 products of order 64 on the fifth-generation tensor cores (kind::f16).
+cudaError_t launch_gemm_umma64_bf16(const void *A, const void *B, float *C, int batch, cudaStream_t st) {
+    if (batch <= 0) return cudaSuccess;
+    unsigned *status = device_status_word();
+    if (status == nullptr) return cudaErrorInvalidDeviceFunction;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if ((e = prepare(umma::k_gemm_umma64_bf16, umma::BF_SMEM_BYTES)) != cudaSuccess) return e;
+    const int grid = batch < 2 * sms ? batch : 2 * sms;  // two CTAs per SM
+    umma::k_gemm_umma64_bf16<<<grid, 288, umma::BF_SMEM_BYTES, st>>>(static_cast<const unsigned short *>(A),
+                                                                     static_cast<const unsigned short *>(B), C,
+                                                                     batch, status);
+    return cudaPeekAtLastError();
+}
+
 cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float *C, int batch, cudaStream_t st) {
     // 16-byte staging needs 16-byte aligned operands
     if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) != 0)
@@ -248,8 +265,8 @@ cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float 
         k_gemm_bf16<NN><<<grid, 128, smem, st>>>(a, b, C, batch); return cudaPeekAtLastError(); } while (0)
         if (n == 16) BF(16);
         if (n == 32) BF(32);
-        BF(64);
 #undef BF
+        return launch_gemm_umma64_bf16(A, B, C, batch, st);
     }
     const size_t smem = (size_t)ppc * (n * (n + 8) + n * (n + 4)) * 4;
     const float *a = static_cast<const float *>(A), *b = static_cast<const float *>(B);
