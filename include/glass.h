@@ -125,13 +125,13 @@ typedef struct {
  * tensor cores: GLASS_MATH_BF16_TC requires opts->dtype == GLASS_BF16 (A and
  * B stored as bfloat16, C as FP32); the TF32 modes read FP32 A and B.
  * Tensor-core modes require m = n = k in {16, 32, 64}, packed colmajor.
- * Order 64 in BF16 and 3xTF32 modes, and the FP32 block-scope placement (pack 1) of
- * order 64 with packed, 16-byte aligned operands, run on the fifth-
- * generation tensor cores (tcgen05, operands in shared memory, accumulator
- * in tensor memory; that kernel also adds the lo*lo product; each error
- * within the FP32 bound 2 k u |A||B|).  That
- * kernel's waits are bounded: one that gives up records GLASS_ERR_TIMEOUT
- * for glass_last_device_status. */
+ * Order 64 runs on the fifth-generation tensor cores (tcgen05, operands in
+ * shared memory, accumulator in tensor memory) in the BF16 and 3xTF32 modes
+ * and for the FP32 block-scope placement (pack 1) with packed, 16-byte
+ * aligned operands; the split-TF32 kernel also adds the lo*lo product, and
+ * its error stays within the FP32 bound 2 k u |A||B|.  Those kernels' waits
+ * are bounded: one that gives up records GLASS_ERR_TIMEOUT for
+ * glass_last_device_status. */
 glass_status glass_batched_gemm(int m, int n, int k,
                                 const void *A, int lda, long long sA,
                                 const void *B, int ldb, long long sB,
