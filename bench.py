@@ -8,7 +8,9 @@ library's measured table selects ("tuned").  The same step with one fixed
 placement (one thread per problem where feasible, else one warp: "plain") is
 timed beside it.
 
-Reported (one JSON line):
+Reported (one compact JSON line on stdout; the per-cell rows and the full
+records of the other configurations go to a detail file, a per-cell table
+to stderr):
   value       batched matrices/s of the tuned step, inputs resident in HBM,
               the K timed steps replayed as one CUDA graph (the library's
               calls are capture-safe) that forks into --streams streams, the
@@ -20,8 +22,12 @@ Reported (one JSON line):
               events around its launches;
   cpu_baseline  the FP64 C oracle on a bounded sample, all host cores (and
               the same sample on one core);
-  peaks       measured FP32/FP64/tensor pipe peaks (glass_peak_probe);
-  plain       the plain step and the tuned/plain speedup.
+  accuracy    the worst per-problem relative error of the tuned and the
+              plain results of every cell against the oracle's results on
+              the same problems (the oracle's sample of the CPU baseline);
+  plain       the plain step and the tuned/plain speedup;
+  extras      headline numbers of the other configurations (mixed sizes,
+              tensor-core GEMM, refinement, learned placement).
 `--impl reference` times the oracle (the reference arm of this task) on the
 same workload, one bounded sample per step.
 """
@@ -291,8 +297,9 @@ def e2e_steps(cells, steps, warmup):
 
 
 # ------------------------------------------------------------ cpu oracle
-def oracle_cell_time(op, n, host, batch, sample):
-    """Seconds the FP64 oracle takes for `sample` problems of a cell."""
+def oracle_cell(op, n, host, batch, sample):
+    """The FP64 oracle on the first `sample` problems of a cell: (seconds,
+    problems, outputs) -- the outputs keyed like gpu_outputs'."""
     import numpy as np
     import oracle
     from paper_2609_28179_gb300.cells import NPTS, rhs_of
@@ -301,36 +308,106 @@ def oracle_cell_time(op, n, host, batch, sample):
     f64 = lambda key, per: host[key][: s * per].astype(np.float64)
     t = time.perf_counter()
     if op == "gemm":
-        oracle.gemm(n, n, n, f64("A", n * n), f64("B", n * n), s)
+        out = {"X": oracle.gemm(n, n, n, f64("A", n * n), f64("B", n * n), s)}
     elif op == "posv":
-        oracle.posv(n, 1, f64("A", n * n), f64("B", n), s)
+        L, X, _ = oracle.posv(n, 1, f64("A", n * n), f64("B", n), s)
+        out = {"X": X, "L": L}
     elif op == "trsm":
-        oracle.trsm(n, k, f64("A", n * n), f64("B", n * k), s)
+        out = {"X": oracle.trsm(n, k, f64("A", n * n), f64("B", n * k), s)}
     elif op == "getrf_getrs":
-        oracle.getrf_getrs(n, 1, f64("A", n * n), f64("B", n), s)
+        LU, piv, X, _ = oracle.getrf_getrs(n, 1, f64("A", n * n), f64("B", n), s)
+        out = {"X": X, "LU": LU, "ipiv": piv}
     elif op == "rot3":
-        oracle.rot3_compose(k, f64("A", 9 * k), s)
-    elif op == "se3":
-        oracle.se3_apply(k, f64("A", 16 * k), NPTS, f64("B", 3 * NPTS), s)
-    return time.perf_counter() - t, s
+        out = {"X": oracle.rot3_compose(k, f64("A", 9 * k), s)}
+    else:
+        out = {"X": oracle.se3_apply(k, f64("A", 16 * k), NPTS, f64("B", 3 * NPTS), s)}
+    return time.perf_counter() - t, s, out
 
 
-def cpu_baseline(hosts, ops_sizes, batch, budget_s=12.0):
+def oracle_cell_time(op, n, host, batch, sample):
+    """Seconds the FP64 oracle takes for `sample` problems of a cell."""
+    dt, s, _ = oracle_cell(op, n, host, batch, sample)
+    return dt, s
+
+
+def gpu_outputs(cell, placement, count):
+    """Outputs of one eager launch of `cell` at `placement` on its pristine
+    input (work set 0, restored first), first `count` problems, as float64
+    host arrays keyed X (solution / product / composed result), L (posv
+    factor, lower triangle), LU and ipiv (getrf)."""
+    import numpy as np
+    import torch
+    import paper_2609_28179_gb300 as g
+    scope, pack = placement
+    cell.restore()
+    g.check(cell.launch(0, scope, pack), f"check {cell.op} n={cell.n}")
+    torch.cuda.synchronize()
+    n, k = cell.n, cell.k
+    s = min(count, cell.batch)
+    w = cell.work[0]
+    h = lambda t, per: t[: s * per].double().cpu().numpy()
+    out = {"count": s}
+    if cell.op == "gemm":
+        out["X"] = h(cell.out, n * n)
+    elif cell.op == "posv":
+        out.update(X=h(w["B"], n), L=h(w["A"], n * n))
+    elif cell.op == "trsm":
+        out["X"] = h(w["B"], n * k)
+    elif cell.op == "getrf_getrs":
+        out.update(X=h(w["B"], n), LU=h(w["A"], n * n), ipiv=cell.ipiv[: s * n].cpu().numpy())
+    elif cell.op == "rot3":
+        out["X"] = h(cell.out, 9)
+    else:
+        from paper_2609_28179_gb300.cells import NPTS
+        out["X"] = h(cell.out, 3 * NPTS)
+    return out
+
+
+def cell_errors(op, n, gpu, ref, s):
+    """Largest per-problem relative error max|y - y*| / max|y*| over the first
+    s problems, over every floating output (posv: only L's lower triangle is
+    defined), and the number of pivot indices that differ from the oracle's."""
+    import numpy as np
+    err = 0.0
+    for key in ("X", "L", "LU"):
+        if key not in gpu or key not in ref:
+            continue
+        per = ref[key].size // s
+        yy = gpu[key].reshape(-1)[: s * per].reshape(s, per)
+        rr = ref[key].reshape(-1)[: s * per].reshape(s, per)
+        if key == "L":
+            lower = np.tril(np.ones((n, n), dtype=bool)).T.reshape(-1)  # column-major lower triangle
+            yy, rr = yy[:, lower], rr[:, lower]
+        num = np.abs(yy - rr).max(1)
+        den = np.maximum(np.abs(rr).max(1), 1e-300)
+        err = max(err, float((num / den).max()))
+    piv = 0
+    if "ipiv" in gpu and "ipiv" in ref:
+        m = s * n
+        piv = int((gpu["ipiv"][:m] != ref["ipiv"][:m]).sum())
+    return err, piv
+
+
+def cpu_baseline(hosts, ops_sizes, batch, budget_s=12.0, gpu=None):
     """Oracle matrices/s over the step's cells, each on an adaptively sized
-    sample (scaled to the full batch)."""
+    sample (scaled to the full batch).  When `gpu` maps a label ("tuned",
+    "plain") to the GPU outputs of each cell's first problems, the oracle's
+    results on the same problems also give each cell's error (the second
+    value: label -> [(rel_err, pivot mismatches, problems compared)])."""
     import oracle
     oracle.build()
     per_cell = budget_s / max(1, len(ops_sizes))
-    full_time, samples = 0.0, []
+    full_time, samples, refs = 0.0, [], []
     for (op, n), host in zip(ops_sizes, hosts):
         sample = 16
         while True:
-            dt, s = oracle_cell_time(op, n, host, batch, sample)
+            dt, s, out = oracle_cell(op, n, host, batch, sample)
             if dt >= per_cell * 0.5 or s >= batch:
                 break
             sample = min(batch, sample * max(2, int(per_cell * 0.6 / max(dt, 1e-4))))
         full_time += dt / s * batch
         samples.append(f"{op}{n}:{s}")
+        refs.append((s, out))
     value = len(ops_sizes) * batch / full_time
     cores = oracle.max_threads()
     # the same samples on one core
@@ -343,10 +420,17 @@ def cpu_baseline(hosts, ops_sizes, batch, budget_s=12.0):
             one_time += dt / s * batch
     finally:
         oracle.set_threads(cores)
+    errs = {}
+    for label, outs in (gpu or {}).items():
+        errs[label] = []
+        for (op, n), (s, ref), got in zip(ops_sizes, refs, outs):
+            cnt = min(s, got["count"])
+            e, piv = cell_errors(op, n, got, ref, cnt)
+            errs[label].append((e, piv, cnt))
     return {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
             "value_1core": len(ops_sizes) * batch / one_time,
             "sample": f"per cell an adaptive prefix of the {batch} problems ({', '.join(samples)}), "
-                      f"scaled to the full batch; value_1core: the same samples on one core"}
+                      f"scaled to the full batch; value_1core: the same samples on one core"}, errs
 
 
 # ------------------------------------------------------------- reference
@@ -410,26 +494,44 @@ def replica_value(problems_per_rank: int, world: int, steps: int, ms_max: float)
     return problems_per_rank * world * steps / (ms_max / 1e3)
 
 
-def kernel_hash():
+# Source files each operation's kernels are built from: a committed DRAM
+# traffic figure stays valid while these files are unchanged.
+KERNEL_SOURCES = {
+    "gemm": ["common.cuh", "k_gemm.cu", "k_gemm_tc.cu", "dev_umma.cuh"],
+    "posv": ["common.cuh", "k_chol_impl.cuh", "k_chol_posv.cu", "dev_chol.cuh", "dev_chol_tc.cuh",
+             "dev_rows.cuh", "dev_trsm_tc.cuh"],
+    "trsm": ["common.cuh", "k_chol_impl.cuh", "k_chol_trsm.cu", "dev_chol.cuh", "dev_chol_tc.cuh",
+             "dev_rows.cuh", "dev_trsm_tc.cuh"],
+    "getrf_getrs": ["common.cuh", "k_lu.cu", "dev_lu.cuh", "dev_lu_tc.cuh", "dev_chol_tc.cuh", "dev_rows.cuh"],
+    "rot3": ["common.cuh", "k_geom.cu"],
+    "se3": ["common.cuh", "k_geom.cu"],
+}
+
+
+def sources_hash(op):
+    """Hash of the kernel sources of one operation (KERNEL_SOURCES)."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2609_28179_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(KERNEL_SOURCES[op]):
         with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:12]
 
 
 def traffic_for(kernel_key):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, or
-    None when the kernels changed since it was captured."""
+    """DRAM bytes per launch of a cell's kernel from the committed ncu
+    summary (profiles/ncu_traffic.json), or None when that operation's kernel
+    sources changed since the capture."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_hash") != kernel_hash():
+    e = d.get("cells", {}).get(kernel_key)
+    if not isinstance(e, dict) or e.get("sources_hash") != sources_hash(kernel_key.split(":")[0]):
         return None
-    return d.get("cells", {}).get(kernel_key)
+    return e.get("bytes")
 
 
 # ------------------------------------------------------------ other configs
@@ -898,6 +1000,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-sample-div", type=int, default=64)
     ap.add_argument("--extras", default="all", help="comma list of extra configs, 'all' or 'none'")
+    ap.add_argument("--detail", default=None, help="file for the per-cell rows and the extra configs' records")
     ap.add_argument("--streams", type=int, default=3,
                     help="streams the step graph forks into (the cells are independent; 3 measured best of 1-8)")
     args = ap.parse_args()
@@ -985,6 +1088,8 @@ def main():
     key = f"{dc.op}:{dc.n}:{dr['placement']}"
     roof["kernel"] = key
     roof["traffic"] = traffic_for(key)
+    roof["algorithmic_bytes"] = dc.bytes
+    roof["us_per_launch"] = round(per_tuned[dom] * 1e3, 2)
     roof["step_share"] = per_tuned[dom] / sum(per_tuned)
     line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -993,23 +1098,103 @@ def main():
             "clocks": clocks,
             "plain": {"value": problems * args.steps / (t_plain / 1e3), "ms_per_step": t_plain / args.steps,
                       "speedup_tuned_over_plain": t_plain / t_tuned},
-            "hbm_weighted_frac": sum(r["frac"] * r["us"] for r in rows) / sum(r["us"] for r in rows),
-            "peaks": {"hbm_gbs": peaks["hbm_gbs"], "hbm_src": peaks["src"], **pipes,
-                      "fp32_nominal_tflops": fp32_peak_tflops(sms, peaks["sm_max_mhz"])}}
+            "hbm_weighted_frac": sum(r["frac"] * r["us"] for r in rows) / sum(r["us"] for r in rows)}
     if t_e2e is not None:
         line["e2e"] = {"value": problems * args.steps / (t_e2e / 1e3), "unit": "matrices/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                        "ms_per_step": t_e2e / args.steps}
+    detail = {"cells": rows, "peaks": {"hbm_gbs": peaks["hbm_gbs"], "hbm_src": peaks["src"], **pipes,
+                                       "fp32_nominal_tflops": fp32_peak_tflops(sms, peaks["sm_max_mhz"])}}
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline([c.host for c in cells], [(c.op, c.n) for c in cells], args.batch)
+        outs = {lab: [gpu_outputs(c, pl, CHECK_PROBLEMS) for c, pl in zip(cells, pls)]
+                for lab, pls in (("tuned", tuned), ("plain", plain))}
+        cb, errs = cpu_baseline([c.host for c in cells], [(c.op, c.n) for c in cells], args.batch, gpu=outs)
+        line["cpu_baseline"] = cb
+        for lab, es in errs.items():
+            for r, (e, piv, cnt) in zip(rows, es):
+                r[f"err_{lab}"] = e
+                r[f"ipiv_mismatch_{lab}"] = piv
+                r["err_problems"] = cnt
+        line["accuracy"] = accuracy_summary(rows)
     if rank == 0 and args.extras != "none":
-        line["extras"] = run_extras(peaks, args.extras)
-    line["cells"] = rows
+        detail["extras"] = run_extras(peaks, args.extras)
+        line["extras"] = summarize_extras(detail["extras"])
     if rank == 0:
+        line["top_cells"] = [f"{r['op']}:{r['n']} {r['placement']} {r['us']}us frac {r['frac']:.2f}"
+                             for r in sorted(rows, key=lambda r: -r["us"])[:6]]
+        path = write_detail(args, detail)
+        line["detail_file"] = path
+        for r in sorted(rows, key=lambda r: -r["us"]):
+            print(f"  {r['op']:>12} n={r['n']:<3} {r['placement']:>7} {r['us']:9.2f} us  {r['gbs']:7.0f} GB/s  "
+                  f"frac {r['frac']:.3f}  plain {r['plain_us']:9.2f} us  err {r.get('err_tuned', float('nan')):.1e}",
+                  file=sys.stderr)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+CHECK_PROBLEMS = 256   # problems per cell compared with the oracle (a prefix of the batch)
+ERR_BAR = 1e-4
+
+
+def accuracy_summary(rows):
+    """Worst per-problem relative error of the tuned and plain results over
+    every cell, against the FP64 oracle on the same inputs."""
+    out = {"bar": ERR_BAR, "cells": len(rows),
+           "sample": f"first min({CHECK_PROBLEMS}, oracle sample) problems of every cell, every output"}
+    for lab in ("tuned", "plain"):
+        es = [(r.get(f"err_{lab}"), r) for r in rows if r.get(f"err_{lab}") is not None]
+        if not es:
+            continue
+        worst = max(es, key=lambda x: x[0])
+        out[f"{lab}_max_rel_err"] = worst[0]
+        out[f"{lab}_worst_cell"] = f"{worst[1]['op']}:{worst[1]['n']}"
+        out[f"{lab}_cells_within_bar"] = sum(1 for e, _ in es if e <= ERR_BAR)
+        out[f"{lab}_ipiv_mismatches"] = sum(r.get(f"ipiv_mismatch_{lab}", 0) for _, r in es)
+    return out
+
+
+def summarize_extras(ex):
+    """A few headline numbers of the other configurations for the result
+    line (the full records go to the detail file)."""
+    out = {}
+
+    def pick(name, fn):
+        try:
+            v = fn(ex[name])
+            if v is not None:
+                out[name] = v
+        except Exception as e:  # report, do not hide
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:200]}
+    pick("plain_posv_n6", lambda d: {"us": round(d["us"], 2), "matrices_per_s": d["matrices_per_s"]})
+    pick("mixed_size", lambda d: {k: d["best"][k] for k in ("schedule", "us", "matrices_per_s", "frac_hbm")})
+    pick("tensor_core_gemm", lambda d: {k: {"us": round(v["us"], 1), "frac_hbm": round(v["frac_hbm"], 3)}
+                                        for k, v in d.items() if k.endswith("n64")})
+    pick("refined_posv", lambda d: {
+        **{f"n{n}_refined_over_plain": d[f"time_n{n}_refine1"]["us"] / d[f"time_n{n}_refine0"]["us"]
+           for n in (32, 64)},
+        **{k: {"x0_bwd": v["x0"]["bwd_err_max"], "x1_bwd": v["x1"]["bwd_err_max"],
+               "x1_failed": v["x1"]["failed"]} for k, v in d.items() if k.startswith("n64_kappa")}})
+    pick("learned_placement", lambda d: {k: {"median_regret": round(d[k]["median"], 4), "p90_regret": round(d[k]["p90"], 4)}
+                                         for k in ("learned", "nearest_grid_table", "fixed_placement")})
+    return out
+
+
+def write_detail(args, detail):
+    """Per-cell rows and the full records of the other configurations go to
+    a JSON file (--detail, default gpurun_out/bench_detail.json under the
+    repository if that folder exists, else the system's temporary folder)."""
+    path = args.detail
+    if not path:
+        d = os.path.join(ROOT, "gpurun_out")
+        path = os.path.join(d if os.path.isdir(d) else tempfile.gettempdir(), "bench_detail.json")
+    try:
+        with open(path, "w") as f:
+            json.dump(detail, f)
+        return path
+    except OSError as e:
+        return f"unwritten: {e}"
 
 
 if __name__ == "__main__":

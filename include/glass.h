@@ -246,9 +246,11 @@ glass_status glass_posv_varsize(int batch, const int *n_dev, const long long *of
  * (about 260 KB, held by every GPU that loads the library until exit).
  * The paper has no counterpart of this entry point.  Arguments are those of
  * glass_posv_varsize without ws / ws_bytes; batch > 65536 returns
- * GLASS_ERR_UNSUPPORTED and launches nothing; nothing is allocated.  The
- * first call on a device looks up the array's device address, so make it
- * before any stream capture.  Every call on a device shares the array: calls
+ * GLASS_ERR_UNSUPPORTED and launches nothing; nothing is allocated.  Every
+ * call looks up the array's device address on the current device (so a
+ * context destroyed and re-created in between is handled); the first call on
+ * a device may also load the library's device code there, so make that first
+ * call before any stream capture.  Every call on a device shares the array: calls
  * that overlap on the GPU race.  Each call rebuilds all the scratch it reads,
  * so earlier contents never leak into a result. */
 glass_status glass_posv_varsize_noalloc(int batch, const int *n_dev, const long long *offA_dev,
@@ -479,9 +481,22 @@ glass_status glass_peak_probe(int kind, int iters, int blocks, int threads, void
 /* ----------------------------------------------------------- diagnostics */
 
 /* Synchronises `stream`, then reads and clears the library's device status
- * word of the current device: GLASS_OK, or GLASS_ERR_TIMEOUT when a bounded
- * device-side wait gave up since the last call. */
+ * word of the current device: GLASS_OK, GLASS_ERR_TIMEOUT when a bounded
+ * device-side wait gave up since the last call, or GLASS_ERR_UNSUPPORTED when
+ * a tensor-core GEMM CTA found its shared memory misaligned (its C is then
+ * left unwritten). */
 glass_status glass_last_device_status(glass_stream_t stream);
+
+/* Test of the bounded-wait path (the paper has no counterpart; failure
+ * handling of the device-side waits above).  Launches the order-64 tcgen05
+ * GEMM of glass_batched_gemm on `batch` problems (A, B, C: contiguous 64 x 64
+ * FP32 batches, 16-byte aligned) with its bulk copies withheld, so that its
+ * first mbarrier waits give up after wait_cycles clock cycles (1 <=
+ * wait_cycles <= 2^31) with nothing in flight: the kernel then records
+ * GLASS_ERR_TIMEOUT for glass_last_device_status, writes nothing to C and
+ * returns, and the context stays usable.  Returns the launch status. */
+glass_status glass_selftest_wait_timeout(const float *A, const float *B, float *C, int batch,
+                                         long long wait_cycles, glass_stream_t stream);
 
 /* Static text for a status code. */
 const char *glass_status_string(glass_status s);

@@ -92,6 +92,7 @@ _SIGS = {
     "glass_mlp_loss_grad": (_i, [_i, _P, _i, _P, _P, _P, _P, _P, _P, _sz, _P]),
     "glass_mlp_adam": (_i, [_i, _P, _P, _P, _P, _i, _f, _f, _f, _f, _P]),
     "glass_last_device_status": (_i, [_P]),
+    "glass_selftest_wait_timeout": (_i, [_P, _P, _P, _i, _ll, _P]),
     "glass_batched_gemm_ex": (_i, [_i, _i, _i, _i, _i, ctypes.c_float, _P, _i, _ll, _P, _i, _ll, ctypes.c_float,
                                    _P, _i, _ll, _i, _OPTS, _P]),
     "glass_riccati_workspace": (ctypes.c_size_t, [_i, _i, _i]),
@@ -282,6 +283,10 @@ def glass_mlp_adam(nparams, w, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e
 
 def glass_last_device_status(stream=None):
     return lib().glass_last_device_status(_stream(stream))
+
+
+def glass_selftest_wait_timeout(A, B, C, batch, wait_cycles, stream=None):
+    return lib().glass_selftest_wait_timeout(_ptr(A), _ptr(B), _ptr(C), batch, wait_cycles, _stream(stream))
 
 
 def glass_batched_gemm_ex(transa, transb, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, opts=None,

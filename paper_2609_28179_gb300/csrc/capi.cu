@@ -944,6 +944,14 @@ glass_status glass_last_device_status(glass_stream_t stream) {
     return v == 0 ? GLASS_OK : (glass_status)v;
 }
 
+glass_status glass_selftest_wait_timeout(const float *A, const float *B, float *C, int batch, long long wait_cycles,
+                                         glass_stream_t stream) {
+    if (batch < 0 || wait_cycles < 1 || wait_cycles > (1ll << 31)) return GLASS_ERR_INVALID_VALUE;
+    if (batch == 0) return GLASS_OK;
+    if (!A || !B || !C) return GLASS_ERR_INVALID_VALUE;
+    return from_cuda(launch_gemm_umma64_ex(A, B, C, batch, wait_cycles, 1, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 const char *glass_status_string(glass_status s) {
     switch (s) {
         case GLASS_OK: return "GLASS_OK";

@@ -270,6 +270,10 @@ cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float 
 // Order-64 products on the fifth-generation tensor cores (3xTF32 split),
 // contiguous 16-byte aligned batches only.
 cudaError_t launch_gemm_umma64(const float *A, const float *B, float *C, int batch, cudaStream_t st);
+// The same with an explicit wait limit (clock cycles) and, for a test of the
+// bounded-wait path, the kernel's bulk copies withheld.
+cudaError_t launch_gemm_umma64_ex(const float *A, const float *B, float *C, int batch, long long wait_cycles,
+                                  int withhold_loads, cudaStream_t st);
 // capi.cu: the device status word of the current device (bounded device-side
 // waits that gave up record GLASS_ERR_TIMEOUT there), or null.
 unsigned *device_status_word();

@@ -261,6 +261,9 @@ constexpr int XCH_OFF = BAR_OFF + 256, XCH_FLOATS = 64 * 65;
 // tensor-memory slot and the failure flag, the exchange buffers.
 constexpr int SMEM_BYTES = XCH_OFF + 2 * XCH_FLOATS * 4;
 constexpr long long WAIT_CYCLES = 2000000000LL;  // about a second
+// Values of the CTA's failure flag: a bounded wait gave up, or the dynamic
+// shared memory is not 1 KB aligned (the swizzled tiles cannot be placed).
+constexpr int kFailTimeout = 1, kFailUnaligned = 2;
 
 // C[p] = A[p] B[p] for p = blockIdx.x, blockIdx.x + gridDim.x, ... < batch;
 // every operand 64 x 64, contiguous (batch stride 4096 floats), 16-byte
@@ -274,14 +277,17 @@ constexpr long long WAIT_CYCLES = 2000000000LL;  // about a second
 //   mma_done[a]  MMAs of problem i complete: op[s] reusable, accumulator a readable
 //   acc_free[a]  accumulator a drained                        (128 arrivals)
 // each waited on with the parity of its use count (i / 2 or i / AS), and the
-// drain warps meet on named barrier 1 for the half-sum exchange.  *status
-// gets GLASS_ERR_TIMEOUT if a wait timed out; from then on every wait is
-// skipped and nothing new is issued, so every role still reaches its
-// barriers.
+// drain warps meet on named barrier 1 for the half-sum exchange.  Every
+// wait gives up after wait_cycles clock cycles; *status then gets
+// GLASS_ERR_TIMEOUT (GLASS_ERR_UNSUPPORTED if the shared memory could not be
+// aligned), every later wait is skipped, nothing new is issued and C is not
+// written, so every role still reaches its barriers.  withhold_loads != 0
+// (a test of that path) makes the issue warp start no bulk copy at all, so
+// the first waits run out with nothing in flight.
 template <int SW, int AS>
 __global__ void __launch_bounds__(32 * (SW + 5), 1)
     k_gemm_umma64(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C, int batch,
-                  unsigned *status) {
+                  unsigned *status, long long wait_cycles, int withhold_loads) {
     static_assert((SW == 4 || SW == 8) && (AS == 2 || AS == 4), "warp roles, accumulator stages");
     constexpr int TCOLS = AS * 128;  // a power of two
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(32 * (SW + 5), 1)
     const int G = gridDim.x, first = blockIdx.x;
     const int count = first < batch ? (batch - first + G - 1) / G : 0;
     if (t == 0) {
-        *failed = (smem_u32(op) & 1023u) != 0;  // the swizzle atoms need 1 KB alignment
+        *failed = (smem_u32(op) & 1023u) != 0 ? kFailUnaligned : 0;  // the swizzle atoms need 1 KB alignment
         for (int k = 0; k < 2; ++k) {
             mbar_init(&raw_full[k], 1);
             mbar_init(&op_full[k], SW * 32);
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(32 * (SW + 5), 1)
 
     auto wait = [&](uint64_t *bar, int use) {
         if (*failed) return;
-        if (!mbar_wait(bar, use & 1, WAIT_CYCLES)) *failed = 1;
+        if (!mbar_wait(bar, use & 1, wait_cycles)) *failed = kFailTimeout;
     };
     auto prob = [&](int i) { return (first + (long long)i * G) * TILE_FLOATS; };
 
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(32 * (SW + 5), 1)
                 for (int u = 0; u < 64; ++u) xb[r * 65 + u] = hold[u];
             asm volatile("bar.sync 1, 128;" ::: "memory");
             float *c = C + prob(i);
-            if (q < 2)
+            if (q < 2 && !*failed)  // after a failure the accumulator holds no product: C stays untouched
 #pragma unroll
                 for (int u = 0; u < 64; ++u) __stcs(c + u * 64 + r, hold[u] + xb[r * 65 + u]);
         }
@@ -379,12 +385,12 @@ __global__ void __launch_bounds__(32 * (SW + 5), 1)
             bulk_g2s(dst + TILE_FLOATS, B + prob(i), TILE_FLOATS * 4, &raw_full[i & 1]);
             loaded = i + 1;
         };
-        for (int i = 0; i < 2 && i < count && !*failed; ++i) load(i);
+        for (int i = 0; i < 2 && i < count && !*failed && !withhold_loads; ++i) load(i);
         for (int i = 0; i < count; ++i) {
             const int s = i & 1, a = i % AS;
             wait(&op_full[s], i >> 1);  // split done: raw[s] consumed, op[s] ready
             if (*failed) break;
-            if (i + 2 < count) load(i + 2);
+            if (i + 2 < count && !withhold_loads) load(i + 2);
             if (i >= AS) wait(&acc_free[a], i / AS - 1);  // problem i - AS drained from accumulator a
             if (*failed) break;
             fence_after_sync();
@@ -400,7 +406,8 @@ __global__ void __launch_bounds__(32 * (SW + 5), 1)
                 mbar_wait(&mma_done[k % AS], (k / AS) & 1, WAIT_CYCLES);
             for (int k = loaded - 1; k >= 0 && k >= loaded - 2; --k)
                 mbar_wait(&raw_full[k & 1], (k >> 1) & 1, WAIT_CYCLES);
-            atomicExch(status, (unsigned)GLASS_ERR_TIMEOUT);
+            atomicExch(status, *failed == kFailUnaligned ? (unsigned)GLASS_ERR_UNSUPPORTED
+                                                         : (unsigned)GLASS_ERR_TIMEOUT);
         }
     }
     fence_before_sync();
@@ -483,7 +490,7 @@ constexpr int BF_SMEM_BYTES = BF_BAR_OFF + 256;
 // SM.
 __global__ void __launch_bounds__(288, 2)
     k_gemm_umma64_bf16(const unsigned short *__restrict__ A, const unsigned short *__restrict__ B,
-                       float *__restrict__ C, int batch, unsigned *status) {
+                       float *__restrict__ C, int batch, unsigned *status, long long wait_cycles) {
     constexpr int SW = 4, AS = 2, TCOLS = 128;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -497,7 +504,7 @@ __global__ void __launch_bounds__(288, 2)
     const int G = gridDim.x, first = blockIdx.x;
     const int count = first < batch ? (batch - first + G - 1) / G : 0;
     if (t == 0) {
-        *failed = (smem_u32(op) & 1023u) != 0;
+        *failed = (smem_u32(op) & 1023u) != 0 ? kFailUnaligned : 0;
         for (int k = 0; k < 2; ++k) {
             mbar_init(&raw_full[k], 1);
             mbar_init(&op_full[k], SW * 32);
@@ -520,7 +527,7 @@ __global__ void __launch_bounds__(288, 2)
 
     auto wait = [&](uint64_t *bar, int use) {
         if (*failed) return;
-        if (!mbar_wait(bar, use & 1, WAIT_CYCLES)) *failed = 1;
+        if (!mbar_wait(bar, use & 1, wait_cycles)) *failed = kFailTimeout;
     };
     auto prob = [&](int i) { return (first + (long long)i * G) * TILE_FLOATS; };  // elements
 
@@ -548,7 +555,7 @@ __global__ void __launch_bounds__(288, 2)
             for (int cc = 0; cc < 64; cc += 32) {
                 float v[32];
                 tmem_ld32(ta + cc, v);
-                if (row >= 0)
+                if (row >= 0 && !*failed)
 #pragma unroll
                     for (int u = 0; u < 32; ++u) __stcs(c + (cc + u) * 64 + row, v[u]);
             }
@@ -587,7 +594,8 @@ __global__ void __launch_bounds__(288, 2)
                 mbar_wait(&mma_done[k % AS], (k / AS) & 1, WAIT_CYCLES);
             for (int k = loaded - 1; k >= 0 && k >= loaded - 2; --k)
                 mbar_wait(&raw_full[k & 1], (k >> 1) & 1, WAIT_CYCLES);
-            atomicExch(status, (unsigned)GLASS_ERR_TIMEOUT);
+            atomicExch(status, *failed == kFailUnaligned ? (unsigned)GLASS_ERR_UNSUPPORTED
+                                                         : (unsigned)GLASS_ERR_TIMEOUT);
         }
     }
     fence_before_sync();

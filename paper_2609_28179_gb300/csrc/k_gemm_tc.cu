@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16 *__restri
 
 }  // namespace
 
-cudaError_t launch_gemm_umma64(const float *A, const float *B, float *C, int batch, cudaStream_t st) {
+cudaError_t launch_gemm_umma64_ex(const float *A, const float *B, float *C, int batch, long long wait_cycles,
+                                  int withhold_loads, cudaStream_t st) {
     if (batch <= 0) return cudaSuccess;
     if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) != 0)
         return cudaErrorInvalidConfiguration;
@@ -230,13 +231,21 @@ cudaError_t launch_gemm_umma64(const float *A, const float *B, float *C, int bat
     constexpr int kSplitWarps = 8, kAccumulators = 2;  // measured best of {4, 8} x {2, 4}
     auto kern = umma::k_gemm_umma64<kSplitWarps, kAccumulators>;
     if ((e = prepare(kern, umma::SMEM_BYTES)) != cudaSuccess) return e;
-    kern<<<batch < sms ? batch : sms, 32 * (kSplitWarps + 5), umma::SMEM_BYTES, st>>>(A, B, C, batch, status);
+    kern<<<batch < sms ? batch : sms, 32 * (kSplitWarps + 5), umma::SMEM_BYTES, st>>>(A, B, C, batch, status,
+                                                                                       wait_cycles, withhold_loads);
     return cudaPeekAtLastError();
+}
+
+cudaError_t launch_gemm_umma64(const float *A, const float *B, float *C, int batch, cudaStream_t st) {
+    return launch_gemm_umma64_ex(A, B, C, batch, umma::WAIT_CYCLES, 0, st);
 }
 
 // BF16 products of order 64 on the fifth-generation tensor cores (kind::f16).
 cudaError_t launch_gemm_umma64_bf16(const void *A, const void *B, float *C, int batch, cudaStream_t st) {
     if (batch <= 0) return cudaSuccess;
+    // 8 KB bulk copies of A and B, 16-byte stores of C
+    if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) != 0)
+        return cudaErrorInvalidConfiguration;
     unsigned *status = device_status_word();
     if (status == nullptr) return cudaErrorInvalidDeviceFunction;
     int dev = 0, sms = 0;
@@ -247,7 +256,7 @@ cudaError_t launch_gemm_umma64_bf16(const void *A, const void *B, float *C, int 
     const int grid = batch < 2 * sms ? batch : 2 * sms;  // two CTAs per SM
     umma::k_gemm_umma64_bf16<<<grid, 288, umma::BF_SMEM_BYTES, st>>>(static_cast<const unsigned short *>(A),
                                                                      static_cast<const unsigned short *>(B), C,
-                                                                     batch, status);
+                                                                     batch, status, umma::WAIT_CYCLES);
     return cudaPeekAtLastError();
 }
 

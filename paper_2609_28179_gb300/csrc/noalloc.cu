@@ -14,15 +14,12 @@
 // them) race on it.  Each call rewrites all of the scratch it reads (the
 // binning kernel resets the ticket and rebuilds the counts and the order),
 // so nothing left over from an earlier call is ever used.
-#include <mutex>
-
 #include "common.cuh"
 
 namespace glass {
 namespace {
 
 constexpr int kNoallocMaxBatch = 65536;
-constexpr int kMaxDevices = 64;
 
 // Scratch of the mixed-size solve for kNoallocMaxBatch instances (the
 // binning header plus one int per instance), held by every GPU that loads
@@ -30,25 +27,16 @@ constexpr int kMaxDevices = 64;
 constexpr size_t kNoallocBytes = 4096 + (size_t)kNoallocMaxBatch * sizeof(int);
 static __device__ __align__(256) unsigned char g_varsize_scratch[kNoallocBytes];
 
-std::mutex g_mu;
-void *g_ptr[kMaxDevices] = {};
-
-// Device address of the array for the current device, looked up once per
-// device.  In host code the array's name is only a host-side stand-in, so
-// the kernels must be given this address.
+// Device address of the array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the kernels must be given
+// this address.  It is looked up on every call rather than cached: a caller
+// that destroys its context (cudaDeviceReset) gets the module loaded again,
+// possibly at another address, and a cached pointer would then dangle.
 cudaError_t scratch_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_varsize_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (g_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_varsize_scratch);
-        if (e != cudaSuccess) return e;
-        g_ptr[dev] = p;
-    }
-    *out = g_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

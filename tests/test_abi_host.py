@@ -170,3 +170,11 @@ def test_fp64_storage_argument_rules(L):
     assert g.glass_batched_trsm(6, 2, BAD, 6, 36, BAD, 6, 12, 4, o, 0) == g.GLASS_ERR_INVALID_VALUE
     o = g.make_opts(dtype=g.GLASS_F64, layout=g.GLASS_LAYOUT_INTERLEAVED32)
     assert g.glass_batched_gemm(4, 4, 4, BAD, 4, 16, BAD, 4, 16, BAD, 4, 16, 4, o, 0) == g.GLASS_ERR_UNSUPPORTED
+
+
+def test_selftest_wait_timeout_rejects_bad_arguments(L):
+    assert g.glass_selftest_wait_timeout(BAD, BAD, BAD, 4, 0, 0) == g.GLASS_ERR_INVALID_VALUE
+    assert g.glass_selftest_wait_timeout(BAD, BAD, BAD, 4, (1 << 31) + 1, 0) == g.GLASS_ERR_INVALID_VALUE
+    assert g.glass_selftest_wait_timeout(BAD, BAD, BAD, -1, 100, 0) == g.GLASS_ERR_INVALID_VALUE
+    assert g.glass_selftest_wait_timeout(None, BAD, BAD, 4, 100, 0) == g.GLASS_ERR_INVALID_VALUE
+    assert g.glass_selftest_wait_timeout(BAD, BAD, BAD, 0, 100, 0) == g.GLASS_OK

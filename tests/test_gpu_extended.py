@@ -119,6 +119,31 @@ def test_umma_gemm64_batches_and_routes(batch):
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("batch", [303, 304, 305, 1000])
+def test_umma_gemm64_bf16_batches_around_two_ctas_per_sm(batch):
+    """BF16 order 64 runs two persistent tcgen05 CTAs per SM (grid
+    min(batch, 2 x SMs)), so batches around and above 2 x 152 give CTAs one,
+    two or many problems: the raw and tile stages are reused, the
+    accumulator-free wait and the phase flips run.  Every product must match
+    the FP64 product of the bf16-rounded operands to FP32 accumulation
+    accuracy, and no bounded wait may have given up."""
+    import torch
+    n = 64
+    A = W.gaussian(batch * n * n, 2800 + batch)
+    B = W.gaussian(batch * n * n, 2900 + batch)
+    Ar, Br = bf16_round(A), bf16_round(B)
+    ref = mats(oracle.gemm(n, n, n, Ar.astype(np.float64), Br.astype(np.float64), batch), batch, n, n)
+    bound = 2 * n * U32 * (np.abs(mats(Ar, batch, n, n)) @ np.abs(mats(Br, batch, n, n))) + 1e-30
+    dA = torch.from_numpy(A).to("cuda").to(torch.bfloat16)
+    dB = torch.from_numpy(B).to("cuda").to(torch.bfloat16)
+    dC = to_dev(np.full(batch * n * n, np.nan, np.float32))
+    o = g.make_opts(dtype=g.GLASS_BF16, math=g.GLASS_MATH_BF16_TC)
+    g.check(g.glass_batched_gemm(n, n, n, dA, n, n * n, dB, n, n * n, dC, n, n * n, batch, o))
+    assert g.glass_last_device_status() == g.GLASS_OK
+    C = mats(host(dC).astype(np.float64), batch, n, n)
+    assert (np.abs(C - ref) <= bound).all(), np.max(np.abs(C - ref) / bound)
+
+
 def test_umma_gemm64_unaligned_operands_take_the_simt_kernel():
     """A 4-byte-offset operand cannot feed the bulk copies; the block-scope
     call still returns the FP32-accurate product (through the SIMT kernel)."""

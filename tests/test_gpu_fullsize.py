@@ -147,6 +147,31 @@ def test_tensor_core_gemm_65536_sampled(n):
         assert (np.abs(got - ref) <= (2 * n * U32 + 2.0 ** -20) * absab + 1e-30).all(), (n, b)
 
 
+@pytest.mark.parametrize("n", [16, 32, 64])
+def test_bf16_tensor_core_gemm_65536_sampled(n):
+    """The BF16 mode at the bench's batch (order 64: two tcgen05 CTAs per SM,
+    each walking about 215 problems through its pipeline): sampled products
+    against the FP64 product of the bf16 operands, and a clear status word."""
+    import torch
+    batch = 65536
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5250 + n)
+    A = torch.randn(batch * n * n, generator=gen, device="cuda").to(torch.bfloat16)
+    B = torch.randn(batch * n * n, generator=gen, device="cuda").to(torch.bfloat16)
+    C = torch.full((batch * n * n,), float("nan"), device="cuda")
+    o = g.make_opts(dtype=g.GLASS_BF16, math=g.GLASS_MATH_BF16_TC)
+    g.check(g.glass_batched_gemm(n, n, n, A, n, n * n, B, n, n * n, C, n, n * n, batch, o))
+    assert g.glass_last_device_status() == g.GLASS_OK
+    Af, Bf = A.float(), B.float()
+    for b in _sample(batch, 5350 + n):
+        b = int(b)
+        a, bb = _problem(Af, b, n * n), _problem(Bf, b, n * n)
+        ref = W.from_colmajor(oracle.gemm(n, n, n, a, bb, 1), 1, n, n)
+        got = W.from_colmajor(_problem(C, b, n * n), 1, n, n)
+        absab = np.abs(W.from_colmajor(a, 1, n, n)) @ np.abs(W.from_colmajor(bb, 1, n, n))
+        assert (np.abs(got - ref) <= 2 * n * U32 * absab + 1e-30).all(), (n, b)
+
+
 @pytest.mark.parametrize("n", [32, 64])
 def test_refined_posv_16384_sampled(n):
     import torch
