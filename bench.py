@@ -363,16 +363,17 @@ def gpu_outputs(cell, placement, count):
     return out
 
 
-def cell_errors(op, n, gpu, ref, s):
+def cell_errors(op, n, gpu, ref, s_ref, s):
     """Largest per-problem relative error max|y - y*| / max|y*| over the first
-    s problems, over every floating output (posv: only L's lower triangle is
-    defined), and the number of pivot indices that differ from the oracle's."""
+    s problems (the oracle's outputs hold s_ref >= s problems), over every
+    floating output (posv: only L's lower triangle is defined), and the
+    number of pivot indices that differ from the oracle's."""
     import numpy as np
     err = 0.0
     for key in ("X", "L", "LU"):
         if key not in gpu or key not in ref:
             continue
-        per = ref[key].size // s
+        per = ref[key].size // s_ref
         yy = gpu[key].reshape(-1)[: s * per].reshape(s, per)
         rr = ref[key].reshape(-1)[: s * per].reshape(s, per)
         if key == "L":
@@ -425,7 +426,7 @@ def cpu_baseline(hosts, ops_sizes, batch, budget_s=12.0, gpu=None):
         errs[label] = []
         for (op, n), (s, ref), got in zip(ops_sizes, refs, outs):
             cnt = min(s, got["count"])
-            e, piv = cell_errors(op, n, got, ref, cnt)
+            e, piv = cell_errors(op, n, got, ref, s, cnt)
             errs[label].append((e, piv, cnt))
     return {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
             "value_1core": len(ops_sizes) * batch / one_time,

@@ -81,6 +81,7 @@ def _load():
                                        ctypes.c_double, _D, _ll, _int]),
             "oracle_btd_matvec_f64": (None, [_int, _int, _D, _D, _D, _D, _int]),
             "oracle_btd_posv_f64": (None, [_int, _int, _D, _D, _D, _I, _int]),
+            "oracle_btd_pcg_f64": (None, [_int, _int, _D, _D, _D, _D, _int, ctypes.c_double, _I, _int]),
             "oracle_rot3_compose_f64": (None, [_int, _D, _ll, _D, _ll, _int]),
             "oracle_se3_apply_f64": (None, [_int, _D, _ll, _int, _D, _ll, _D, _ll, _int]),
             "oracle_mlp_nparams": (_ll, [_int, _int, _int]),
@@ -348,6 +349,15 @@ def btd_posv(nb, N, D, O, b, batch):
     _load().oracle_btd_posv_f64(nb, N, _dp(_f64(D)), _dp(_f64(O) if N > 1 else np.zeros(1)), _dp(x), _ip(info),
                                 batch)
     return x, info[:batch]
+
+
+def btd_pcg(nb, N, D, O, b, x0, iters, tol, batch):
+    """Block-Jacobi PCG on the block-tridiagonal T: (x, iters_done)."""
+    x = _f64(x0)
+    done = np.zeros(max(1, batch), dtype=np.int32)
+    _load().oracle_btd_pcg_f64(nb, N, _dp(_f64(D)), _dp(_f64(O)), _dp(_f64(b)), _dp(x), int(iters), float(tol),
+                               _ip(done), batch)
+    return x, done[:batch]
 
 
 def rot3_compose(chain, Rs, batch, sRs=None, sR=9):

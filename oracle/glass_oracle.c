@@ -1001,3 +1001,92 @@ void oracle_btd_posv_f64(int nb, int N, const double *D, const double *O, double
         free(T);
     }
 }
+
+/* Batched preconditioned conjugate gradient on the symmetric block-
+ * tridiagonal T above: the iterative solver of the structured routines
+ * (Sec. III-B names "direct and iterative solvers" for trajectory
+ * optimization and fixes neither the method nor the preconditioner; the
+ * reading here is the textbook PCG of Hestenes and Stiefel with the
+ * block-Jacobi preconditioner M = blockdiag(D_0, ..., D_{N-1})):
+ *   r = b - T x, z = M^{-1} r, p = z, rho = r'z, rho0 = rho;
+ *   k = 0; while k < iters and rho > tol^2 rho0 (and rho > 0):
+ *     q = T p; alpha = rho / p'q; x = x + alpha p; r = r - alpha q;
+ *     z = M^{-1} r; rho_new = r'z; p = z + (rho_new / rho) p;
+ *     rho = rho_new; k = k + 1.
+ * M^{-1} v applies each D_i^{-1} by the dense Cholesky solve of D_i.  x holds
+ * the initial guess on entry and the last iterate on return; iters_done[b]
+ * is k, or -1 (x untouched) when some D_i is not positive definite, and the
+ * loop also stops (k as reached) when p'Tp <= 0. */
+void oracle_btd_pcg_f64(int nb, int N, const double *D, const double *O, const double *bv, double *x,
+                        int iters, double tol, int *iters_done, int batch)
+{
+    OMP_FOR
+    for (int b = 0; b < batch; ++b) {
+        const int m = N * nb;
+        const double *Db = D + (long long)b * N * nb * nb;
+        const double *Ob = O + (long long)b * (N > 1 ? N - 1 : 0) * nb * nb;
+        const double *bb = bv + (long long)b * m;
+        double *xb = x + (long long)b * m;
+        double *T = (double *)malloc(sizeof(double) * (size_t)m * m);
+        double *L = (double *)malloc(sizeof(double) * (size_t)N * nb * nb);
+        double *r = (double *)malloc(sizeof(double) * (size_t)m * 4);
+        double *z = r + m, *p = z + m, *q = p + m;
+        btd_assemble(nb, N, Db, Ob, T);
+        int ok = 1;
+        for (int i = 0; i < N && ok; ++i) {   /* Cholesky factors of the diagonal blocks */
+            memcpy(L + (long long)i * nb * nb, Db + (long long)i * nb * nb, sizeof(double) * nb * nb);
+            if (potrf_one(nb, L + (long long)i * nb * nb, nb) != 0) ok = 0;
+        }
+        if (!ok) {
+            iters_done[b] = -1;
+        } else {
+            /* r = b - T x */
+            for (int i = 0; i < m; ++i) {
+                double s = 0.0;
+                for (int c = 0; c < m; ++c) s += T[c * m + i] * xb[c];
+                r[i] = bb[i] - s;
+            }
+            /* z = M^{-1} r */
+            for (int i = 0; i < m; ++i) z[i] = r[i];
+            for (int i = 0; i < N; ++i) {
+                forward_lower(nb, L + (long long)i * nb * nb, nb, z + i * nb, 0);
+                backward_lower_transposed(nb, L + (long long)i * nb * nb, nb, z + i * nb);
+            }
+            for (int i = 0; i < m; ++i) p[i] = z[i];
+            double rho = 0.0;
+            for (int i = 0; i < m; ++i) rho += r[i] * z[i];
+            const double rho0 = rho;
+            int k = 0;
+            while (k < iters && rho > 0.0 && rho > tol * tol * rho0) {
+                double pq = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    double s = 0.0;
+                    for (int c = 0; c < m; ++c) s += T[c * m + i] * p[c];
+                    q[i] = s;
+                    pq += p[i] * s;
+                }
+                if (!(pq > 0.0)) break;
+                const double alpha = rho / pq;
+                for (int i = 0; i < m; ++i) {
+                    xb[i] += alpha * p[i];
+                    r[i] -= alpha * q[i];
+                }
+                for (int i = 0; i < m; ++i) z[i] = r[i];
+                for (int i = 0; i < N; ++i) {
+                    forward_lower(nb, L + (long long)i * nb * nb, nb, z + i * nb, 0);
+                    backward_lower_transposed(nb, L + (long long)i * nb * nb, nb, z + i * nb);
+                }
+                double rho_new = 0.0;
+                for (int i = 0; i < m; ++i) rho_new += r[i] * z[i];
+                const double beta = rho_new / rho;
+                for (int i = 0; i < m; ++i) p[i] = z[i] + beta * p[i];
+                rho = rho_new;
+                ++k;
+            }
+            iters_done[b] = k;
+        }
+        free(r);
+        free(L);
+        free(T);
+    }
+}

@@ -20,3 +20,23 @@ def test_stream_assignment_is_longest_first_and_balanced():
     # the two longest cells never share a stream when there are two or more
     i1, i2 = sorted(range(len(per)), key=lambda i: -per[i])[:2]
     assert bench.stream_assignment(per, 2)[i1] != bench.stream_assignment(per, 2)[i2]
+
+
+def test_cell_errors_per_problem_relative_and_lower_triangle_only():
+    """The bench's accuracy figure: the largest per-problem max|y - y*| /
+    max|y*| over the compared prefix; for posv only L's lower triangle
+    counts; pivot mismatches are counted."""
+    import numpy as np
+    n, s_ref, s = 3, 10, 4
+    ref = {"X": np.arange(s_ref * n, dtype=float) + 1.0,
+           "L": np.tile(np.eye(n).T.reshape(-1) * 2.0, s_ref), "ipiv": np.zeros(s_ref * n, np.int32)}
+    got = {"X": ref["X"][: s * n].copy(), "L": ref["L"][: s * n * n].copy(), "ipiv": np.zeros(s * n, np.int32),
+           "count": s}
+    got["X"][n + 1] *= 1.01                 # problem 1, |x*| max 6
+    got["L"][2 * n * n + n * 1 + 0] = 99.0  # problem 2, (0, 1): upper triangle, ignored
+    got["ipiv"][5] = 2
+    e, piv = bench.cell_errors("posv", n, got, ref, s_ref, s)
+    assert abs(e - 0.05 / 6.0) < 1e-12 and piv == 1
+    got["L"][2 * n * n + 1] = 2.5           # problem 2, (1, 0): lower triangle
+    e, _ = bench.cell_errors("posv", n, got, ref, s_ref, s)
+    assert abs(e - 2.5 / 2.0) < 1e-12

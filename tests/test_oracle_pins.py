@@ -796,3 +796,85 @@ def test_btd_scalar_tridiagonal_closed_form_and_info():
     O[:] = 0.0
     _, info = oracle.btd_posv(2, 3, _btd_flat(D), _btd_flat(O), np.zeros(6), 1)
     assert info[0] == 3
+
+
+# ------------------------------------------------ block-Jacobi PCG (iterative)
+def _btd_spd(nb, N, batch, seed):
+    """An SPD block-tridiagonal case (off-diagonal blocks halved; positive
+    definiteness checked with numpy.linalg.eigvalsh)."""
+    D, O = _btd_case(nb, N, batch, seed)
+    O = 0.5 * O
+    assert (np.linalg.eigvalsh(_btd_dense(D, O)) > 0).all()
+    return D, O
+
+
+def _blockdiag_inverse(D):
+    """Dense inverse of blockdiag(D_0..D_{N-1}) of one problem (numpy.linalg.inv per block)."""
+    N, nb = D.shape[0], D.shape[1]
+    M = np.zeros((N * nb, N * nb))
+    for i in range(N):
+        M[i * nb:(i + 1) * nb, i * nb:(i + 1) * nb] = np.linalg.inv(D[i])
+    return M
+
+
+@pytest.mark.parametrize("nb,N", [(1, 9), (3, 5), (6, 4)])
+def test_btd_pcg_iterates_match_scipy_cg(nb, N):
+    """Each PCG iterate equals SciPy's preconditioned CG iterate (same x0,
+    preconditioner blockdiag(D)^-1, no tolerance stop) for k = 1..6."""
+    from scipy.sparse.linalg import cg
+    batch = 3
+    D, O = _btd_spd(nb, N, batch, 140 + nb)
+    T = _btd_dense(D, O)
+    rng = np.random.default_rng(141)
+    b = rng.standard_normal((batch, N * nb))
+    x0 = rng.standard_normal((batch, N * nb))
+    for k in range(1, 7):
+        X, done = oracle.btd_pcg(nb, N, _btd_flat(D), _btd_flat(O), b.reshape(-1), x0.reshape(-1), k, 0.0, batch)
+        X = X.reshape(batch, -1)
+        assert (done == k).all()
+        for p in range(batch):
+            its = []
+            cg(T[p], b[p], x0=x0[p].copy(), rtol=0.0, atol=0.0, maxiter=k, M=_blockdiag_inverse(D[p]),
+               callback=lambda xk: its.append(xk.copy()))
+            assert len(its) == k
+            assert np.abs(X[p] - its[-1]).max() <= 1e-10 * np.abs(its[-1]).max(), (k, p)
+
+
+def test_btd_pcg_converges_to_the_direct_solve_and_lowers_the_energy_error():
+    """In exact arithmetic CG ends within N*nb steps; the FP64 iterate then
+    matches SciPy's banded Cholesky solve, and the T-norm of the error never
+    grows from one iterate to the next (CG minimises it over the Krylov space)."""
+    nb, N, batch = 4, 6, 2
+    D, O = _btd_spd(nb, N, batch, 150)
+    T = _btd_dense(D, O)
+    b = np.random.default_rng(151).standard_normal((batch, N * nb))
+    x0 = np.zeros_like(b)
+    want = np.linalg.solve(T, b[..., None])[..., 0]
+    prev = None
+    for k in range(0, N * nb + 1):
+        X, _ = oracle.btd_pcg(nb, N, _btd_flat(D), _btd_flat(O), b.reshape(-1), x0.reshape(-1), k, 0.0, batch)
+        e = X.reshape(batch, -1) - want
+        energy = np.einsum("bi,bij,bj->b", e, T, e)
+        if prev is not None:
+            assert (energy <= prev * (1 + 1e-9) + 1e-24).all(), k
+        prev = energy
+    assert np.abs(e).max() <= 1e-8 * np.abs(want).max()
+
+
+def test_btd_pcg_exact_preconditioner_and_failure():
+    """A single block (or zero off-diagonal blocks) makes the preconditioner
+    T itself: one iteration solves the system and the tolerance stops the
+    loop there; a non-SPD diagonal block gives iters_done = -1 and leaves x."""
+    for nb, N in ((5, 1), (3, 4)):
+        D, O = _btd_case(nb, N, 2, 160 + N)
+        O[:] = 0.0
+        b = np.random.default_rng(161).standard_normal((2, N * nb))
+        X, done = oracle.btd_pcg(nb, N, _btd_flat(D), _btd_flat(O), b.reshape(-1), np.zeros(2 * N * nb), 10, 1e-8, 2)
+        assert (done == 1).all()
+        want = np.linalg.solve(_btd_dense(D, O), b[..., None])[..., 0]
+        assert np.abs(X.reshape(2, -1) - want).max() <= 1e-12 * np.abs(want).max()
+    D, O = _btd_case(2, 3, 1, 162)
+    D[0, 2] = -np.eye(2)
+    x0 = np.arange(6.0)
+    X, done = oracle.btd_pcg(2, 3, _btd_flat(D), _btd_flat(O), np.ones(6), x0, 5, 0.0, 1)
+    assert done[0] == -1 and np.array_equal(X, x0)
