@@ -463,6 +463,27 @@ glass_status glass_batched_btd_matvec(int nb, int N, const void *D, const void *
 glass_status glass_batched_btd_posv(int nb, int N, void *D, void *O, void *b, int *info, int batch,
                                     const glass_opts *opts, glass_stream_t stream);
 
+/* Iterative solve of the same T x = b (Sec. III-B names direct and
+ * iterative solvers for these operators; the method is the reading of this
+ * library): preconditioned conjugate gradient with the block-Jacobi
+ * preconditioner M = blockdiag(D_0, ..., D_{N-1}).  r = b - T x, z = M^{-1}
+ * r, p = z, rho = r'z, rho0 = rho; while k < iters and rho > tol^2 rho0 (and
+ * rho > 0): q = T p, alpha = rho / p'q (the loop also ends when p'q <= 0),
+ * x += alpha p, r -= alpha q, z = M^{-1} r, p = z + (r'z / rho) p, k += 1.
+ * tol = 0 runs exactly `iters` iterations on an SPD T.  x [batch][N*nb]
+ * holds the initial guess on entry and the last iterate on return (warm
+ * starts); b [batch][N*nb] is read only; D and O as above, read only.
+ * iters_done[b] (device int) receives k, or -1 when some D_i is not
+ * positive definite (x is then left as given).  ws: device scratch of
+ * glass_btd_pcg_workspace(nb, N, batch) bytes, 16-byte aligned (it holds
+ * the D_i^{-1}); else GLASS_ERR_WORKSPACE.  1 <= nb <= 32, 1 <= N <= 64,
+ * iters >= 0, tol >= 0.  One warp per problem; placement pack = warps per
+ * CTA (0: up to 4 as shared memory allows). */
+size_t glass_btd_pcg_workspace(int nb, int N, int batch);
+glass_status glass_batched_btd_pcg(int nb, int N, const void *D, const void *O, const void *b, void *x,
+                                   int iters, float tol, int *iters_done, void *ws, size_t ws_bytes,
+                                   int batch, const glass_opts *opts, glass_stream_t stream);
+
 /* ------------------------------------------------------- measurement aid */
 
 /* Pipe-throughput probe (no counterpart in the paper; it supplies the

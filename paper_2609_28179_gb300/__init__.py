@@ -115,6 +115,8 @@ _SIGS = {
     "glass_batched_trsv": (_i, [_i, _P, _i, _ll, _P, _ll, _i, _OPTS, _P]),
     "glass_batched_btd_matvec": (_i, [_i, _i, _P, _P, _P, _P, _i, _OPTS, _P]),
     "glass_batched_btd_posv": (_i, [_i, _i, _P, _P, _P, _P, _i, _OPTS, _P]),
+    "glass_btd_pcg_workspace": (_sz, [_i, _i, _i]),
+    "glass_batched_btd_pcg": (_i, [_i, _i, _P, _P, _P, _P, _i, _f, _P, _P, _sz, _i, _OPTS, _P]),
     "glass_robo_placement": (_i, [_i, _i, _i, ctypes.POINTER(glass_placement)]),
     "glass_robo_feasible": (_i, [_i, _i, glass_placement]),
     "glass_peak_probe": (_i, [_i, _i, _i, _i, _P, ctypes.POINTER(ctypes.c_double), _P]),
@@ -373,6 +375,15 @@ def glass_batched_btd_matvec(nb, N, D, O, x, y, batch, opts=None, stream=None):
 def glass_batched_btd_posv(nb, N, D, O, b, info, batch, opts=None, stream=None):
     return lib().glass_batched_btd_posv(nb, N, _ptr(D), _ptr(O), _ptr(b), _ptr(info), batch, _opts(opts),
                                         _stream(stream))
+
+
+def glass_btd_pcg_workspace(nb, N, batch):
+    return lib().glass_btd_pcg_workspace(nb, N, batch)
+
+
+def glass_batched_btd_pcg(nb, N, D, O, b, x, iters, tol, iters_done, ws, ws_bytes, batch, opts=None, stream=None):
+    return lib().glass_batched_btd_pcg(nb, N, _ptr(D), _ptr(O), _ptr(b), _ptr(x), iters, tol, _ptr(iters_done),
+                                       _ptr(ws), ws_bytes, batch, _opts(opts), _stream(stream))
 
 
 def glass_robo_placement(op, n, batch):

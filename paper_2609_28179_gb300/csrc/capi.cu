@@ -863,6 +863,37 @@ glass_status glass_batched_btd_posv(int nb, int N, void *D, void *O, void *b, in
                                      info, batch, pack, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+size_t glass_btd_pcg_workspace(int nb, int N, int batch) {
+    if (nb < 1 || N < 1 || batch < 0) return 0;
+    return (size_t)batch * N * nb * nb * sizeof(float);
+}
+
+glass_status glass_batched_btd_pcg(int nb, int N, const void *D, const void *O, const void *b, void *x, int iters,
+                                   float tol, int *iters_done, void *ws, size_t ws_bytes, int batch,
+                                   const glass_opts *opts, glass_stream_t stream) {
+    const glass_opts &o = opts_or_default(opts);
+    GLASS_TRY(check_common(o));
+    if (nb < 1 || N < 1 || batch < 0 || iters < 0 || !(tol >= 0.f)) return GLASS_ERR_INVALID_VALUE;
+    if (nb > 32 || N > 64) return GLASS_ERR_UNSUPPORTED;
+    if (batch == 0) return GLASS_OK;
+    if (o.dtype != GLASS_F32 || o.math != GLASS_MATH_FP32 || o.layout != GLASS_LAYOUT_COLMAJOR)
+        return GLASS_ERR_UNSUPPORTED;
+    if (!D || (N > 1 && !O) || !b || !x || !iters_done) return GLASS_ERR_INVALID_VALUE;
+    if (!ws || ws_bytes < glass_btd_pcg_workspace(nb, N, batch) || (reinterpret_cast<uintptr_t>(ws) & 15) != 0)
+        return GLASS_ERR_WORKSPACE;
+    if (o.placement.scope != GLASS_SCOPE_AUTO && o.placement.scope != GLASS_SCOPE_WARP) return GLASS_ERR_INVALID_VALUE;
+    int pack = o.placement.pack;
+    if (pack == 0) {  // as many warps per CTA (up to 4) as fit the per-CTA shared memory
+        pack = 4;
+        while (pack > 1 && btd_pcg_smem(nb, N, pack) > 100 * 1024) pack >>= 1;
+    }
+    if (!valid_pack(pack)) return GLASS_ERR_INVALID_VALUE;
+    if (btd_pcg_smem(nb, N, pack) > 227 * 1024) return GLASS_ERR_UNSUPPORTED;
+    return from_cuda(launch_btd_pcg(nb, N, static_cast<const float *>(D), static_cast<const float *>(O),
+                                    static_cast<const float *>(b), static_cast<float *>(x), iters, tol, iters_done,
+                                    static_cast<float *>(ws), batch, pack, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 glass_status glass_robo_placement(int op, int n, int batch, glass_placement *out) {
     if (out == nullptr || op < 0 || op >= GLASS_ROBO_NUM_OPS || batch < 0) return GLASS_ERR_INVALID_VALUE;
     const Placement pl = robo_resolve(op, n < 1 ? 1 : n, batch);

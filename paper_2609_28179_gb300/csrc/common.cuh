@@ -122,51 +122,41 @@ __device__ __forceinline__ void divmod_small(int e, int d, float inv_d, int &q, 
 }
 
 // --------------------------------------------------------------- staging
-// Copy problems b0 .. b0+cnt-1 of M (rows x cols each) into shared memory,
-// problem p at sm + p*S, column-major with leading dimension `rows`.  Uses
-// 16-byte streaming loads when the batch is packed and aligned.  All
-// threads of the CTA take part; the caller synchronises afterwards.
+// Copy problems b0 .. b0+cnt-1 of M (rows x cols each, column-major layout)
+// into shared memory, problem p at sm + p*S, column-major with leading
+// dimension `rows`.  Every element is one 4-byte cp.async copy (consecutive
+// threads copy consecutive elements: 128 coalesced bytes per warp for a
+// packed batch), all of a thread's copies in flight at once, so a CTA pays
+// one memory round trip however many problems it stages (a register-staged
+// loop waits once per few loads, which dominates when a few warps per SM
+// stage many small problems).  All threads of the CTA take part; the copies
+// are complete for this thread on return, and the caller synchronises the
+// CTA afterwards.
 __device__ __forceinline__ void stage_in(float *sm, int S, const Mat &M, int b0, int cnt) {
     const int per = M.rows * M.cols;
     const int total = cnt * per;
-    const float inv = 1.0f / (float)per;
+    const int T = blockDim.x;
+    // element e = p * per + q of the staged range, advanced by T per copy
+    int p = threadIdx.x / per, q = threadIdx.x - p * per;
+    const int dp = T / per, dq = T - dp * per;
     if (M.packed()) {
         const float *g = M.p + (long long)b0 * per;
-        if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
-            const int nv = total >> 2;
-            const float4 *g4 = reinterpret_cast<const float4 *>(g);
-#pragma unroll 4
-            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-                float4 x = __ldcs(g4 + v);
-                int p, q;
-                divmod_small(v * 4, per, inv, p, q);
-                float xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    sm[p * S + q] = xs[u];
-                    if (++q == per) { q = 0; ++p; }
-                }
-            }
-            for (int e = (nv << 2) + threadIdx.x; e < total; e += blockDim.x) {
-                int p, q;
-                divmod_small(e, per, inv, p, q);
-                sm[p * S + q] = __ldcs(g + e);
-            }
-        } else {
-            for (int e = threadIdx.x; e < total; e += blockDim.x) {
-                int p, q;
-                divmod_small(e, per, inv, p, q);
-                sm[p * S + q] = __ldcs(g + e);
-            }
+        for (int e = threadIdx.x; e < total; e += T) {
+            cp_async4(sm + p * S + q, g + e);
+            p += dp;
+            q += dq;
+            if (q >= per) { q -= per; ++p; }
         }
     } else {
-        for (int e = threadIdx.x; e < total; e += blockDim.x) {
-            int p, q;
-            divmod_small(e, per, inv, p, q);
+        for (int e = threadIdx.x; e < total; e += T) {
             const int j = q / M.rows, i = q - j * M.rows;
-            sm[p * S + q] = M.get(b0 + p, i, j);
+            cp_async4(sm + p * S + q, M.p + (long long)(b0 + p) * M.s + (long long)j * M.ld + i);
+            p += dp;
+            q += dq;
+            if (q >= per) { q -= per; ++p; }
         }
     }
+    cp_async_wait_all();
 }
 
 // Inverse of stage_in: write the staged problems back to M.
@@ -324,6 +314,9 @@ cudaError_t launch_btd_matvec(int nb, int N, const float *D, const float *O, con
                               int pack, cudaStream_t st);
 cudaError_t launch_btd_posv(int nb, int N, float *D, float *O, float *bx, int *info, int batch, int pack,
                             cudaStream_t st);
+size_t btd_pcg_smem(int nb, int N, int pack);
+cudaError_t launch_btd_pcg(int nb, int N, const float *D, const float *O, const float *b, float *x, int iters,
+                           float tol, int *done, float *ws, int batch, int pack, cudaStream_t st);
 // k_fp64.cu (op = glass_op)
 bool feasible_f64(int op, int n, Placement pl);
 cudaError_t launch_gemm_f64(int m, int n, int k, const double *A, int lda, long long sA, const double *B, int ldb,

@@ -266,6 +266,205 @@ __global__ void __launch_bounds__(256) k_btd_posv(int nb, int N, float *D, float
     }
 }
 
+// ------------------------------------------------ block-Jacobi PCG
+// Per-warp shared memory (floats) of k_btd_pcg: the Cholesky factor of one
+// diagonal block (pitch NB + 1) and the four vectors x, r, p, w of N*nb
+// entries each (element (i, r) of a vector at i * nb + r).
+__host__ __device__ inline int pcg_warp_floats(int NB, int nb, int N) { return NB * (NB + 1) + 4 * N * nb; }
+
+// Sum over the lanes of a warp; every lane receives the same bits.
+__device__ __forceinline__ float lane_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(GLASS_FULL_MASK, v, o);
+    return v;
+}
+
+// out = T v over the whole problem; returns this lane's share of v'out.
+// Lane r forms row r of every block row: D_i v_i + O_{i-1} v_{i-1} +
+// O_i^T v_{i+1}, the entries of v read from shared memory as broadcasts.
+template <int NB>
+__device__ __forceinline__ float pcg_matvec(int nb, int N, const float *Db, const float *Ob, const float *v,
+                                            float *out, int r) {
+    const long long bb = (long long)nb * nb;
+    float dotp = 0.f;
+    if (r < nb) {
+        for (int i = 0; i < N; ++i) {
+            const float *Di = Db + i * bb, *vi = v + i * nb;
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (c < nb) s = fmaf(Di[c * nb + r], vi[c], s);
+            if (i > 0) {
+                const float *Op = Ob + (i - 1) * bb, *vp = vi - nb;
+#pragma unroll
+                for (int c = 0; c < NB; ++c)
+                    if (c < nb) s = fmaf(Op[c * nb + r], vp[c], s);
+            }
+            if (i + 1 < N) {
+                const float *On = Ob + i * bb, *vn = vi + nb;
+#pragma unroll
+                for (int c = 0; c < NB; ++c)
+                    if (c < nb) s = fmaf(On[r * nb + c], vn[c], s);
+            }
+            out[i * nb + r] = s;
+            dotp = fmaf(vi[r], s, dotp);
+        }
+    }
+    __syncwarp();
+    return dotp;
+}
+
+// z = M^{-1} v blockwise with the stored inverses (symmetric, column-major:
+// lane r reads row r of each as a coalesced column); returns this lane's
+// share of v'z.
+template <int NB>
+__device__ __forceinline__ float pcg_precond(int nb, int N, const float *Mb, const float *v, float *z, int r) {
+    const long long bb = (long long)nb * nb;
+    float dotp = 0.f;
+    if (r < nb) {
+        for (int i = 0; i < N; ++i) {
+            const float *Mi = Mb + i * bb, *vi = v + i * nb;
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (c < nb) s = fmaf(Mi[c * nb + r], vi[c], s);
+            z[i * nb + r] = s;
+            dotp = fmaf(vi[r], s, dotp);
+        }
+    }
+    __syncwarp();
+    return dotp;
+}
+
+// Block-Jacobi preconditioned conjugate gradient on the symmetric
+// block-tridiagonal T, one problem per warp, lane r the r-th row of every
+// block.  Set-up: each D_i is factored in registers (Cholesky, row per
+// lane) and D_i^{-1} = L_i^{-T} L_i^{-1} is written to the workspace, lane c
+// forming column c by a forward and a backward sweep over L_i in shared
+// memory.  Then the textbook recurrence: r = b - T x, z = M^{-1} r, p = z,
+// rho = r'z; while k < iters and rho > tol2 * rho0 (and rho > 0): q = T p,
+// alpha = rho / p'q (stop if p'q <= 0), x += alpha p, r -= alpha q,
+// z = M^{-1} r, p = z + (r'z / rho) p.  The reductions are warp sums, so the
+// loop control is uniform over the warp.
+template <int NB>
+__global__ void __launch_bounds__(256) k_btd_pcg(int nb, int N, const float *D, const float *O, const float *bv,
+                                                 float *x, int iters, float tol2, int *done, float *ws, int batch) {
+    constexpr int P = NB + 1;
+    extern __shared__ float smem[];
+    const int r = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int m = N * nb;
+    float *Ls = smem + (long long)w * pcg_warp_floats(NB, nb, N);
+    float *xs = Ls + NB * P, *rs = xs + m, *ps = rs + m, *vs = ps + m;
+    const long long b = (long long)blockIdx.x * (blockDim.x >> 5) + w;
+    if (b >= batch) return;  // whole warp
+    const long long bb = (long long)nb * nb;
+    const float *Db = D + b * N * bb, *Ob = O + b * (N > 1 ? N - 1 : 0) * bb;
+    float *Mb = ws + b * N * bb;
+    const bool live = r < nb;
+    // ------------------------------------------ inverses of the diagonal blocks
+    for (int i = 0; i < N; ++i) {
+        const float *Di = Db + i * bb;
+        float d[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) d[c] = (c < nb && live) ? Di[c * nb + r] : 0.f;
+        bool fail = false;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            if (j < nb) {
+                const float djj = __shfl_sync(GLASS_FULL_MASK, d[j], j);
+                if (!(djj > 0.f)) fail = true;
+                const float l = sqrtf(djj), rl = 1.0f / l;
+                if (r == j) d[j] = l;
+                else if (r > j) d[j] *= rl;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    if (k > j && k < nb) {
+                        const float lkj = __shfl_sync(GLASS_FULL_MASK, d[j], k);
+                        if (r >= k) d[k] = fmaf(-d[j], lkj, d[k]);
+                    }
+                }
+            }
+        }
+        if (fail) {  // uniform: every lane saw the same pivots
+            if (r == 0) done[b] = -1;
+            return;
+        }
+        if (live)
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (c < nb) Ls[r * P + c] = c <= r ? d[c] : 0.f;
+        __syncwarp();
+        if (live) {
+            float y[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {  // L y = e_r
+                if (j < nb) {
+                    float s = j == r ? 1.f : 0.f;
+#pragma unroll
+                    for (int k = 0; k < NB; ++k)
+                        if (k < j) s = fmaf(-Ls[j * P + k], y[k], s);
+                    y[j] = s / Ls[j * P + j];
+                }
+            }
+#pragma unroll
+            for (int j = NB - 1; j >= 0; --j) {  // L^T z = y
+                if (j < nb) {
+                    float s = y[j];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k)
+                        if (k > j && k < nb) s = fmaf(-Ls[k * P + j], y[k], s);
+                    y[j] = s / Ls[j * P + j];
+                }
+            }
+            float *Mi = Mb + i * bb;
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+                if (j < nb) Mi[r * nb + j] = y[j];  // column r (= row r) of D_i^{-1}
+        }
+        __syncwarp();
+    }
+    __threadfence_block();  // the inverses are read back by other lanes of this warp
+    __syncwarp();
+    // ------------------------------------------ r = b - T x, z = M^{-1} r, p = z
+    const float *bb_ = bv + b * m;
+    float *xb = x + b * m;
+    if (live)
+        for (int i = 0; i < N; ++i) xs[i * nb + r] = xb[i * nb + r];
+    __syncwarp();
+    pcg_matvec<NB>(nb, N, Db, Ob, xs, vs, r);
+    if (live)
+        for (int i = 0; i < N; ++i) rs[i * nb + r] = bb_[i * nb + r] - vs[i * nb + r];
+    __syncwarp();
+    float rho = lane_sum(pcg_precond<NB>(nb, N, Mb, rs, ps, r));
+    const float rho0 = rho;
+    int k = 0;
+    while (k < iters && rho > 0.f && rho > tol2 * rho0) {
+        const float pq = lane_sum(pcg_matvec<NB>(nb, N, Db, Ob, ps, vs, r));
+        if (!(pq > 0.f)) break;
+        const float alpha = rho / pq;
+        if (live)
+            for (int i = 0; i < N; ++i) {
+                const int e = i * nb + r;
+                xs[e] = fmaf(alpha, ps[e], xs[e]);
+                rs[e] = fmaf(-alpha, vs[e], rs[e]);
+            }
+        __syncwarp();
+        const float rho_new = lane_sum(pcg_precond<NB>(nb, N, Mb, rs, vs, r));
+        const float beta = rho_new / rho;
+        if (live)
+            for (int i = 0; i < N; ++i) {
+                const int e = i * nb + r;
+                ps[e] = fmaf(beta, ps[e], vs[e]);
+            }
+        __syncwarp();
+        rho = rho_new;
+        ++k;
+    }
+    if (live)
+        for (int i = 0; i < N; ++i) xb[i * nb + r] = xs[i * nb + r];
+    if (r == 0) done[b] = k;
+}
+
 int nb_bucket(int nb) { return nb <= 8 ? 8 : nb <= 16 ? 16 : 32; }
 
 }  // namespace
@@ -315,6 +514,22 @@ cudaError_t launch_btd_posv(int nb, int N, float *D, float *O, float *bx, int *i
     cudaError_t e = prepare_kernel(reinterpret_cast<const void *>(kern), sm);
     if (e != cudaSuccess) return e;
     kern<<<grid, th, sm, st>>>(nb, N, D, O, bx, info, batch);
+    return cudaPeekAtLastError();
+}
+
+size_t btd_pcg_smem(int nb, int N, int pack) {
+    return (size_t)pack * pcg_warp_floats(nb_bucket(nb), nb, N) * 4;
+}
+
+cudaError_t launch_btd_pcg(int nb, int N, const float *D, const float *O, const float *b, float *x, int iters,
+                           float tol, int *done, float *ws, int batch, int pack, cudaStream_t st) {
+    const int grid = ceil_div(batch, pack), th = 32 * pack;
+    const int NB = nb_bucket(nb);
+    const size_t sm = btd_pcg_smem(nb, N, pack);
+    auto kern = NB == 8 ? k_btd_pcg<8> : NB == 16 ? k_btd_pcg<16> : k_btd_pcg<32>;
+    cudaError_t e = prepare_kernel(reinterpret_cast<const void *>(kern), sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, th, sm, st>>>(nb, N, D, O, b, x, iters, tol * tol, done, ws, batch);
     return cudaPeekAtLastError();
 }
 

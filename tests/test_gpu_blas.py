@@ -138,3 +138,83 @@ def test_btd_posv_reports_the_failing_global_column():
     dinfo = _dev(np.zeros(batch, np.int32), np.int32)
     g.check(g.glass_batched_btd_posv(nb, N, _dev(D), _dev(O), _dev(np.zeros(batch * N * nb)), dinfo, batch))
     assert np.array_equal(_host(dinfo), info_ref) and (info_ref[1::2] == 3).all()
+
+
+def _btd_spd(nb, N, batch, seed):
+    """SPD block-tridiagonal inputs (the off-diagonal blocks of _btd halved)."""
+    D, O = _btd(nb, N, batch, seed)
+    return D, (0.5 * O).astype(np.float32)
+
+
+def _pcg(nb, N, D, O, b, x0, iters, tol, batch, pack=0, ws_bytes=None):
+    import torch
+    dx = _dev(x0)
+    done = _dev(np.full(batch, -7, np.int32), np.int32)
+    need = g.glass_btd_pcg_workspace(nb, N, batch)
+    ws = torch.empty(max(16, need), dtype=torch.uint8, device="cuda")
+    st = g.glass_batched_btd_pcg(nb, N, _dev(D), _dev(O), _dev(b), dx, iters, tol, done, ws,
+                                 need if ws_bytes is None else ws_bytes, batch, g.make_opts(pack=pack))
+    return st, _host(dx), _host(done)
+
+
+@pytest.mark.parametrize("nb,N", [(1, 1), (1, 9), (3, 5), (6, 16), (12, 8), (16, 3), (32, 2), (7, 33), (12, 32),
+                                  (6, 64)])
+def test_btd_pcg_iterates_match_the_oracle(nb, N):
+    """After k = 1, 2 and 5 iterations (tol = 0: exactly k) every problem's
+    iterate matches the FP64 oracle's k-th iterate from the same x0 within
+    1e-4 of the problem's largest entry."""
+    batch = 67
+    D, O = _btd_spd(nb, N, batch, 360 + nb + N)
+    r = W.rng(361)
+    b = r.standard_normal(batch * N * nb).astype(np.float32)
+    x0 = r.standard_normal(batch * N * nb).astype(np.float32)
+    for k in ((1,) if N == 1 else (1, 2, 5)):  # one block: M = T, one iteration solves exactly
+        want, wdone = oracle.btd_pcg(nb, N, D.astype(np.float64), O.astype(np.float64), b.astype(np.float64),
+                                     x0.astype(np.float64), k, 0.0, batch)
+        assert (wdone == k).all()
+        for pack in (0, 1):
+            st, X, done = _pcg(nb, N, D, O, b, x0, k, 0.0, batch, pack)
+            assert st == g.GLASS_OK, g.status_string(st)
+            assert (done == k).all(), (nb, N, k, pack)
+            X, Wm = X.reshape(batch, -1), want.reshape(batch, -1)
+            scale = np.abs(Wm).max(1, keepdims=True)
+            assert (np.abs(X - Wm) <= 1e-4 * scale).all(), (nb, N, k, pack, np.max(np.abs(X - Wm) / scale))
+
+
+@pytest.mark.parametrize("nb,N", [(6, 32), (12, 32), (16, 64)])
+def test_btd_pcg_converges_to_the_direct_solution(nb, N):
+    """With a tolerance the loop stops by itself; the result then matches
+    the oracle's direct (dense Cholesky) solve within 1e-4 per problem, and
+    the iteration count is within one of the oracle's PCG at the same
+    tolerance (the last comparison can fall either side in FP32)."""
+    batch = 37
+    D, O = _btd_spd(nb, N, batch, 370 + nb)
+    b = W.rng(371).standard_normal(batch * N * nb).astype(np.float32)
+    x0 = np.zeros_like(b)
+    direct, info = oracle.btd_posv(nb, N, D.astype(np.float64), O.astype(np.float64), b.astype(np.float64), batch)
+    assert (info == 0).all()
+    _, wdone = oracle.btd_pcg(nb, N, D.astype(np.float64), O.astype(np.float64), b.astype(np.float64),
+                              x0.astype(np.float64), 500, 1e-6, batch)
+    st, X, done = _pcg(nb, N, D, O, b, x0, 500, 1e-6, batch)
+    assert st == g.GLASS_OK
+    assert (done > 0).all() and (done < 500).all() and (np.abs(done - wdone) <= 1).all(), (done, wdone)
+    X, Dm = X.reshape(batch, -1), direct.reshape(batch, -1)
+    assert (np.abs(X - Dm) <= 1e-4 * np.abs(Dm).max(1, keepdims=True)).all()
+
+
+def test_btd_pcg_edge_cases():
+    """iters = 0 leaves x; a non-SPD diagonal block gives -1 and leaves x; a
+    short workspace is refused before any launch."""
+    nb, N, batch = 3, 4, 6
+    D, O = _btd_spd(nb, N, batch, 380)
+    b = np.ones(batch * N * nb, np.float32)
+    x0 = W.rng(381).standard_normal(batch * N * nb).astype(np.float32)
+    st, X, done = _pcg(nb, N, D, O, b, x0, 0, 0.0, batch)
+    assert st == g.GLASS_OK and (done == 0).all() and np.array_equal(X, x0)
+    Dm = D.reshape(batch, N, nb, nb)
+    Dm[2, 3] = -np.eye(nb, dtype=np.float32)
+    st, X, done = _pcg(nb, N, D, O, b, x0, 5, 0.0, batch)
+    assert st == g.GLASS_OK and done[2] == -1 and (np.delete(done, 2) == 5).all()
+    assert np.array_equal(X.reshape(batch, -1)[2], x0.reshape(batch, -1)[2])
+    st, _, _ = _pcg(nb, N, D, O, b, x0, 5, 0.0, batch, ws_bytes=g.glass_btd_pcg_workspace(nb, N, batch) - 4)
+    assert st == g.GLASS_ERR_WORKSPACE
