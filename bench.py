@@ -671,7 +671,7 @@ def extra_tc_gemm(peaks, batch=65536):
 
 
 def extra_refine(peaks, batch=16384):
-    """Refined SPD solve: n in {32, 64}, kappa swept 1e1..1e6, one FP64-residual
+    """Refined SPD solve: n in {32, 64}, kappa swept 1e1..1e6 by decades, one FP64-residual
     step; forward error of x0 and x1 against the FP64 solution (numpy/LAPACK)
     of the same FP32-rounded systems on a sample, and time at full batch."""
     import numpy as np
@@ -682,7 +682,7 @@ def extra_refine(peaks, batch=16384):
     out = {}
     sample = 128
     for n in (32, 64):
-        for kappa in (1e1, 1e3, 1e6):
+        for kappa in (1e1, 1e2, 1e3, 1e4, 1e5, 1e6):
             A = W.kappa_spd(n, sample, kappa, 1005)
             b = W.gaussian(n * sample, 1006)
             Am = W.from_colmajor(A, sample, n, n).astype(np.float64)
@@ -704,8 +704,10 @@ def extra_refine(peaks, batch=16384):
                 be = (np.abs(R).max((1, 2)) / (np.abs(Am).sum(2).max(1) * np.abs(Xm).max((1, 2)) +
                                                np.abs(bm).max((1, 2))))[ok]
                 row[f"x{refine}"] = {"fwd_err_median": float(np.median(fwd)) if ok.any() else None,
+                                     "fwd_err_max": float(fwd.max()) if ok.any() else None,
                                      "bwd_err_max": float(be.max()) if ok.any() else None,
-                                     "failed": int((~ok).sum())}
+                                     "failed": int((~ok).sum()),
+                                     "within_1e-4_fwd": int((fwd <= 1e-4).sum())}
             out[f"n{n}_kappa{kappa:.0e}"] = row
     # time at full batch (kappa 1e3 inputs), refined and plain
     for n in (32, 64):
@@ -720,8 +722,8 @@ def extra_refine(peaks, batch=16384):
             for x, y in zip(As, bs):
                 x.copy_(A)
                 y.copy_(b)
-        for refine in (0, 1):
-            o = g.make_opts(refine_steps=refine, fp64_diag=refine)
+        for refine, fp64d in ((0, 0), (1, 1), (1, 0), (0, 1)):
+            o = g.make_opts(refine_steps=refine, fp64_diag=fp64d)
             k = [0]
 
             def fn():
@@ -730,8 +732,8 @@ def extra_refine(peaks, batch=16384):
                 g.glass_batched_posv(n, 1, As[i], n, n * n, bs[i], n, n, info, batch, o)
             ms = _graph_time(fn, sets, setup=setup)
             by = bytes_flops("posv", n, 1)[0] * batch + (4 * n * batch if refine else 0)
-            out[f"time_n{n}_refine{refine}"] = {"us": ms * 1e3, "matrices_per_s": batch / (ms / 1e3),
-                                                "gbs": by / (ms / 1e3) / 1e9}
+            key = f"time_n{n}_refine{refine}" + ("" if fp64d == refine else f"_fp64diag{fp64d}")
+            out[key] = {"us": ms * 1e3, "matrices_per_s": batch / (ms / 1e3), "gbs": by / (ms / 1e3) / 1e9}
     return out
 
 
@@ -886,7 +888,8 @@ def extra_robo(peaks, batches=(4096, 1 << 20)):
                     us = _graph_time(lambda: cell.launch(scope, pack), 16) * 1e3
                     if best is None or us < best[0]:
                         best = (us, pack)
-                per_scope[g.SCOPE_NAMES[scope]] = {"ns_per_problem": best[0] * 1e3 / batch, "pack": best[1]}
+                if best is not None:  # element-wise operations are thread scope only
+                    per_scope[g.SCOPE_NAMES[scope]] = {"ns_per_problem": best[0] * 1e3 / batch, "pack": best[1]}
             us = _graph_time(lambda: cell.launch(), 16) * 1e3
             out[f"{name}:b{batch}"] = {"scopes": per_scope, "table_ns_per_problem": us * 1e3 / batch,
                                        "table_gbs": cell.bytes / (us / 1e6) / 1e9,
@@ -1175,8 +1178,11 @@ def summarize_extras(ex):
     pick("refined_posv", lambda d: {
         **{f"n{n}_refined_over_plain": d[f"time_n{n}_refine1"]["us"] / d[f"time_n{n}_refine0"]["us"]
            for n in (32, 64)},
-        **{k: {"x0_bwd": v["x0"]["bwd_err_max"], "x1_bwd": v["x1"]["bwd_err_max"],
-               "x1_failed": v["x1"]["failed"]} for k, v in d.items() if k.startswith("n64_kappa")}})
+        **{f"n{n}_refined_fp32diag_over_plain": d[f"time_n{n}_refine1_fp64diag0"]["us"] / d[f"time_n{n}_refine0"]["us"]
+           for n in (32, 64)},
+        **{k: {"x0_fwd_med": v["x0"]["fwd_err_median"], "x1_fwd_med": v["x1"]["fwd_err_median"],
+               "x1_bwd_max": v["x1"]["bwd_err_max"], "x1_failed": v["x1"]["failed"]}
+           for k, v in d.items() if k.startswith("n64_kappa")}})
     pick("learned_placement", lambda d: {k: {"median_regret": round(d[k]["median"], 4), "p90_regret": round(d[k]["p90"], 4)}
                                          for k in ("learned", "nearest_grid_table", "fixed_placement")})
     return out

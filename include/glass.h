@@ -111,7 +111,7 @@ typedef struct {
     int layout;       /* glass_layout */
     glass_placement placement;
     int refine_steps; /* posv only: iterative-refinement steps (0 or 1) */
-    int fp64_diag;    /* Cholesky: FP64 sqrt/reciprocal of the diagonal */
+    int fp64_diag;    /* Cholesky: diagonal sqrt/reciprocal to FP64 accuracy */
     int use_learned;  /* auto placement: consult the learned cost model for
                          shapes outside the measured grid */
 } glass_opts;
@@ -158,8 +158,11 @@ glass_status glass_batched_potrs(int n, int nrhs, const void *L, int lda, long l
  * With opts->refine_steps == 1 the residual r = b - A x0 is formed in FP64
  * from the original A (re-read before L is written back) and one correction
  * dx = solve(L, r) is added, x1 = x0 + dx, for every right-hand side;
- * opts->fp64_diag computes the diagonal square roots and reciprocals in
- * FP64.  nrhs == 0 factors only. */
+ * opts->fp64_diag computes the diagonal square roots and reciprocals to
+ * FP64 accuracy, each rounded once to FP32 (the square root is the FP32 one,
+ * which equals the rounded FP64 square root; the reciprocal is corrected by
+ * its exact FP32 remainders, so GB300's narrow FP64 pipe is not needed).
+ * nrhs == 0 factors only. */
 glass_status glass_batched_posv(int n, int nrhs, void *A, int lda, long long sA,
                                 void *B, int ldb, long long sB, int *info,
                                 int batch, const glass_opts *opts, glass_stream_t stream);
@@ -353,7 +356,7 @@ int glass_riccati_feasible(int nx, int nu, glass_placement p);
 /* ------------------------------------------------- robotics operations */
 
 /* The robotics operations of the paper's placement table (Sec. IV-E,
- * Table II), each at thread, warp or block scope.  Conventions (the paper
+ * Table II).  Conventions (the paper
  * requires an operation's interface to fix them, Sec. III-B):
  *  - quaternion q = (w, x, y, z), Hamilton product, unit norm expected;
  *  - rotation vector d: angle |d| about d / |d|, Exp(d) = (cos |d|/2,
@@ -377,11 +380,12 @@ int glass_riccati_feasible(int nx, int nu, glass_placement p);
  * (q: 4, d: 3, T: 16, xi: 6, v/m: 6, 3x3: 9, eigen/singular values: 3);
  * quaternion and transform arrays must be 16-byte aligned.  argmax and
  * softmax read x[b*sx + i], i < n, and write idx[b] / y[b*sy + i].
- * Placement: scope thread (one problem per thread, 32*pack per CTA), warp
- * (one problem per warp) or block (a 64-thread team, pack <= 4); auto
- * resolves from the measured table.  The element-wise operations run on the
- * first thread of a warp or block team; argmax and softmax spread the n
- * values over the team. */
+ * Placement: scope thread (one problem per thread, 32*pack per CTA); argmax
+ * and softmax also warp (one problem per warp) or block (a 64-thread team,
+ * pack <= 4), the n values spread over the team; auto resolves from the
+ * measured table.  The seven element-wise operations accept thread scope
+ * only (a warp or block placement returns GLASS_ERR_INVALID_VALUE): a
+ * problem is a short serial chain with nothing for a team to share. */
 typedef enum {
     GLASS_ROBO_QUAT_RETRACT = 0,
     GLASS_ROBO_QUAT_ERROR = 1,

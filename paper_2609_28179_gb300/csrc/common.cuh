@@ -203,16 +203,44 @@ __device__ __forceinline__ void stage_out(const float *sm, int S, const Mat &M, 
 }
 
 // Diagonal square root and reciprocal of a Cholesky pivot d > 0, in FP32 or
-// (fp64 == true) in FP64 rounded once to FP32.
+// (fp64 == true) to FP64 accuracy rounded once to FP32 -- the values an FP64
+// square root and division give, without FP64 operations, which GB300's
+// narrow FP64 pipe makes costly (every lane would issue them per column):
+//  - the FP64 square root rounded to FP32 is sqrtf(d) itself (a 53-bit
+//    square root rounds to the correctly rounded 24-bit one, 53 >= 2*24+2);
+//  - 1/sqrt(d) = (1/l)(1 + t)^(-1/2) with t = (d - l^2)/l^2, and 1/l =
+//    r0 / (1 - eps) with eps = 1 - l r0, r0 the rounded reciprocal; both
+//    remainders are exact in FP32 by one fused multiply-add (Markstein), so
+//    1/sqrt(d) = r0 (1 + eps - t/2) up to terms of order 2^-46, formed as
+//    r0 + r0 (eps - t/2) and rounded once: the FP64 result except within
+//    about 2^-46 of a rounding boundary.
 __device__ __forceinline__ void chol_diag(float d, bool fp64, float &l, float &r) {
+    l = sqrtf(d);
+    const float r0 = __frcp_rn(l);  // the correctly rounded 1 / l
     if (fp64) {
-        const double s = sqrt((double)d);
-        l = (float)s;
-        r = (float)(1.0 / s);
+        const float e = fmaf(-l, l, d);       // d - l^2, exact
+        const float eps = fmaf(-l, r0, 1.0f);  // 1 - l r0, exact
+        const float t = e * r0 * r0;           // (d - l^2) / l^2, |t| < 2^-22
+        r = fmaf(r0, fmaf(-0.5f, t, eps), r0);
     } else {
-        l = sqrtf(d);
-        r = __frcp_rn(l);  // the correctly rounded 1 / l
+        r = r0;
     }
+}
+
+// FP32 -> FP64 conversion on the integer pipe, without branches: for a
+// normal value the sign moves to bit 63, the 8-bit exponent is rebiased from
+// 127 to 1023 and the 23-bit fraction becomes the top of the 52-bit one
+// (exact); zeros keep their sign, infinities and NaNs (payload included)
+// stay infinities and NaNs, subnormals become zero of the same sign (an
+// absolute change below 2^-126).  On GB300 the FP64 pipe is narrow, and the
+// hardware conversion would occupy it as much as the fused multiply-add
+// that uses the value.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e8 = (u >> 23) & 0xffu;
+    const unsigned e11 = e8 == 0u ? 0u : (e8 == 0xffu ? 0x7ffu : e8 + 896u);
+    const unsigned m = e8 == 0u ? 0u : (u & 0x7fffffu);
+    return __hiloint2double((int)((u & 0x80000000u) | (e11 << 20) | (m >> 3)), (int)(m << 29));
 }
 
 // ------------------------------------------------------- launch helpers

@@ -358,5 +358,59 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
     }
 }
 
+// K right-hand sides at once (x[k][q] = row lane + 32q of column k), the
+// same sweeps as potrs with the K independent chains interleaved step by
+// step: K shuffles and K fused multiply-adds per slot and step, so the
+// latency of one shuffle-and-update chain is shared by K solves.
+template <int NMAX, int K>
+__device__ __forceinline__ void potrs_k(const float *As, const float *dv, float (&x)[K][Shape<NMAX>::R], int n) {
+    static_assert(NMAX == 32 || NMAX == 64, "orders 17..32 or 33..64");
+    constexpr int LD = Shape<NMAX>::LD;
+    constexpr int R = Shape<NMAX>::R;
+    const int lane = threadIdx.x & 31;
+    // forward: x <- L^{-1} x down the columns of L
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        if (i < n) {
+            const int qi = i / 32, li = i % 32;
+            const float d = dv[i];
+            float c[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) c[q] = As[i * LD + lane + 32 * q];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float yi = __shfl_sync(GLASS_FULL_MASK, x[k][qi], li) * d;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int row = lane + 32 * q;
+                    if (row == i) x[k][q] = yi;
+                    else if (row > i) x[k][q] = fmaf(-c[q], yi, x[k][q]);  // rows >= n: zero factor rows
+                }
+            }
+        }
+    }
+    // backward: x <- L^{-T} x down the columns of the mirrored upper triangle
+#pragma unroll
+    for (int i = NMAX - 1; i >= 0; --i) {
+        if (i < n) {
+            const int qi = i / 32, li = i % 32;
+            const float d = dv[i];
+            float c[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) c[q] = As[i * LD + lane + 32 * q];  // l_{i,row} for row < i
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float xi = __shfl_sync(GLASS_FULL_MASK, x[k][qi], li) * d;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int row = lane + 32 * q;
+                    if (row == i) x[k][q] = xi;
+                    else if (row < i) x[k][q] = fmaf(-c[q], xi, x[k][q]);
+                }
+            }
+        }
+    }
+}
+
 }  // namespace tcwarp
 }  // namespace glass

@@ -233,10 +233,59 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
 }
 
 // Per-warp shared memory (floats) of k_chol_tc: A, 1/l_jj, two 16-float
-// broadcast segments.
-template <int NMAX>
+// broadcast segments, and (RF) the first solution of the refinement step as
+// NMAX doubles.
+template <int NMAX, bool RF = false>
 constexpr int tc_floats() {
-    return NMAX * tcwarp::Shape<NMAX>::LD + NMAX + 32;
+    return NMAX * tcwarp::Shape<NMAX>::LD + NMAX + 32 + (RF ? 2 * NMAX : 0);
+}
+
+// r = b - A x in FP64 for one right-hand side of the tensor-core posv: A
+// the ORIGINAL symmetric operand in global memory (lower triangle, still
+// intact: the factor is written back last), x widened to FP64 in shared
+// memory (xd, NMAX doubles, zero beyond n), lane rows i = lane + 32 q.  One
+// step per column k, every lane busy: a_ik is read from column k below its
+// diagonal (coalesced over the lanes) or, above it, as a_ki from the row's
+// own column; x_k is a shared-memory broadcast.  The FP64 pipe does n fused
+// multiply-adds per row (two partial sums each) and, in the 64-row kernel,
+// the widening of A's entries (the 32-row kernel widens them on the integer
+// pipe, f2d_bits).
+template <int NMAX>
+__device__ __forceinline__ void residual_f64(const float *ga, long long lda, const double *xd,
+                                             const float (&bq)[tcwarp::Shape<NMAX>::R], int n,
+                                             float (&r)[tcwarp::Shape<NMAX>::R]) {
+    constexpr int R = tcwarp::Shape<NMAX>::R;
+    const int lane = threadIdx.x & 31;
+    double acc[R][2];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        acc[q][0] = (double)bq[q];
+        acc[q][1] = 0.0;
+    }
+    // Widening on the integer pipe measured faster for the 32-row kernel
+    // (refined solve at batch 16384: 128 vs 155 us) and slower for the
+    // 64-row one (731 vs 605 us), which keeps the hardware conversion.
+    auto widen = [](float a) { return NMAX == 32 ? f2d_bits(a) : (double)a; };
+    auto step = [&](int k, int s) {
+        const double xk = xd[k];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = lane + 32 * q;
+            if (i < n) {
+                const float aik = i >= k ? ga[(long long)k * lda + i] : ga[(long long)i * lda + k];
+                acc[q][s] = fma(-widen(aik), xk, acc[q][s]);
+            }
+        }
+    };
+    int k = 0;
+#pragma unroll 4
+    for (; k + 1 < n; k += 2) {
+        step(k, 0);
+        step(k + 1, 1);
+    }
+    if (k < n) step(k, 0);
+#pragma unroll
+    for (int q = 0; q < R; ++q) r[q] = (float)(acc[q][0] + acc[q][1]);
 }
 
 // Warp scope, orders 17..64: blocked Cholesky with tensor-core trailing
@@ -252,9 +301,10 @@ __global__ void __launch_bounds__(256, 1) k_chol_tc(int n, int nrhs, Mat A, Mat 
     constexpr int R = tcwarp::Shape<NMAX>::R;
     extern __shared__ __align__(16) float smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *As = smem + w * tc_floats<NMAX>();
+    float *As = smem + w * tc_floats<NMAX, RF>();
     float *dv = As + NMAX * LD;
     float *bc = dv + NMAX;
+    double *xd = reinterpret_cast<double *>(bc + 32);  // NMAX doubles (RF), 16-byte aligned
     const int b = blockIdx.x * (blockDim.x >> 5) + w;
     if (b >= batch) return;  // whole warp
     tcwarp::stage<NMAX, true>(As, A.p + (long long)b * A.s, A.ld, n);
@@ -268,36 +318,17 @@ __global__ void __launch_bounds__(256, 1) k_chol_tc(int n, int nrhs, Mat A, Mat 
                 const int i = lane + 32 * q;
                 x[q] = (i < n) ? B.cget(b, i, c) : 0.f;
             }
+            float bq[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) bq[q] = x[q];
             tcwarp::potrs<NMAX>(As, dv, x, n);
             if constexpr (RF) {
-                const float *ga = A.p + (long long)b * A.s;
-                double acc[R][2];  // two partial sums per row hide the FP64 latency
 #pragma unroll
-                for (int q = 0; q < R; ++q) {
-                    const int i = lane + 32 * q;
-                    acc[q][0] = (i < n) ? (double)B.cget(b, i, c) : 0.0;
-                    acc[q][1] = 0.0;
-                }
-#pragma unroll 2
-                for (int k = 0; k < n; ++k) {
-                    float xk = 0.f;
-#pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        const float v = __shfl_sync(GLASS_FULL_MASK, x[q], k & 31);
-                        if ((k >> 5) == q) xk = v;
-                    }
-#pragma unroll
-                    for (int q = 0; q < R; ++q) {
-                        const int i = lane + 32 * q;
-                        if (i < n) {  // the lower triangle holds a_ik = a_ki
-                            const float aik = i >= k ? ga[(long long)k * A.ld + i] : ga[(long long)i * A.ld + k];
-                            acc[q][k & 1] = fma(-(double)aik, (double)xk, acc[q][k & 1]);
-                        }
-                    }
-                }
+                for (int q = 0; q < R; ++q) xd[lane + 32 * q] = (double)x[q];  // rows >= n hold 0
+                __syncwarp();
                 float r[R];
-#pragma unroll
-                for (int q = 0; q < R; ++q) r[q] = (float)(acc[q][0] + acc[q][1]);
+                residual_f64<NMAX>(A.p + (long long)b * A.s, A.ld, xd, bq, n, r);
+                __syncwarp();  // xd is rewritten for the next right-hand side
                 tcwarp::potrs<NMAX>(As, dv, r, n);
 #pragma unroll
                 for (int q = 0; q < R; ++q) x[q] += r[q];
@@ -552,7 +583,10 @@ cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *in
 }
 
 // Shared memory of the blocked tensor-core Cholesky, per warp (bytes).
-inline size_t tc_smem(int n) { return (size_t)(n > 32 ? tc_floats<64>() : tc_floats<32>()) * 4; }
+inline size_t tc_smem(int n, bool rf = false) {
+    return (size_t)(n > 32 ? (rf ? tc_floats<64, true>() : tc_floats<64>())
+                           : (rf ? tc_floats<32, true>() : tc_floats<32>())) * 4;
+}
 
 // Shared memory of the many-right-hand-side solve kernels, per problem
 // (bytes), for a team of T threads: column-per-thread up to order 32,
@@ -601,9 +635,9 @@ cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info
             if (n > 16) {
                 const int grid = ceil_div(batch, pack);
                 if (n > 32)
-                    return launch_k(k_chol_tc<OP, 64, RF>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B,
+                    return launch_k(k_chol_tc<OP, 64, RF>, grid, 32 * pack, tc_smem(n, RF) * pack, st, n, nrhs, A, B,
                                     info, batch, fp64diag);
-                return launch_k(k_chol_tc<OP, 32, RF>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info,
+                return launch_k(k_chol_tc<OP, 32, RF>, grid, 32 * pack, tc_smem(n, RF) * pack, st, n, nrhs, A, B, info,
                                 batch, fp64diag);
             }
         }
@@ -661,7 +695,7 @@ size_t smem_of(int n, int nrhs, Placement pl, int refine) {
             return (size_t)32 * pl.pack * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4;
         case SCOPE_WARP: {
             if (OP == C_TRSM) return solve_cols_per(n, nrhs, 32) * pl.pack;
-            if (has_factor(OP) && n > 16) return tc_smem(n) * pl.pack;
+            if (has_factor(OP) && n > 16) return tc_smem(n, refine != 0) * pl.pack;
             const int N = nmax_bucket(n);
             return (size_t)pl.pack * (N + (refine ? N * (N + 1) : 0)) * 4;
         }

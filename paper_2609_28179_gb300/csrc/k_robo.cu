@@ -8,11 +8,13 @@
 // Hamilton product; rotation vectors; twists and motion vectors with the
 // linear part first; right perturbations; 4x4 and 3x3 matrices column-major.
 //
-// Thread scope computes one problem per thread (32*pack per CTA); warp and
-// block scope give each problem a warp or a 64-thread team.  The
-// element-wise operations run on the team's first lane (the placement the
-// table measures against), argmax and softmax spread the n elements over the
-// team and reduce with shuffles (and shared memory across warps).
+// Thread scope computes one problem per thread (32*pack per CTA).  argmax
+// and softmax also run at warp and block scope, the n elements of a problem
+// spread over a warp or a 64-thread team and reduced with shuffles (and
+// shared memory across warps).  The element-wise operations are thread scope
+// only: one problem is a short serial chain of dependent arithmetic with
+// nothing for a team to share, so a team placement would leave all but one
+// lane idle.
 #include <math.h>
 
 #include "common.cuh"
@@ -361,11 +363,10 @@ struct ClosestRotation {
     }
 };
 
-template <int T, class Op>
+template <class Op>
 __global__ void __launch_bounds__(256) k_elementwise(Op op, int batch) {
-    const int team = threadIdx.x / T, rank = threadIdx.x % T;
-    const long long b = (long long)blockIdx.x * (blockDim.x / T) + team;
-    if (b >= batch || rank != 0) return;
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
     op(b);
 }
 
@@ -444,14 +445,8 @@ __global__ void __launch_bounds__(256) k_softmax(int n, const float *x, long lon
 
 template <class Op>
 cudaError_t launch_elementwise(Op op, int batch, Placement pl, cudaStream_t st) {
-    if (pl.scope == SCOPE_THREAD) {
-        const int th = 32 * pl.pack;
-        k_elementwise<1, Op><<<ceil_div(batch, th), th, 0, st>>>(op, batch);
-    } else if (pl.scope == SCOPE_WARP) {
-        k_elementwise<32, Op><<<ceil_div(batch, pl.pack), 32 * pl.pack, 0, st>>>(op, batch);
-    } else {
-        k_elementwise<64, Op><<<ceil_div(batch, pl.pack), 64 * pl.pack, 0, st>>>(op, batch);
-    }
+    const int th = 32 * pl.pack;  // thread scope: one problem per thread
+    k_elementwise<Op><<<ceil_div(batch, th), th, 0, st>>>(op, batch);
     return cudaPeekAtLastError();
 }
 
@@ -462,7 +457,7 @@ bool feasible_robo(int op, int n, Placement pl) {
     if (pl.scope == SCOPE_BLOCK && pl.pack > 4) return false;
     if (pl.scope < SCOPE_THREAD || pl.scope > SCOPE_BLOCK) return false;
     if (op == ROBO_ARGMAX || op == ROBO_SOFTMAX) return n >= 1;
-    return true;
+    return pl.scope == SCOPE_THREAD;  // element-wise: nothing for a team to share
 }
 
 cudaError_t launch_robo(int op, int n, const float *a, const float *b, long long sa, float *o1, float *o2, float *o3,

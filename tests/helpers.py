@@ -48,3 +48,19 @@ def backward_error(A, X, B):
     nX = np.abs(X).sum(-1).max(-1)
     nB = np.abs(B).sum(-1).max(-1)
     return num / (nA * nX + nB)
+
+
+def per_problem_rel(got, want, batch, mask=None):
+    """Largest over the batch of the per-problem error max|got - want| /
+    max|want| (flat column-major arrays with equal per-problem sizes; mask
+    selects entries within a problem)."""
+    g_ = np.asarray(got, np.float64).reshape(batch, -1)
+    w_ = np.asarray(want, np.float64).reshape(batch, -1)
+    if mask is not None:
+        g_, w_ = g_[:, mask], w_[:, mask]
+    return float((np.abs(g_ - w_).max(1) / np.maximum(np.abs(w_).max(1), 1e-300)).max())
+
+
+def lower_mask(n):
+    """Entries of a column-major n x n matrix on or below the diagonal."""
+    return np.tril(np.ones((n, n), dtype=bool)).T.reshape(-1)

@@ -5,8 +5,10 @@ several tiles with ragged tails.  Bars:
   - integer / index results (pivots, info) bit-exact;
   - exact-arithmetic inputs (integer / dyadic constructions) bit-exact;
   - FP32 results: solves within 1e-4 normwise backward error (the stated
-    relative-residual bar) and elementwise within 1e-4 of the oracle scaled
-    by the result's magnitude (the inputs are well conditioned, kappa < 1e2);
+    relative-residual bar) and, problem by problem, within 1e-4 of the
+    oracle scaled by that problem's largest entry (the inputs are well
+    conditioned, kappa < 1e2); LU factors also within the rounding-error
+    bound of the factorization itself, entry by entry;
   - GEMM elementwise within the classical bound k * 2^-23 * (|A||B|)_ij.
 """
 import numpy as np
@@ -15,7 +17,8 @@ import pytest
 import oracle
 import paper_2609_28179_gb300 as g
 from paper_2609_28179_gb300 import workloads as W
-from tests.helpers import U32, backward_error, dev, host, opts_for, placements, sync, to_dev, zeros_i32
+from tests.helpers import (U32, backward_error, dev, host, lower_mask, opts_for, per_problem_rel, placements, sync,
+                           to_dev, zeros_i32)
 
 pytestmark = pytest.mark.gpu
 
@@ -115,9 +118,8 @@ def test_posv_all_placements(n, nrhs):
         X = host(dB).astype(np.float64)
         L = host(dA).astype(np.float64)
         tag = (n, nrhs, scope, pack)
-        assert np.abs(X - X_ref).max() <= 1e-4 * np.abs(X_ref).max(), tag
-        Lm, Lr = np.tril(mats(L, batch, n, n)), np.tril(mats(L_ref, batch, n, n))
-        assert np.abs(Lm - Lr).max() <= 1e-4 * np.abs(Lr).max(), tag
+        assert per_problem_rel(X, X_ref, batch) <= 1e-4, tag
+        assert per_problem_rel(L, L_ref, batch, lower_mask(n)) <= 1e-4, tag
         # upper triangle left as it was
         up = np.triu_indices(n, 1)
         assert np.array_equal(mats(L, batch, n, n)[:, up[0], up[1]], Am[:, up[0], up[1]]), tag
@@ -174,7 +176,7 @@ def test_trsm_square_rhs_all_placements(n):
         g.check(g.glass_batched_trsm(n, k, to_dev(Lcm), n, n * n, dB, n, n * k, batch, opts_for(scope, pack)))
         sync()
         X = host(dB).astype(np.float64)
-        assert np.abs(X - ref).max() <= 1e-4 * np.abs(ref).max(), (n, scope, pack)
+        assert per_problem_rel(X, ref, batch) <= 1e-4, (n, scope, pack)
 
 
 @pytest.mark.parametrize("n", [4, 17, 64])
@@ -232,9 +234,17 @@ def test_getrf_getrs_all_placements(n):
         assert (host(info)[:batch] == 0).all(), tag
         assert np.array_equal(host(ipiv)[:batch * n], piv_ref), tag
         LU = host(dA).astype(np.float64)
-        assert np.abs(LU - LU_ref).max() <= 1e-4 * np.abs(LU_ref).max() * max(1, n / 8), tag
-        X = host(dB).astype(np.float64)
+        assert per_problem_rel(LU, LU_ref, batch) <= 1e-4, tag
+        # the factorization's own rounding-error bound (Higham, Thm. 9.3):
+        # |P A - L U| <= gamma |L||U| entry by entry, with gamma = (2n + 16) u
+        # covering FP32 accumulation and the 3xTF32 products of the
+        # tensor-core updates (each within 12 u of exact)
+        Lf = np.tril(mats(LU, batch, n, n), -1) + np.eye(n)
+        Uf = np.triu(mats(LU, batch, n, n))
         Am = mats(A, batch, n, n).astype(np.float64)
+        PA = np.stack([Am[b][_perm_from_ipiv(piv_ref[b * n:(b + 1) * n], n)] for b in range(batch)])
+        assert (np.abs(PA - Lf @ Uf) <= (2 * n + 16) * U32 * (np.abs(Lf) @ np.abs(Uf)) + 1e-30).all(), tag
+        X = host(dB).astype(np.float64)
         assert backward_error(Am, mats(X, batch, n, 2), mats(B, batch, n, 2).astype(np.float64)).max() <= 1e-4, tag
 
 
@@ -288,7 +298,9 @@ def test_rot3_compose_all_placements(chain):
         g.check(g.glass_batched_rot3_compose(chain, to_dev(Rs), 9 * chain, dR, 9, batch, opts_for(scope, pack)))
         sync()
         R = host(dR).astype(np.float64)
-        assert np.abs(R - ref).max() <= 1e-5 * max(1, chain / 8), (chain, scope, pack)
+        # each 3x3 product of unit-scale rotations adds at most ~9u per entry
+        # (three-term dot products whose |terms| sum to <= 3), inputs carry u
+        assert np.abs(R - ref).max() <= 12 * (chain + 1) * U32, (chain, scope, pack)
         Rm = mats(R, batch, 3, 3)
         assert np.abs(np.transpose(Rm, (0, 2, 1)) @ Rm - np.eye(3)).max() < 1e-4
 
@@ -309,7 +321,7 @@ def test_se3_apply_all_placements(chain, npts):
                                           batch, opts_for(scope, pack)))
         sync()
         Q = host(dQ).astype(np.float64)
-        assert np.abs(Q - ref).max() <= 1e-5 * max(1, chain / 4) * np.abs(ref).max(), (chain, npts, scope, pack)
+        assert per_problem_rel(Q, ref, batch) <= 12 * (chain + 2) * U32, (chain, npts, scope, pack)
 
 
 def test_se3_apply_unaligned_points_take_the_scalar_path():
@@ -328,7 +340,7 @@ def test_se3_apply_unaligned_points_take_the_scalar_path():
                                           batch, opts_for(scope, pack)))
         sync()
         Q = bufQ[1:].cpu().numpy().astype(np.float64)
-        assert np.abs(Q - ref).max() <= 1e-5 * max(1, chain / 4) * np.abs(ref).max(), (scope, pack)
+        assert per_problem_rel(Q, ref, batch) <= 12 * (chain + 2) * U32, (scope, pack)
 
 
 # ---------------------------------------------------------------- layouts
@@ -356,6 +368,5 @@ def test_interleaved_layout_posv_and_roundtrip(n):
     g.check(g.glass_from_interleaved32(n, 1, iB, oB, batch))
     sync()
     X = host(oB).astype(np.float64)
-    assert np.abs(X - X_ref).max() <= 1e-4 * np.abs(X_ref).max()
-    L = np.tril(mats(host(oA), batch, n, n))
-    assert np.abs(L - np.tril(mats(L_ref, batch, n, n))).max() <= 1e-4 * np.abs(L_ref).max()
+    assert per_problem_rel(X, X_ref, batch) <= 1e-4
+    assert per_problem_rel(host(oA), L_ref, batch, lower_mask(n)) <= 1e-4

@@ -11,7 +11,11 @@ from paper_2609_28179_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 BATCH = 333   # ragged against every CTA size
-PLACEMENTS = [(s, p) for s in (0, 1, 2) for p in (1, 2, 4, 8) if not (s == 2 and p == 8)]
+# argmax and softmax spread a problem over a warp or a 64-thread team; the
+# element-wise operations (one problem's arithmetic is a short serial chain)
+# are served at thread scope only
+PLACEMENTS_TEAM = [(s, p) for s in (0, 1, 2) for p in (1, 2, 4, 8) if not (s == 2 and p == 8)]
+PLACEMENTS = [(0, p) for p in (1, 2, 4, 8)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -183,7 +187,7 @@ def test_argmax_and_softmax(n):
     sx = n + 3
     idx_ref = oracle.argmax(n, x.astype(np.float64), BATCH, sx=sx)
     sm_ref = oracle.softmax(n, x.astype(np.float64), BATCH, sx=sx).reshape(BATCH, n)
-    for s, p in PLACEMENTS:
+    for s, p in PLACEMENTS_TEAM:
         idx = _empty(BATCH, "int")
         g.check(g.glass_batched_argmax(n, _dev(x), sx, idx, BATCH, _opts(s, p)), f"argmax {s}x{p}")
         assert np.array_equal(_host(idx), idx_ref), (n, s, p)
@@ -192,3 +196,16 @@ def test_argmax_and_softmax(n):
         got = _host(y).reshape(BATCH, n + 1)
         assert np.abs(got[:, :n] - sm_ref).max() <= 2e-6 * max(1, n / 16), (n, s, p)
         assert np.isnan(got[:, n]).all()                   # gap untouched
+
+
+def test_element_wise_operations_refuse_team_placements():
+    """A warp or block placement would run an element-wise operation's short
+    serial chain on one lane of the team: such placements are not offered."""
+    for op in range(7):
+        for s, p in [(1, 1), (1, 4), (2, 1), (2, 4)]:
+            assert not g.glass_robo_feasible(op, 1, s, p)
+        assert g.glass_robo_feasible(op, 1, 0, 1)
+    for op in (7, 8):
+        assert g.glass_robo_feasible(op, 16, 1, 1) and g.glass_robo_feasible(op, 16, 2, 4)
+    q = _dev(W.unit_quaternions(8, 5))
+    assert g.glass_batched_quat_retract(q, _dev(np.zeros(24)), _empty(32), 8, _opts(1, 1)) == g.GLASS_ERR_INVALID_VALUE
