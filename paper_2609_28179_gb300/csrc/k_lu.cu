@@ -1,7 +1,7 @@
 // k_lu.cu -- batched getrf + getrs (partial pivoting) at thread, warp and
 // block scope.  Thread scope stages 32*pack problems through shared memory;
 // warp scope loads rows straight into registers (one per lane) up to order
-// 32 and runs the blocked tensor-core factorization (dev_lu_tc.cuh) on the
+// 16 and runs the blocked tensor-core factorization (dev_lu_tc.cuh) on the
 // problem in shared memory above that; block scope is a 64-thread row team
 // (dev_rows.cuh), one row per thread.
 #include "dev_lu.cuh"

@@ -217,17 +217,19 @@ def _separated_general(n, batch, seed, gap=1e-3):
 
 
 @pytest.mark.parametrize("n", NS)
-def test_getrf_getrs_all_placements(n):
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_getrf_getrs_all_placements(n, nrhs):
     batch = 200
     A = _separated_general(n, batch, 900 + 10 * n)
-    B = W.gaussian(batch * n * 2, 901 + n)
-    LU_ref, piv_ref, X_ref, info_ref = oracle.getrf_getrs(n, 2, A.astype(np.float64), B.astype(np.float64), batch)
+    B = W.gaussian(batch * n * nrhs, 901 + n)
+    LU_ref, piv_ref, X_ref, info_ref = oracle.getrf_getrs(n, nrhs, A.astype(np.float64), B.astype(np.float64),
+                                                          batch)
     _, piv32, _, _ = oracle.getrf(n, A, batch, precision="f32")
     assert np.array_equal(piv32, piv_ref)
-    for scope, pack in placements(g.GLASS_OP_GETRF_GETRS, n, 2):
+    for scope, pack in placements(g.GLASS_OP_GETRF_GETRS, n, nrhs):
         dA, dB = to_dev(A), to_dev(B)
         ipiv, info = zeros_i32(batch * n), zeros_i32(batch)
-        g.check(g.glass_batched_getrf_getrs(n, 2, dA, n, n * n, ipiv, dB, n, 2 * n, info, batch,
+        g.check(g.glass_batched_getrf_getrs(n, nrhs, dA, n, n * n, ipiv, dB, n, nrhs * n, info, batch,
                                             opts_for(scope, pack)), f"lu {n} {scope} {pack}")
         sync()
         tag = (n, scope, pack)
@@ -245,7 +247,7 @@ def test_getrf_getrs_all_placements(n):
         PA = np.stack([Am[b][_perm_from_ipiv(piv_ref[b * n:(b + 1) * n], n)] for b in range(batch)])
         assert (np.abs(PA - Lf @ Uf) <= (2 * n + 16) * U32 * (np.abs(Lf) @ np.abs(Uf)) + 1e-30).all(), tag
         X = host(dB).astype(np.float64)
-        assert backward_error(Am, mats(X, batch, n, 2), mats(B, batch, n, 2).astype(np.float64)).max() <= 1e-4, tag
+        assert backward_error(Am, mats(X, batch, n, nrhs), mats(B, batch, n, nrhs).astype(np.float64)).max() <= 1e-4, tag
 
 
 @pytest.mark.parametrize("n", [2, 6, 12, 24, 64])
