@@ -428,10 +428,13 @@ def cpu_baseline(hosts, ops_sizes, batch, budget_s=12.0, gpu=None):
             cnt = min(s, got["count"])
             e, piv = cell_errors(op, n, got, ref, s, cnt)
             errs[label].append((e, piv, cnt))
+    sizes = [int(t.split(":")[1]) for t in samples]
     return {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
             "value_1core": len(ops_sizes) * batch / one_time,
-            "sample": f"per cell an adaptive prefix of the {batch} problems ({', '.join(samples)}), "
-                      f"scaled to the full batch; value_1core: the same samples on one core"}, errs
+            "sample": f"per cell an adaptive prefix of its {batch} problems ({min(sizes)}..{max(sizes)} problems, "
+                      f"about {budget_s / max(1, len(ops_sizes)):.2f} s of oracle work each; per-cell sizes in the "
+                      f"detail file), scaled to the full batch; value_1core: the same samples on one core",
+            "per_cell_sample": samples}, errs
 
 
 # ------------------------------------------------------------- reference
@@ -1113,6 +1116,7 @@ def main():
         outs = {lab: [gpu_outputs(c, pl, CHECK_PROBLEMS) for c, pl in zip(cells, pls)]
                 for lab, pls in (("tuned", tuned), ("plain", plain))}
         cb, errs = cpu_baseline([c.host for c in cells], [(c.op, c.n) for c in cells], args.batch, gpu=outs)
+        detail["cpu_baseline_samples"] = cb.pop("per_cell_sample")
         line["cpu_baseline"] = cb
         for lab, es in errs.items():
             for r, (e, piv, cnt) in zip(rows, es):

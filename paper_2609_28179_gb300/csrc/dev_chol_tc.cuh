@@ -49,38 +49,59 @@ struct Shape {
 };
 
 // Stage the column-major n x n operand at ga (leading dimension lda) into As
-// (pitch LD, a multiple of 4) with cp.async copies, every copy of the lane in flight at once:
-// 16-byte copies when n and lda are multiples of 4 and ga is 16-byte aligned,
-// 4-byte copies otherwise.  Everything outside the operand is zero; LOWER
-// skips what lies above the diagonal (16-byte groups wholly above it in the
-// vector form) and leaves it zero or as read -- it is never used.  Ends with
-// the copies complete and visible to the warp.
+// (pitch LD, a multiple of 4) with cp.async copies, every copy of the lane
+// in flight at once: 16-byte copies when n and lda are multiples of 4 and ga
+// is 16-byte aligned, 4-byte copies otherwise.  Everything outside the
+// operand is zero; LOWER skips what lies above the diagonal (16-byte groups
+// wholly above it in the vector form) and leaves it zero or as read -- it is
+// never used.  The copies form two groups, columns 0..15 first, so that a
+// factorization can start on its first panel while the rest arrives: after
+// stage_async, wait_first() makes columns 0..15 complete and visible to the
+// warp, wait_all() everything.
 template <int NMAX, bool LOWER, int LD = Shape<NMAX>::LD>
-__device__ __forceinline__ void stage(float *As, const float *ga, long long lda, int n) {
+__device__ __forceinline__ void stage_async(float *As, const float *ga, long long lda, int n) {
     constexpr int R = Shape<NMAX>::R;
     const int lane = threadIdx.x & 31;
     const bool vec = (n & 3) == 0 && (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(ga) & 15) == 0;
-    if (vec) {
+    auto columns = [&](int k0, int k1) {
+        if (vec) {
 #pragma unroll 4
-        for (int e = lane; e < NMAX * NMAX / 4; e += 32) {
-            const int k = e / (NMAX / 4), r = 4 * (e % (NMAX / 4));
-            float *d = As + k * LD + r;
-            if (k < n && r < n && (!LOWER || r + 3 >= k)) cp_async16(d, ga + (long long)k * lda + r);
-            else *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    } else {
-#pragma unroll 4
-        for (int k = 0; k < NMAX; ++k)
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const int i = lane + 32 * q;
-                float *d = As + k * LD + i;
-                if (k < n && i < n && (!LOWER || i >= k)) cp_async4(d, ga + (long long)k * lda + i);
-                else *d = 0.f;
+            for (int e = k0 * (NMAX / 4) + lane; e < k1 * (NMAX / 4); e += 32) {
+                const int k = e / (NMAX / 4), r = 4 * (e % (NMAX / 4));
+                float *d = As + k * LD + r;
+                if (k < n && r < n && (!LOWER || r + 3 >= k)) cp_async16(d, ga + (long long)k * lda + r);
+                else *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-    }
-    cp_async_wait_all();
+        } else {
+#pragma unroll 4
+            for (int k = k0; k < k1; ++k)
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int i = lane + 32 * q;
+                    float *d = As + k * LD + i;
+                    if (k < n && i < n && (!LOWER || i >= k)) cp_async4(d, ga + (long long)k * lda + i);
+                    else *d = 0.f;
+                }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    columns(0, 16);
+    columns(16, NMAX);
+}
+__device__ __forceinline__ void wait_first() {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncwarp();
+}
+__device__ __forceinline__ void wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+}
+
+// stage_async, then everything complete and visible to the warp.
+template <int NMAX, bool LOWER, int LD = Shape<NMAX>::LD>
+__device__ __forceinline__ void stage(float *As, const float *ga, long long lda, int n) {
+    stage_async<NMAX, LOWER, LD>(As, ga, lda, n);
+    wait_all();
 }
 
 // Write the n x n result in As back to ga (LOWER: the lower triangle only,
@@ -214,7 +235,9 @@ __device__ __forceinline__ void panel(float *As, int n, int c0, float *dv, float
 
 // In-place Cholesky of the lower triangle of As (order n <= NMAX); dv[j]
 // receives 1 / l_jj; bc is 32 floats (16-byte aligned) of per-warp scratch.
-// Returns info (uniform).
+// As may still be arriving from stage_async beyond column 15 (wait_first()
+// done): the first panel reads only columns 0..15, and the copies are
+// waited for before anything else.  Returns info (uniform).
 template <int NMAX>
 __device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, bool fp64diag) {
     constexpr int LD = Shape<NMAX>::LD;
@@ -228,6 +251,7 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, boo
         } else {
             panel<NMAX, 0>(As, n, c0, dv, bc, fp64diag, info);
         }
+        if (c0 == 0) wait_all();  // columns 16.. of a stage_async'd operand (a no-op after stage)
         // ---- 2. trailing update on the tensor cores, 16 x 16 per step
         float *wp = opaque(As);
         const int r0 = c0 + 16;

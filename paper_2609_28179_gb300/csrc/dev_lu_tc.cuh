@@ -140,6 +140,7 @@ __device__ __forceinline__ void panel(float *As, int *prow, int n, int c0, int *
                 if (k > j + 1) update(k);
         }
     }
+    if (c0 == 0) tcwarp::wait_all();  // columns 16.. of a stage_async'd operand
     // ---- 2. panel to its logical rows; permute the other columns and prow
     int pr[R];
 #pragma unroll
@@ -177,6 +178,9 @@ __device__ __forceinline__ void panel(float *As, int *prow, int n, int c0, int *
 
 // In-place LU of As (order n <= NMAX).  prow[i] (initially i) receives the
 // original row held by logical row i; ipiv_s the interchanges, dv[j] = 1/u_jj.
+// As may still be arriving from stage_async beyond column 15 (wait_first()
+// done): the first panel factors columns 0..15 in registers and waits for
+// the copies before it touches any other column.
 template <int NMAX>
 __device__ __forceinline__ int getrf(float *As, int n, int *prow, int *ipiv_s, float *dv) {
     constexpr int LD = Shape<NMAX>::LD;

@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(256, 1) k_chol_tc(int n, int nrhs, Mat A, Mat 
     double *xd = reinterpret_cast<double *>(bc + 32);  // NMAX doubles (RF), 16-byte aligned
     const int b = blockIdx.x * (blockDim.x >> 5) + w;
     if (b >= batch) return;  // whole warp
-    tcwarp::stage<NMAX, true>(As, A.p + (long long)b * A.s, A.ld, n);
+    tcwarp::stage_async<NMAX, true>(As, A.p + (long long)b * A.s, A.ld, n);
+    tcwarp::wait_first();  // the first panel starts while columns 16.. arrive
     const int inf = tcwarp::potrf<NMAX>(As, n, dv, bc, fp64diag != 0);
     if (lane == 0) info[b] = inf;
     if (has_rhs(OP)) {

@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(256, 1) k_lu_tc(int n, int nrhs, Mat A, int *i
     if (b >= batch) return;  // whole warp
 #pragma unroll
     for (int q = 0; q < R; ++q) prow[lane + 32 * q] = lane + 32 * q;
-    tcwarp::stage<NMAX, false, LD>(As, A.p + (long long)b * A.s, A.ld, n);
+    tcwarp::stage_async<NMAX, false, LD>(As, A.p + (long long)b * A.s, A.ld, n);
+    tcwarp::wait_first();  // the first panel starts while columns 16.. arrive
     const int inf = tclu::getrf<NMAX>(As, n, prow, ps, dv);
     if (lane == 0) info[b] = inf;
     int *gp = ipiv + (long long)b * n;
