@@ -24,6 +24,9 @@ OPS = ["gemm", "posv", "trsm", "getrf_getrs", "rot3", "se3"]
 OP_ID = {"gemm": g.GLASS_OP_GEMM, "posv": g.GLASS_OP_POSV, "trsm": g.GLASS_OP_TRSM,
          "getrf_getrs": g.GLASS_OP_GETRF_GETRS, "rot3": g.GLASS_OP_ROT3, "se3": g.GLASS_OP_SE3}
 SWEEP_N = [3, 6, 7, 12, 14, 24, 32, 64]
+# Orders of the placement table: the sweep's, plus 16 (the smallest order of
+# the tensor-core GEMM kernels, which the FP32 block placement uses there).
+TABLE_N = [3, 6, 7, 12, 14, 16, 24, 32, 64]
 SWEEP_B = [1, 64, 1024, 16384]
 NPTS = 1024
 DESTRUCTIVE = {"posv", "trsm", "getrf_getrs"}

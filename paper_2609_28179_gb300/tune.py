@@ -104,13 +104,13 @@ def _sets_for(op, n, batch):
 def sweep(out_path: str, ops=None, sizes=None, batches=None, seed: int = 7, iters: int = 5):
     import torch
     import paper_2609_28179_gb300 as g
-    from paper_2609_28179_gb300.cells import OPS, SWEEP_B, SWEEP_N, Cell
+    from paper_2609_28179_gb300.cells import OPS, SWEEP_B, TABLE_N, Cell
     g.lib()
     rng = random.Random(seed)
     os.makedirs(os.path.dirname(out_path) or ".", exist_ok=True)
     with open(out_path, "w") as f:
         for op in ops or OPS:
-            for n in sizes or SWEEP_N:
+            for n in sizes or TABLE_N:
                 for batch in batches or SWEEP_B:
                     cell = Cell(op, n, batch, sets=_sets_for(op, n, batch), device_inputs=True, seed=seed + n)
                     meas = measure(cell, g.PLACEMENTS, iters=iters, rng=rng)
@@ -191,7 +191,7 @@ def load_grid(path: str = GRID_FILE):
 
 
 def codegen(inp: str = GRID_FILE, out: str = TABLE_H):
-    from paper_2609_28179_gb300.cells import OPS, SWEEP_B, SWEEP_N
+    from paper_2609_28179_gb300.cells import OPS, SWEEP_B, TABLE_N as SWEEP_N
     cells = load_grid(inp)
     rows = []
     for op in OPS:

@@ -30,10 +30,10 @@ def test_committed_tables_match_the_committed_measurements(gen, inp, committed, 
 
 
 def test_measurement_files_cover_the_grid():
-    from paper_2609_28179_gb300.cells import OPS, SWEEP_B, SWEEP_N
+    from paper_2609_28179_gb300.cells import OPS, SWEEP_B, TABLE_N
     cells = tune.load_grid()
     for op in OPS:
-        for n in SWEEP_N:
+        for n in TABLE_N:
             for b in SWEEP_B:
                 meas = cells[(op, n, b)]
                 assert meas, (op, n, b)
