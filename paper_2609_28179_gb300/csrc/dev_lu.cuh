@@ -264,4 +264,96 @@ __device__ __forceinline__ void getrs(const float (&a)[LU<NMAX>::R][NMAX], const
 
 }  // namespace warp
 
+// ------------------------------------------------------------ half-warp
+// Orders <= 16 with two problems per warp: lanes 16 h .. 16 h + 15 hold the
+// rows of problem h (row r in lane 16 h + r).  The same rule and result as
+// warp::getrf -- largest |a_ij| among the rows not yet eliminated, smallest
+// logical position on ties -- with the reductions as butterflies inside each
+// half (shuffle distances 8, 4, 2, 1 never cross halves).  A zero pivot takes
+// the same path as any other (its multipliers are exactly zero: every
+// candidate is zero), so the two halves never diverge.
+namespace half {
+
+__device__ __forceinline__ unsigned half_max(unsigned v) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(GLASS_FULL_MASK, v, o));
+    return v;
+}
+__device__ __forceinline__ unsigned half_min(unsigned v) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(GLASS_FULL_MASK, v, o));
+    return v;
+}
+
+// a[*]: row r = lane % 16 of this half's problem; pos receives the row's
+// final logical position.  sm: this half's shared scratch, 2 * NMAX words
+// (pp[j] = row chosen at step j, prc[j] = 1 / u_jj).  ipiv_out receives
+// ipiv[0..n) (lane 0 of the half writes).  Returns info.
+template <int NMAX>
+__device__ __forceinline__ int getrf(float (&a)[NMAX], int &pos, int *sm, int *ipiv_out, int n) {
+    static_assert(NMAX <= 16, "half-warp: orders up to 16");
+    const int lane = threadIdx.x & 31, r = lane & 15, base = lane & 16;
+    int *pp = sm;
+    float *prc = reinterpret_cast<float *>(sm + NMAX);
+    bool done = r >= n;
+    pos = r;
+    int info = 0;
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+            const unsigned key = done ? 0u : __float_as_uint(fabsf(a[j])) + 1u;
+            const unsigned kmax = half_max(key);
+            const int ppos = (int)half_min(key == kmax ? (unsigned)pos : 0xffffffffu);
+            const unsigned m = __ballot_sync(GLASS_FULL_MASK, !done && pos == ppos);
+            const int pphys = __ffs((m >> base) & 0xffffu) - 1;  // the winner's row in this half
+            if (ipiv_out != nullptr && r == 0) ipiv_out[j] = ppos;
+            if (pos == j) pos = ppos;
+            if (r == pphys) { pos = j; done = true; }
+            const float pv = __shfl_sync(GLASS_FULL_MASK, a[j], base + pphys);
+            const float rc = pv != 0.f ? 1.0f / pv : 0.f;
+            if (r == 0) { pp[j] = pphys; prc[j] = rc; }
+            if (pv == 0.f && info == 0) info = j + 1;
+            const float mj = done ? 0.f : a[j] * rc;
+            if (!done) a[j] = mj;
+#pragma unroll
+            for (int k = 0; k < NMAX; ++k) {  // fixed range: keeps a[] in registers
+                if (k > j && k < n) {
+                    const float pk = __shfl_sync(GLASS_FULL_MASK, a[k], base + pphys);
+                    a[k] = fmaf(-mj, pk, a[k]);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    return info;
+}
+
+// One right-hand side held by physical row (x = b of row lane % 16, the
+// row's original index): on return x is the solution component at logical
+// position pos.
+template <int NMAX>
+__device__ __forceinline__ void getrs(const float (&a)[NMAX], int pos, const int *sm, float &x, int n) {
+    const int lane = threadIdx.x & 31, r = lane & 15, base = lane & 16;
+    const int *pp = sm;
+    const float *prc = reinterpret_cast<const float *>(sm + NMAX);
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+            const float yj = __shfl_sync(GLASS_FULL_MASK, x, base + pp[j]);
+            if (pos > j && r < n) x = fmaf(-a[j], yj, x);
+        }
+    }
+#pragma unroll
+    for (int j = NMAX - 1; j >= 0; --j) {
+        if (j < n) {
+            const int pj = pp[j];
+            const float xj = __shfl_sync(GLASS_FULL_MASK, x, base + pj) * prc[j];
+            if (r == pj) x = xj;
+            else if (pos < j && r < n) x = fmaf(-a[j], xj, x);
+        }
+    }
+}
+
+}  // namespace half
+
 }  // namespace glass

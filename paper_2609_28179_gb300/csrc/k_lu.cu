@@ -1,9 +1,9 @@
 // k_lu.cu -- batched getrf + getrs (partial pivoting) at thread, warp and
 // block scope.  Thread scope stages 32*pack problems through shared memory;
-// warp scope loads rows straight into registers (one per lane) up to order
-// 16 and runs the blocked tensor-core factorization (dev_lu_tc.cuh) on the
-// problem in shared memory above that; block scope is a 64-thread row team
-// (dev_rows.cuh), one row per thread.
+// warp scope loads rows straight into registers up to order 16 -- two
+// problems per warp, one per half -- and runs the blocked tensor-core
+// factorization (dev_lu_tc.cuh) on the problem in shared memory above that;
+// block scope is a 64-thread row team (dev_rows.cuh), one row per thread.
 #include "dev_lu.cuh"
 #include "dev_lu_tc.cuh"
 #include "dev_rows.cuh"
@@ -116,6 +116,39 @@ __global__ void __launch_bounds__(256, NMAX <= 32 ? 2 : 1) k_lu_warp(int n, int 
             if (k < n && lane + 32 * q < n) wa[(long long)k * A.ld + pos[q]] = a[q][k];
 }
 
+// Warp scope, orders up to 16: two problems per warp, one per half (row r in
+// lane 16 h + r); half-warp primitive of dev_lu.cuh.  A half without a
+// problem (odd batch) runs on zeros and stores nothing: the shuffles need
+// the whole warp.
+template <int NMAX>
+__global__ void __launch_bounds__(256) k_lu_half(int n, int nrhs, Mat A, int *ipiv, Mat B, int *info, int batch) {
+    extern __shared__ int hsmem[];
+    const int lane = threadIdx.x & 31, r = lane & 15, h = lane >> 4, w = threadIdx.x >> 5;
+    int *sm = hsmem + (2 * w + h) * 2 * NMAX;
+    const long long pair = (long long)blockIdx.x * (blockDim.x >> 5) + w;
+    if (2 * pair >= batch) return;  // whole warp
+    const long long b = 2 * pair + h;
+    const bool live = b < batch;
+    float a[NMAX];
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) a[k] = (live && k < n && r < n) ? A.cget(b, r, k) : 0.f;
+    int pos;
+    const int inf = half::getrf<NMAX>(a, pos, sm, live ? ipiv + b * n : nullptr, n);
+    if (live && r == 0) info[b] = inf;
+#pragma unroll 1
+    for (int c = 0; c < nrhs; ++c) {
+        float x = (live && r < n) ? B.cget(b, r, c) : 0.f;
+        half::getrs<NMAX>(a, pos, sm, x, n);
+        if (live && r < n) B.cset(b, pos, c, x);
+    }
+    if (live && r < n) {
+        float *wa = opaque(A.p + b * A.s);
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k)
+            if (k < n) wa[(long long)k * A.ld + pos] = a[k];
+    }
+}
+
 // Warp scope, orders 33..64: blocked LU with tensor-core trailing updates on
 // the problem held in the warp's shared memory (dev_lu_tc.cuh); per warp
 // A (NMAX x LD), 1/u_jj, the interchanges and the original row of each
@@ -219,7 +252,7 @@ size_t smem_lu(int n, int nrhs, Placement pl) {
         case SCOPE_WARP:
             return n > 32   ? (size_t)pl.pack * lu_tc_floats<64>() * 4
                    : n > 16 ? (size_t)pl.pack * lu_tc_floats<32>() * 4
-                            : (size_t)pl.pack * 2 * 16 * 4;
+                            : (size_t)pl.pack * 4 * 16 * 4;
         default: {
             const int N = n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64;
             const int f = N == 8 ? lu_team_floats<8>() : N == 16 ? lu_team_floats<16>()
@@ -266,10 +299,12 @@ cudaError_t launch_getrf_getrs(int n, int nrhs, Mat A, int *ipiv, Mat B, int *in
         const int th = 32 * pl.pack;
         if (n > 32) return go(k_lu_tc<64>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
         if (n > 16) return go(k_lu_tc<32>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
+        // orders up to 16: two problems per warp (half-warp primitive)
         const int N = n <= 8 ? 8 : 16;
-        const size_t sw = (size_t)pl.pack * 2 * N * 4;
-        if (N == 8) return go(k_lu_warp<8>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
-        return go(k_lu_warp<16>, grid, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
+        const size_t sw = (size_t)pl.pack * 4 * N * 4;
+        const int g2 = ceil_div(batch, 2 * pl.pack);
+        if (N == 8) return go(k_lu_half<8>, g2, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
+        return go(k_lu_half<16>, g2, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
     }
     const int th = rows::T * pl.pack;
     if (n <= 8) return go(k_lu_rows<8>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
