@@ -6,8 +6,9 @@
 // the rows still to be eliminated wins, the smallest current row index on
 // ties; ipiv[j] records the exchanged row in sequential-swap form.
 //
-// Warp scope keeps every row in the registers of one lane and never moves
-// it: a pivot exchange only relabels logical positions (pos[]), the
+// Warp scope (orders up to 16, two problems per warp) keeps every row in the
+// registers of one lane and never moves it: a pivot exchange only relabels
+// logical positions (pos), the
 // multipliers stay with their physical row, and the final packed factor is
 // written out row by row at each row's logical position.  This is the same
 // factorization as the explicit-swap algorithm (rows carry their
@@ -108,167 +109,11 @@ __device__ __forceinline__ void getrs(const float (&a)[NMAX][NMAX], const int (&
 
 }  // namespace thread
 
-namespace warp {
-
-// Sort key of a pivot candidate: larger |v| first, then smaller logical
-// position; the low bits carry the physical row.  0 = not a candidate.
-__device__ __forceinline__ unsigned long long piv_key(float absv, int pos, int phys) {
-    return ((unsigned long long)__float_as_uint(absv) << 32) | (1u << 12) | ((unsigned)(63 - pos) << 6) |
-           (unsigned)phys;
-}
-
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(GLASS_FULL_MASK, k, o);
-        k = v > k ? v : k;
-    }
-    return k;
-}
-
-template <int NMAX>
-struct LU {
-    static constexpr int R = (NMAX + 31) / 32;
-};
-
-// Rows lane+32q in a[q][*]; pos[q] receives each row's final logical
-// position.  sm: the warp's shared scratch, 2*NMAX words: pp[j] = physical
-// row chosen at step j, prc[j] = 1 / u_jj (read back by getrs).
-// The pivot is found with two warp reductions (redux.sync): the largest
-// |a_ij| bit pattern among candidate rows (|x| orders like its IEEE bits),
-// then the smallest logical position carrying it -- exactly "largest
-// magnitude, smallest row index on ties".  ipiv_out (may be null) receives
-// ipiv[0..n).  Returns info (uniform).
-template <int NMAX>
-__device__ __forceinline__ int getrf(float (&a)[LU<NMAX>::R][NMAX], int (&pos)[LU<NMAX>::R], int *sm,
-                                     int *ipiv_out, int n) {
-    constexpr int R = LU<NMAX>::R;
-    const int lane = threadIdx.x & 31;
-    int *pp = sm;
-    float *prc = reinterpret_cast<float *>(sm + NMAX);
-    bool done[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) { pos[q] = lane + 32 * q; done[q] = false; }
-    int info = 0;
-#pragma unroll
-    for (int j = 0; j < NMAX; ++j) {
-        if (j < n) {
-            // candidate key: |a_ij| bits + 1 (0 = no candidate); per lane the
-            // best of its rows, smaller position on equal keys
-            unsigned key = 0, kpos = 0xffffffffu;
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const int i = lane + 32 * q;
-                if (!done[q] && i < n) {
-                    const unsigned kq = __float_as_uint(fabsf(a[q][j])) + 1u;
-                    if (kq > key || (kq == key && (unsigned)pos[q] < kpos)) { key = kq; kpos = pos[q]; }
-                }
-            }
-            const unsigned kmax = __reduce_max_sync(GLASS_FULL_MASK, key);
-            const int ppos = (int)__reduce_min_sync(GLASS_FULL_MASK, key == kmax ? kpos : 0xffffffffu);
-            if (ipiv_out != nullptr && lane == 0) ipiv_out[j] = ppos;
-            // physical row of the winner
-            int pphys = 0;
-#pragma unroll
-            for (int q = R - 1; q >= 0; --q) {
-                const unsigned m = __ballot_sync(GLASS_FULL_MASK, !done[q] && lane + 32 * q < n && pos[q] == ppos);
-                if (m) pphys = 32 * q + __ffs(m) - 1;
-            }
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const int i = lane + 32 * q;
-                if (pos[q] == j) pos[q] = ppos;
-                if (i == pphys) { pos[q] = j; done[q] = true; }
-            }
-            const int pq = pphys >> 5, pl = pphys & 31;
-            float pvsel = a[0][j];
-#pragma unroll
-            for (int q = 1; q < R; ++q)
-                if (pq == q) pvsel = a[q][j];
-            const float pv = __shfl_sync(GLASS_FULL_MASK, pvsel, pl);
-            const float rc = pv != 0.f ? 1.0f / pv : 0.f;
-            if (lane == 0) { pp[j] = pphys; prc[j] = rc; }
-            if (pv == 0.f) {
-                if (info == 0) info = j + 1;
-                continue;
-            }
-            float m[R];
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                m[q] = a[q][j] * rc;
-                if (!done[q]) a[q][j] = m[q];
-            }
-#pragma unroll
-            for (int k = j + 1; k < NMAX; ++k) {
-                if (k < n) {
-                    float sel = a[0][k];
-#pragma unroll
-                    for (int q = 1; q < R; ++q)
-                        if (pq == q) sel = a[q][k];
-                    const float pk = __shfl_sync(GLASS_FULL_MASK, sel, pl);
-#pragma unroll
-                    for (int q = 0; q < R; ++q)
-                        if (!done[q]) a[q][k] = fmaf(-m[q], pk, a[q][k]);
-                }
-            }
-        }
-    }
-    __syncwarp();
-    return info;
-}
-
-// One right-hand side held by physical row (x[q] = b of row lane+32q, the
-// row's ORIGINAL index): on return x[q] is the solution component at
-// logical position pos[q].  sm: the scratch written by getrf.
-template <int NMAX>
-__device__ __forceinline__ void getrs(const float (&a)[LU<NMAX>::R][NMAX], const int (&pos)[LU<NMAX>::R],
-                                      const int *sm, float (&x)[LU<NMAX>::R], int n) {
-    constexpr int R = LU<NMAX>::R;
-    const int lane = threadIdx.x & 31;
-    const int *pp = sm;
-    const float *prc = reinterpret_cast<const float *>(sm + NMAX);
-#pragma unroll
-    for (int j = 0; j < NMAX; ++j) {
-        if (j < n) {
-            const int pj = pp[j];
-            const int pq = pj >> 5;
-            float sel = x[0];
-#pragma unroll
-            for (int q = 1; q < R; ++q)
-                if (pq == q) sel = x[q];
-            const float yj = __shfl_sync(GLASS_FULL_MASK, sel, pj & 31);
-#pragma unroll
-            for (int q = 0; q < R; ++q)
-                if (pos[q] > j && lane + 32 * q < n) x[q] = fmaf(-a[q][j], yj, x[q]);
-        }
-    }
-#pragma unroll
-    for (int j = NMAX - 1; j >= 0; --j) {
-        if (j < n) {
-            const int pj = pp[j];
-            const int pq = pj >> 5;
-            float sel = x[0];
-#pragma unroll
-            for (int q = 1; q < R; ++q)
-                if (pq == q) sel = x[q];
-            const float xj = __shfl_sync(GLASS_FULL_MASK, sel, pj & 31) * prc[j];
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const int i = lane + 32 * q;
-                if (i == pj) x[q] = xj;
-                else if (pos[q] < j && i < n) x[q] = fmaf(-a[q][j], xj, x[q]);
-            }
-        }
-    }
-}
-
-}  // namespace warp
-
 // ------------------------------------------------------------ half-warp
 // Orders <= 16 with two problems per warp: lanes 16 h .. 16 h + 15 hold the
-// rows of problem h (row r in lane 16 h + r).  The same rule and result as
-// warp::getrf -- largest |a_ij| among the rows not yet eliminated, smallest
-// logical position on ties -- with the reductions as butterflies inside each
+// rows of problem h (row r in lane 16 h + r).  The pivot rule of every scope
+// -- largest |a_ij| among the rows not yet eliminated, smallest logical
+// position on ties -- with the reductions as butterflies inside each
 // half (shuffle distances 8, 4, 2, 1 never cross halves).  A zero pivot takes
 // the same path as any other (its multipliers are exactly zero: every
 // candidate is zero), so the two halves never diverge.

@@ -76,46 +76,6 @@ __global__ void __launch_bounds__(256) k_lu_thread(int n_rt, int nrhs, Mat A, in
     }
 }
 
-template <int NMAX>
-__global__ void __launch_bounds__(256, NMAX <= 32 ? 2 : 1) k_lu_warp(int n, int nrhs, Mat A, int *ipiv, Mat B,
-                                                                    int *info, int batch) {
-    constexpr int R = warp::LU<NMAX>::R;
-    extern __shared__ int ismem[];
-    const int lane = threadIdx.x & 31;
-    int *sm = ismem + (threadIdx.x >> 5) * 2 * NMAX;
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (b >= batch) return;
-    float a[R][NMAX];
-    int pos[R];
-#pragma unroll
-    for (int k = 0; k < NMAX; ++k)
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int i = lane + 32 * q;
-            a[q][k] = (k < n && i < n) ? A.cget(b, i, k) : 0.f;
-        }
-    const int inf = warp::getrf<NMAX>(a, pos, sm, ipiv + (long long)b * n, n);
-    if (lane == 0) info[b] = inf;
-    for (int c = 0; c < nrhs; ++c) {
-        float x[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int i = lane + 32 * q;
-            x[q] = (i < n) ? B.cget(b, i, c) : 0.f;
-        }
-        warp::getrs<NMAX>(a, pos, sm, x, n);
-#pragma unroll
-        for (int q = 0; q < R; ++q)
-            if (lane + 32 * q < n) B.cset(b, pos[q], c, x[q]);
-    }
-    float *wa = opaque(A.p + (long long)b * A.s);
-#pragma unroll
-    for (int k = 0; k < NMAX; ++k)
-#pragma unroll
-        for (int q = 0; q < R; ++q)
-            if (k < n && lane + 32 * q < n) wa[(long long)k * A.ld + pos[q]] = a[q][k];
-}
-
 // Warp scope, orders up to 16: two problems per warp, one per half (row r in
 // lane 16 h + r); half-warp primitive of dev_lu.cuh.  A half without a
 // problem (odd batch) runs on zeros and stores nothing: the shuffles need
