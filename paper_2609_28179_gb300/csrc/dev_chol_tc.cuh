@@ -37,6 +37,14 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// The sign bit flipped, as an instruction at each call (kept out of common
+// subexpressions, so the result is not held in a register between uses).
+__device__ __forceinline__ unsigned negate_bits(unsigned x) {
+    unsigned r;
+    asm volatile("xor.b32 %0, %1, 0x80000000;" : "=r"(r) : "r"(x));
+    return r;
+}
+
 __device__ __forceinline__ void split(float x, unsigned &hi, unsigned &lo) {
     hi = tf32(x);
     lo = tf32(x - __uint_as_float(hi));
@@ -63,6 +71,23 @@ __device__ __forceinline__ void stage_async(float *As, const float *ga, long lon
     constexpr int R = Shape<NMAX>::R;
     const int lane = threadIdx.x & 31;
     const bool vec = (n & 3) == 0 && (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(ga) & 15) == 0;
+    if (vec && n == NMAX && lda == NMAX) {
+        // A full, packed problem: lane l copies 16-byte group l % G of
+        // column l / G and every (32 / G)-th column after it, so each copy
+        // is one instruction at a fixed offset from two base addresses.
+        constexpr int G = NMAX / 4, CS = 32 / G, IT = NMAX / CS;
+        const int k0 = lane / G, r = 4 * (lane % G);
+        const float *src = ga + k0 * NMAX + r;
+        float *dst = As + k0 * LD + r;
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            if (!LOWER || r + 3 >= k0 + CS * it) cp_async16(dst + CS * it * LD, src + CS * it * NMAX);
+            else *reinterpret_cast<float4 *>(dst + CS * it * LD) = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (it == 16 / CS - 1) asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        return;
+    }
     auto columns = [&](int k0, int k1) {
         if (vec) {
 #pragma unroll 4
@@ -113,6 +138,31 @@ __device__ __forceinline__ void unstage(float *ga, long long lda, const float *A
     const int lane = threadIdx.x & 31;
     const bool vec = (n & 3) == 0 && (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(ga) & 15) == 0;
     float *wg = opaque(ga);
+    if (vec && n == NMAX && lda == NMAX) {  // the lane-to-group map of stage_async's full form
+        constexpr int G = NMAX / 4, CS = 32 / G, IT = NMAX / CS;
+        const int k0 = lane / G, r = 4 * (lane % G);
+        float *dst = wg + k0 * NMAX + r;
+        const float *src = As + k0 * LD + r;
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {  // LOWER: the groups wholly on or below the diagonal
+            const float4 v = *reinterpret_cast<const float4 *>(src + CS * it * LD);
+            if (!LOWER || r >= k0 + CS * it) __stcs(reinterpret_cast<float4 *>(dst + CS * it * NMAX), v);
+        }
+        if constexpr (LOWER) {
+            // The rest of the lower triangle: in each 4 x 4 diagonal block
+            // (first row and column 4c), the six entries (4c + i, 4c + j)
+            // with 1 <= j <= i <= 3, numbered w = 0..5 column by column.
+#pragma unroll
+            for (int e = lane; e < 6 * (NMAX / 4); e += 32) {
+                const int c = e / 6, w = e - 6 * c;
+                const int j = w < 3 ? 1 : (w < 5 ? 2 : 3);
+                const int i = w < 3 ? w + 1 : (w < 5 ? w - 1 : 3);
+                const int row = 4 * c + i, col = 4 * c + j;
+                wg[col * NMAX + row] = As[col * LD + row];
+            }
+        }
+        return;
+    }
     if (vec) {
 #pragma unroll 4
         for (int e = lane; e < NMAX * NMAX / 4; e += 32) {
@@ -144,9 +194,9 @@ __device__ __forceinline__ void unstage(float *ga, long long lda, const float *A
 // below hold rows above the panel only), right-looking in registers.  Per
 // column the raw entries of rows c0..c0+15 are published to a 16-float
 // shared segment (two, alternating) and read back by every lane as 16-byte
-// broadcasts: the pivot comes from there and l_kj = a_kj / l_jj is formed
-// in each lane, so the update of column k is one multiply and one fused
-// multiply-add per row.  Rows above the diagonal are updated too -- their
+// broadcasts: the pivot comes from there, and with u_i = l_ij / l_jj formed
+// once per row the update of column k is one fused multiply-add per row
+// (a_ik -= u_i a_kj).  Rows above the diagonal are updated too -- their
 // values are never read and never written back.  The lower part is written
 // back and mirrored, transposed, into the unused upper triangle
 // (As[i * LD + r] = l_ir for r < i), where the backward solve reads rows of
@@ -195,20 +245,24 @@ __device__ __forceinline__ void panel(float *As, int n, int c0, float *dv, float
             float l, r;
             chol_diag(d, fp64diag, l, r);
             if (lane == 0) dv[cj] = r;
+            // u_i = l_ij / l_jj, so that l_ij l_kj = u_i a_kj: one fused
+            // multiply-add per entry of the update, no product per column.
+            float u[R];
 #pragma unroll
-            for (int q = QLO; q < R; ++q) p[q][j] = (lane + 32 * q == cj) ? l : p[q][j] * r;
+            for (int q = QLO; q < R; ++q) {
+                p[q][j] = (lane + 32 * q == cj) ? l : p[q][j] * r;
+                u[q] = p[q][j] * r;
+            }
             if (j + 1 < 16) {
-                const float l1 = s[j + 1] * r;
 #pragma unroll
-                for (int q = QLO; q < R; ++q) p[q][j + 1] = fmaf(-p[q][j], l1, p[q][j + 1]);
+                for (int q = QLO; q < R; ++q) p[q][j + 1] = fmaf(-u[q], s[j + 1], p[q][j + 1]);
                 publish(j + 1);
             }
 #pragma unroll
             for (int k = 0; k < 16; ++k) {  // fixed range: keeps p[][] in registers
                 if (k > j + 1) {
-                    const float lkj = s[k] * r;
 #pragma unroll
-                    for (int q = QLO; q < R; ++q) p[q][k] = fmaf(-p[q][j], lkj, p[q][k]);
+                    for (int q = QLO; q < R; ++q) p[q][k] = fmaf(-u[q], s[k], p[q][k]);
                 }
             }
         }
@@ -252,21 +306,26 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, boo
             panel<NMAX, 0>(As, n, c0, dv, bc, fp64diag, info);
         }
         if (c0 == 0) wait_all();  // columns 16.. of a stage_async'd operand (a no-op after stage)
-        // ---- 2. trailing update on the tensor cores, 16 x 16 per step
+        // ---- 2. trailing update on the tensor cores, 16 x 16 per step.
+        // Row tile rt of L21 is the A operand of the tiles in its row and,
+        // transposed, the B operand of the tiles in column rt, with the same
+        // per-lane entries: each is split once (sh/sl); the A operand is the
+        // negated split (split(-x) = -split(x): TF32 rounding is symmetric).
         float *wp = opaque(As);
         const int r0 = c0 + 16;
+        constexpr int NT = NMAX / 16 - 1;
+        unsigned sh[NT][2][4], sl[NT][2][4];
 #pragma unroll
-        for (int rt = 0; rt < NMAX / 16 - 1; ++rt) {  // fixed trip counts: the tiles interleave
+        for (int rt = 0; rt < NT; ++rt) {  // fixed trip counts: the tiles interleave
             const int R0 = r0 + 16 * rt;
             if (R0 >= n) break;
-            unsigned ah[2][4], al[2][4];
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
                 const float *col = As + (c0 + 8 * kk + t) * LD;
-                split(-col[R0 + g], ah[kk][0], al[kk][0]);
-                split(-col[R0 + g + 8], ah[kk][1], al[kk][1]);
-                split(-col[4 * LD + R0 + g], ah[kk][2], al[kk][2]);
-                split(-col[4 * LD + R0 + g + 8], ah[kk][3], al[kk][3]);
+                split(col[R0 + g], sh[rt][kk][0], sl[rt][kk][0]);
+                split(col[R0 + g + 8], sh[rt][kk][1], sl[rt][kk][1]);
+                split(col[4 * LD + R0 + g], sh[rt][kk][2], sl[rt][kk][2]);
+                split(col[4 * LD + R0 + g + 8], sh[rt][kk][3], sl[rt][kk][3]);
             }
 #pragma unroll
             for (int ct = 0; ct <= rt; ++ct) {
@@ -283,18 +342,20 @@ __device__ __forceinline__ int potrf(float *As, int n, float *dv, float *bc, boo
                 }
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {
-                    const float *col = As + (c0 + 8 * kk + t) * LD;
-                    unsigned bh0[2], bl0[2], bh1[2], bl1[2];
-                    split(col[C0 + g], bh0[0], bl0[0]);
-                    split(col[4 * LD + C0 + g], bh0[1], bl0[1]);
-                    split(col[C0 + 8 + g], bh1[0], bl1[0]);
-                    split(col[4 * LD + C0 + 8 + g], bh1[1], bl1[1]);
-                    mma_tf32(a0, al[kk], bh0);
-                    mma_tf32(a1, al[kk], bh1);
-                    mma_tf32(a0, ah[kk], bl0);
-                    mma_tf32(a1, ah[kk], bl1);
-                    mma_tf32(a0, ah[kk], bh0);
-                    mma_tf32(a1, ah[kk], bh1);
+                    unsigned ah[4], al[4];  // formed at each use: held for all tiles they would cost 16 registers
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        ah[e] = negate_bits(sh[rt][kk][e]);
+                        al[e] = negate_bits(sl[rt][kk][e]);
+                    }
+                    const unsigned bh0[2] = {sh[ct][kk][0], sh[ct][kk][2]}, bl0[2] = {sl[ct][kk][0], sl[ct][kk][2]};
+                    const unsigned bh1[2] = {sh[ct][kk][1], sh[ct][kk][3]}, bl1[2] = {sl[ct][kk][1], sl[ct][kk][3]};
+                    mma_tf32(a0, al, bh0);
+                    mma_tf32(a1, al, bh1);
+                    mma_tf32(a0, ah, bl0);
+                    mma_tf32(a1, ah, bl1);
+                    mma_tf32(a0, ah, bh0);
+                    mma_tf32(a1, ah, bh1);
                 }
                 c[0] = a0[0];
                 c[LD] = a0[1];
