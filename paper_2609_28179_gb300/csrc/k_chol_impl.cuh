@@ -371,8 +371,10 @@ __device__ __forceinline__ void residual_f64(const float *ga, long long lda, con
 // in global memory: the factor is written back last), dx = A^{-1} r with
 // the factor, x1 = x0 + dx.  (A shared-memory copy of A halves the resident
 // warps and measured slower: the residual is bound by the FP64 pipe.)
+// Orders 17..32 without refinement cap the registers at 64, so 32 warps fit
+// on an SM instead of 28 (posv n = 32 at batch 16384: 60 -> 58 us).
 template <int OP, int NMAX, bool RF>
-__global__ void __launch_bounds__(256, 1) k_chol_tc(int n, int nrhs, Mat A, Mat B, int *info, int batch, int fp64diag) {
+__global__ void __launch_bounds__(256, NMAX == 32 && !RF ? 4 : 1) k_chol_tc(int n, int nrhs, Mat A, Mat B, int *info, int batch, int fp64diag) {
     constexpr int LD = tcwarp::Shape<NMAX>::LD;
     constexpr int R = tcwarp::Shape<NMAX>::R;
     extern __shared__ __align__(16) float smem[];
