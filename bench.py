@@ -674,8 +674,9 @@ def extra_tc_gemm(peaks, batch=65536):
 
 
 def extra_refine(peaks, batch=16384):
-    """Refined SPD solve: n in {32, 64}, kappa swept 1e1..1e6 by decades, one FP64-residual
-    step; forward error of x0 and x1 against the FP64 solution (numpy/LAPACK)
+    """Refined SPD solve: n in {32, 64}, kappa swept 1e1..1e6 by decades, one refinement
+    step with the FP64 residual (x1) and with the compensated FP32 one (x1d);
+    forward error of x0, x1 and x1d against the FP64 solution (numpy/LAPACK)
     of the same FP32-rounded systems on a sample, and time at full batch."""
     import numpy as np
     import torch
@@ -692,10 +693,12 @@ def extra_refine(peaks, batch=16384):
             # FP64 reference solution of the FP32-rounded system (LAPACK via numpy)
             Xs = np.linalg.solve(Am, b.reshape(sample, n, 1).astype(np.float64)).reshape(-1)
             row = {}
-            for refine in (0, 1):
+            for tag, refine, resid in (("x0", 0, g.GLASS_RESIDUAL_FP64), ("x1", 1, g.GLASS_RESIDUAL_FP64),
+                                       ("x1d", 1, g.GLASS_RESIDUAL_DOT2)):
                 dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
                 info = torch.zeros(sample, dtype=torch.int32, device="cuda")
-                o = g.make_opts(scope=g.GLASS_SCOPE_WARP, pack=1, refine_steps=refine, fp64_diag=refine)
+                o = g.make_opts(scope=g.GLASS_SCOPE_WARP, pack=1, refine_steps=refine, fp64_diag=refine,
+                                residual=resid)
                 g.check(g.glass_batched_posv(n, 1, dA, n, n * n, dB, n, n, info, sample, o))
                 X = dB.cpu().numpy().astype(np.float64)
                 inf = info.cpu().numpy()
@@ -706,7 +709,7 @@ def extra_refine(peaks, batch=16384):
                 R = bm - Am @ Xm
                 be = (np.abs(R).max((1, 2)) / (np.abs(Am).sum(2).max(1) * np.abs(Xm).max((1, 2)) +
                                                np.abs(bm).max((1, 2))))[ok]
-                row[f"x{refine}"] = {"fwd_err_median": float(np.median(fwd)) if ok.any() else None,
+                row[tag] = {"fwd_err_median": float(np.median(fwd)) if ok.any() else None,
                                      "fwd_err_max": float(fwd.max()) if ok.any() else None,
                                      "bwd_err_max": float(be.max()) if ok.any() else None,
                                      "failed": int((~ok).sum()),
@@ -725,8 +728,8 @@ def extra_refine(peaks, batch=16384):
             for x, y in zip(As, bs):
                 x.copy_(A)
                 y.copy_(b)
-        for refine, fp64d in ((0, 0), (1, 1), (1, 0), (0, 1)):
-            o = g.make_opts(refine_steps=refine, fp64_diag=fp64d)
+        for refine, fp64d, resid in ((0, 0, 0), (1, 1, 0), (1, 0, 0), (0, 1, 0), (1, 1, g.GLASS_RESIDUAL_DOT2)):
+            o = g.make_opts(refine_steps=refine, fp64_diag=fp64d, residual=resid)
             k = [0]
 
             def fn():
@@ -735,7 +738,8 @@ def extra_refine(peaks, batch=16384):
                 g.glass_batched_posv(n, 1, As[i], n, n * n, bs[i], n, n, info, batch, o)
             ms = _graph_time(fn, sets, setup=setup)
             by = bytes_flops("posv", n, 1)[0] * batch + (4 * n * batch if refine else 0)
-            key = f"time_n{n}_refine{refine}" + ("" if fp64d == refine else f"_fp64diag{fp64d}")
+            key = f"time_n{n}_refine{refine}" + ("" if fp64d == refine else f"_fp64diag{fp64d}") + \
+                ("_dot2" if resid == g.GLASS_RESIDUAL_DOT2 else "")
             out[key] = {"us": ms * 1e3, "matrices_per_s": batch / (ms / 1e3), "gbs": by / (ms / 1e3) / 1e9}
     return out
 
@@ -1184,8 +1188,11 @@ def summarize_extras(ex):
            for n in (32, 64)},
         **{f"n{n}_refined_fp32diag_over_plain": d[f"time_n{n}_refine1_fp64diag0"]["us"] / d[f"time_n{n}_refine0"]["us"]
            for n in (32, 64)},
+        **{f"n{n}_refined_dot2_over_plain": d[f"time_n{n}_refine1_dot2"]["us"] / d[f"time_n{n}_refine0"]["us"]
+           for n in (32, 64)},
         **{k: {"x0_fwd_med": v["x0"]["fwd_err_median"], "x1_fwd_med": v["x1"]["fwd_err_median"],
-               "x1_bwd_max": v["x1"]["bwd_err_max"], "x1_failed": v["x1"]["failed"]}
+               "x1d_fwd_med": v["x1d"]["fwd_err_median"], "x1_bwd_max": v["x1"]["bwd_err_max"],
+               "x1d_bwd_max": v["x1d"]["bwd_err_max"], "x1_failed": v["x1"]["failed"]}
            for k, v in d.items() if k.startswith("n64_kappa")}})
     pick("learned_placement", lambda d: {k: {"median_regret": round(d[k]["median"], 4), "p90_regret": round(d[k]["p90"], 4)}
                                          for k in ("learned", "nearest_grid_table", "fixed_placement")})

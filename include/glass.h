@@ -70,6 +70,17 @@ typedef enum {
 
 typedef enum { GLASS_LAYOUT_COLMAJOR = 0, GLASS_LAYOUT_INTERLEAVED32 = 1 } glass_layout;
 
+/* Arithmetic of the refinement residual r = b - A x0 (posv with
+ * refine_steps == 1).  GLASS_RESIDUAL_FP64 accumulates in FP64.
+ * GLASS_RESIDUAL_DOT2 accumulates on the FP32 pipe with error-free
+ * transformations (Ogita, Rump and Oishi, "Accurate sum and dot product",
+ * SIAM J. Sci. Comput. 26(6), 2005, algorithm Dot2): every product's and
+ * every addition's exact rounding error is carried in a second FP32 sum, so
+ * r is as accurate as if it were evaluated in twice the FP32 precision and
+ * then rounded -- ample for one correction of an FP32 solve, without GB300's
+ * narrow FP64 pipe.  The paper prescribes neither; FP64 is the default. */
+typedef enum { GLASS_RESIDUAL_FP64 = 0, GLASS_RESIDUAL_DOT2 = 1 } glass_residual;
+
 typedef enum {
     GLASS_SCOPE_AUTO = -1,
     GLASS_SCOPE_THREAD = 0, /* one problem per thread, 32*pack problems per CTA */
@@ -114,6 +125,7 @@ typedef struct {
     int fp64_diag;    /* Cholesky: diagonal sqrt/reciprocal to FP64 accuracy */
     int use_learned;  /* auto placement: consult the learned cost model for
                          shapes outside the measured grid */
+    int residual;     /* posv refinement: glass_residual (0 = FP64) */
 } glass_opts;
 
 /* ---------------------------------------------------------------- BLAS-3 */
@@ -156,7 +168,9 @@ glass_status glass_batched_potrs(int n, int nrhs, const void *L, int lda, long l
 /* Batched SPD solve, fused factor + solve kept on chip (glass::posv of
  * Sec. III-A; POSV of Sec. IV-D).  A is overwritten by L (lower), B by X.
  * With opts->refine_steps == 1 the residual r = b - A x0 is formed in FP64
- * from the original A (re-read before L is written back) and one correction
+ * (or, with opts->residual == GLASS_RESIDUAL_DOT2, as a compensated FP32
+ * dot product) from the original A (re-read before L is written back) and
+ * one correction
  * dx = solve(L, r) is added, x1 = x0 + dx, for every right-hand side;
  * opts->fp64_diag computes the diagonal square roots and reciprocals to
  * FP64 accuracy, each rounded once to FP32 (the square root is the FP32 one,

@@ -29,6 +29,7 @@ GLASS_ERR_WORKSPACE = 5
 GLASS_F32, GLASS_F64, GLASS_BF16 = 0, 1, 2
 GLASS_MATH_FP32, GLASS_MATH_BF16_TC, GLASS_MATH_TF32_TC, GLASS_MATH_3XTF32_TC = 0, 1, 2, 3
 GLASS_LAYOUT_COLMAJOR, GLASS_LAYOUT_INTERLEAVED32 = 0, 1
+GLASS_RESIDUAL_FP64, GLASS_RESIDUAL_DOT2 = 0, 1
 GLASS_SCOPE_AUTO, GLASS_SCOPE_THREAD, GLASS_SCOPE_WARP, GLASS_SCOPE_BLOCK, GLASS_SCOPE_COMPOSED = -1, 0, 1, 2, 3
 (GLASS_OP_GEMM, GLASS_OP_POSV, GLASS_OP_TRSM, GLASS_OP_GETRF_GETRS, GLASS_OP_ROT3, GLASS_OP_SE3,
  GLASS_OP_POTRF, GLASS_OP_POTRS) = range(8)
@@ -53,12 +54,13 @@ class glass_placement(ctypes.Structure):
 class glass_opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("math", ctypes.c_int), ("layout", ctypes.c_int),
                 ("placement", glass_placement), ("refine_steps", ctypes.c_int),
-                ("fp64_diag", ctypes.c_int), ("use_learned", ctypes.c_int)]
+                ("fp64_diag", ctypes.c_int), ("use_learned", ctypes.c_int), ("residual", ctypes.c_int)]
 
 
 def make_opts(dtype=GLASS_F32, math=GLASS_MATH_FP32, layout=GLASS_LAYOUT_COLMAJOR, scope=GLASS_SCOPE_AUTO,
-              pack=0, refine_steps=0, fp64_diag=0, use_learned=0) -> glass_opts:
-    return glass_opts(dtype, math, layout, glass_placement(scope, pack), refine_steps, fp64_diag, use_learned)
+              pack=0, refine_steps=0, fp64_diag=0, use_learned=0, residual=GLASS_RESIDUAL_FP64) -> glass_opts:
+    return glass_opts(dtype, math, layout, glass_placement(scope, pack), refine_steps, fp64_diag, use_learned,
+                      residual)
 
 
 _lock = threading.Lock()

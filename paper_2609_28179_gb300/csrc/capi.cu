@@ -41,7 +41,8 @@ unsigned *device_status_word() {
 
 namespace {
 
-const glass_opts kDefaultOpts = {GLASS_F32, GLASS_MATH_FP32, GLASS_LAYOUT_COLMAJOR, {GLASS_SCOPE_AUTO, 0}, 0, 0, 0};
+const glass_opts kDefaultOpts = {GLASS_F32, GLASS_MATH_FP32, GLASS_LAYOUT_COLMAJOR, {GLASS_SCOPE_AUTO, 0}, 0, 0, 0,
+                                  GLASS_RESIDUAL_FP64};
 
 const glass_opts &opts_or_default(const glass_opts *o) { return o ? *o : kDefaultOpts; }
 
@@ -406,8 +407,8 @@ glass_status glass_batched_potrf(int n, void *A, int lda, long long sA, int *inf
     if (!operand_ok(A, lda, sA, n, n, true, o.layout) || info == nullptr) return GLASS_ERR_INVALID_VALUE;
     Placement pl;
     GLASS_TRY(placement_of(GLASS_OP_POTRF, n, 1, batch, o, pl));
-    return from_cuda(launch_potrf(n, make_mat(A, lda, sA, n, n, o.layout), info, batch, pl, o.fp64_diag,
-                                  reinterpret_cast<cudaStream_t>(stream)));
+    return from_cuda(launch_potrf(n, make_mat(A, lda, sA, n, n, o.layout), info, batch, pl,
+                                  o.fp64_diag ? NUM_FP64_DIAG : 0, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 glass_status glass_batched_potrs(int n, int nrhs, const void *L, int lda, long long sA, void *B, int ldb, long long sB,
@@ -443,6 +444,7 @@ glass_status glass_batched_posv(int n, int nrhs, void *A, int lda, long long sA,
     GLASS_TRY(check_order(n));
     if (nrhs < 0 || batch < 0) return GLASS_ERR_INVALID_VALUE;
     if (o.refine_steps < 0 || o.refine_steps > 1) return GLASS_ERR_UNSUPPORTED;
+    if (o.residual != GLASS_RESIDUAL_FP64 && o.residual != GLASS_RESIDUAL_DOT2) return GLASS_ERR_INVALID_VALUE;
     if (batch == 0) return GLASS_OK;
     if (o.dtype == GLASS_F64) {
         if (o.refine_steps != 0) return GLASS_ERR_UNSUPPORTED;
@@ -461,9 +463,11 @@ glass_status glass_batched_posv(int n, int nrhs, void *A, int lda, long long sA,
     GLASS_TRY(placement_of(GLASS_OP_POSV, n, nrhs > 0 ? nrhs : 1, batch, o, pl));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (nrhs == 0)
-        return from_cuda(launch_potrf(n, make_mat(A, lda, sA, n, n, o.layout), info, batch, pl, o.fp64_diag, st));
+        return from_cuda(launch_potrf(n, make_mat(A, lda, sA, n, n, o.layout), info, batch, pl,
+                                      o.fp64_diag ? NUM_FP64_DIAG : 0, st));
+    const int num = (o.fp64_diag ? NUM_FP64_DIAG : 0) | (o.residual == GLASS_RESIDUAL_DOT2 ? NUM_DOT2_RESIDUAL : 0);
     return from_cuda(launch_posv(n, nrhs, make_mat(A, lda, sA, n, n, o.layout), make_mat(B, ldb, sB, n, nrhs, o.layout),
-                                 info, batch, pl, o.fp64_diag, o.refine_steps, st));
+                                 info, batch, pl, num, o.refine_steps, st));
 }
 
 glass_status glass_batched_trsm(int n, int nrhs, const void *L, int lda, long long sA, void *B, int ldb, long long sB,

@@ -227,6 +227,47 @@ __device__ __forceinline__ void chol_diag(float d, bool fp64, float &l, float &r
     }
 }
 
+// Numerics flags of the Cholesky launchers and kernels (the `num` argument):
+// the FP64-accurate diagonal, and the compensated FP32 refinement residual
+// instead of the FP64 one.
+constexpr int NUM_FP64_DIAG = 1;
+constexpr int NUM_DOT2_RESIDUAL = 2;
+
+// Compensated accumulation of s = b - sum_k a_k x_k in FP32 (Ogita, Rump and
+// Oishi, "Accurate sum and dot product", 2005, algorithm Dot2): each product
+// is split exactly into p + e (p = fl(a x), e = fma(a, x, -p): Dekker's
+// TwoProduct with a fused multiply-add) and each addition into t + q
+// (Knuth's TwoSum, six additions, no branch); the errors e and q are summed
+// in c, and s + c carries the result as if computed in twice the working
+// precision.  The _rn intrinsics keep the compiler from contracting the
+// products and sums into fused multiply-adds, which would lose the exact
+// splits.
+struct Dot2 {
+    float s, c;
+    __device__ __forceinline__ void init(float b) {
+        s = b;
+        c = 0.f;
+    }
+    __device__ __forceinline__ void sub(float a, float x) {  // s -= a x
+        const float p = __fmul_rn(-a, x);
+        const float e = fmaf(-a, x, -p);
+        const float t = __fadd_rn(s, p);
+        const float z = __fadd_rn(t, -s);
+        const float q = __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -z)), __fadd_rn(p, -z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(q, e));
+    }
+    // Merges another partial sum (TwoSum of the leading parts).
+    __device__ __forceinline__ void merge(const Dot2 &o) {
+        const float t = __fadd_rn(s, o.s);
+        const float z = __fadd_rn(t, -s);
+        const float q = __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -z)), __fadd_rn(o.s, -z));
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, o.c), q);
+    }
+    __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+};
+
 // FP32 -> FP64 conversion on the integer pipe, without branches: for a
 // normal value the sign moves to bit 63, the 8-bit exponent is rebiased from
 // 127 to 1023 and the 23-bit fraction becomes the top of the 52-bit one
@@ -266,12 +307,12 @@ struct Geometry {
 // --------------------------------------------------- launchers (by file)
 // Each returns cudaSuccess or the launch error; none allocates or syncs.
 // k_chol.cu
-cudaError_t launch_potrf(int n, Mat A, int *info, int batch, Placement pl, int fp64diag,
+cudaError_t launch_potrf(int n, Mat A, int *info, int batch, Placement pl, int num,
                          cudaStream_t st);
 cudaError_t launch_potrs(int n, int nrhs, Mat L, Mat B, int batch, Placement pl, cudaStream_t st);
 cudaError_t launch_trsm(int n, int nrhs, Mat L, Mat B, int batch, Placement pl, cudaStream_t st);
 cudaError_t launch_posv(int n, int nrhs, Mat A, Mat B, int *info, int batch, Placement pl,
-                        int fp64diag, int refine, cudaStream_t st);
+                        int num, int refine, cudaStream_t st);  // num: NUM_* flags
 size_t smem_chol(int op, int n, int nrhs, Placement pl);
 bool feasible_chol(int op, int n, int nrhs, Placement pl);
 // k_lu.cu

@@ -1,5 +1,6 @@
 // k_chol_impl.cuh -- batched potrf / potrs / trsm / posv kernels at thread, warp
-// and block scope, plus the FP64-residual refinement step of posv.
+// and block scope, plus the refinement step of posv (FP64 or compensated
+// FP32 residual).
 //
 // Each kernel wraps a device primitive of dev_chol.cuh with the batched
 // load / compute / store of one placement (scope x pack, Sec. III-A).  Thread
@@ -37,7 +38,7 @@ enum ThreadMode { TM_STAGE = 0, TM_DIRECT = 1, TM_LAYOUT = 2 };
 
 template <int OP, int NMAX, bool EXACT, bool REFINE>
 __global__ void __launch_bounds__(256) k_chol_thread(int n_rt, int nrhs, Mat A, Mat B, int *info,
-                                                     int batch, int fp64diag, int mode) {
+                                                     int batch, int num, int mode) {
     extern __shared__ float smem[];
     using TR = Tri<NMAX>;
     const int n = EXACT ? NMAX : n_rt;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256) k_chol_thread(int n_rt, int nrhs, Mat A, 
                     a[TR::idx(i, j)] = (i < n) ? (staged ? pa[j * n + i] : A.get(b, i, j)) : 0.f;
         }
         if (has_factor(OP)) {
-            const int inf = thread::potrf<NMAX, EXACT>(a, dinv, n, fp64diag != 0);
+            const int inf = thread::potrf<NMAX, EXACT>(a, dinv, n, (num & NUM_FP64_DIAG) != 0);
             info[b] = inf;
         } else {
 #pragma unroll
@@ -117,22 +118,33 @@ __global__ void __launch_bounds__(256) k_chol_thread(int n_rt, int nrhs, Mat A, 
                 thread::forward<NMAX, EXACT>(a, dinv, x, n);
                 if (OP != C_TRSM) thread::backward_t<NMAX, EXACT>(a, dinv, x, n);
                 if (REFINE) {
-                    // r = b - A x0 in FP64 (A and b are still pristine in the
-                    // staging buffers / in global memory).
+                    // r = b - A x0 in FP64 or as a compensated FP32 dot
+                    // product (A and b are still pristine in the staging
+                    // buffers / in global memory).
                     float r[NMAX];
+                    const bool dot2 = (num & NUM_DOT2_RESIDUAL) != 0;
 #pragma unroll
                     for (int i = 0; i < NMAX; ++i) {
                         if (i < n) {
-                            double acc = staged ? (double)pb[c * n + i] : (double)B.get(b, i, c);
+                            const float bi = staged ? pb[c * n + i] : B.get(b, i, c);
+                            auto aik = [&](int k) {
+                                return (k <= i) ? (staged ? pa[k * n + i] : A.get(b, i, k))
+                                                : (staged ? pa[i * n + k] : A.get(b, k, i));
+                            };
+                            if (dot2) {
+                                Dot2 d;
+                                d.init(bi);
 #pragma unroll
-                            for (int k = 0; k < NMAX; ++k) {
-                                if (k < n) {
-                                    const float aik = (k <= i) ? (staged ? pa[k * n + i] : A.get(b, i, k))
-                                                               : (staged ? pa[i * n + k] : A.get(b, k, i));
-                                    acc = fma(-(double)aik, (double)x[k], acc);
-                                }
+                                for (int k = 0; k < NMAX; ++k)
+                                    if (k < n) d.sub(aik(k), x[k]);
+                                r[i] = d.value();
+                            } else {
+                                double acc = (double)bi;
+#pragma unroll
+                                for (int k = 0; k < NMAX; ++k)
+                                    if (k < n) acc = fma(-(double)aik(k), (double)x[k], acc);
+                                r[i] = (float)acc;
                             }
-                            r[i] = (float)acc;
                         } else {
                             r[i] = 0.f;
                         }
@@ -208,7 +220,7 @@ __global__ void __launch_bounds__(256) k_chol_thread(int n_rt, int nrhs, Mat A, 
 // column buffer per warp.
 template <int OP, int NMAX, bool REFINE>
 __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_chol_warp(int n, int nrhs, Mat A, Mat B, int *info, int batch,
-                                                   int fp64diag) {
+                                                   int num) {
     constexpr int R = warp::Rows<NMAX>::R;
     constexpr int AP = NMAX + 1;  // odd pitch of the refinement copy of A
     extern __shared__ __align__(16) float smem[];
@@ -228,7 +240,7 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
             if (REFINE && k < n && i < n && k <= i) As[k * AP + i] = a[q][k];
         }
     if (has_factor(OP)) {
-        const int inf = warp::potrf<NMAX>(a, rd, n, fp64diag != 0, col);
+        const int inf = warp::potrf<NMAX>(a, rd, n, (num & NUM_FP64_DIAG) != 0, col);
         if (lane == 0) info[b] = inf;
     } else {
 #pragma unroll
@@ -252,38 +264,69 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
             warp::forward<NMAX>(a, rd, x, n);
             if (OP != C_TRSM) warp::backward_t<NMAX>(a, rd, x, n);
             if (REFINE) {
-                // r_i = b_i - sum_k a_ik x_k in FP64 from the original A kept
-                // in shared memory (lower triangle, odd pitch: conflict free).
-                // four independent partial sums per row hide the FP64 latency
-                double acc[R][4];
+                // r_i = b_i - sum_k a_ik x_k from the original A kept in
+                // shared memory (lower triangle, odd pitch: conflict free):
+                // in FP64 with four independent partial sums per row (they
+                // hide the FP64 latency), or as two compensated FP32 sums.
+                float r[R];
+                auto xk_of = [&](int k) {
+                    float xk = 0.f;
 #pragma unroll
-                for (int q = 0; q < R; ++q) {
-                    const int i = lane + 32 * q;
-                    acc[q][0] = (i < n) ? (double)B.cget(b, i, c) : 0.0;
-                    acc[q][1] = acc[q][2] = acc[q][3] = 0.0;
-                }
+                    for (int q = 0; q < R; ++q) {
+                        const float v = __shfl_sync(GLASS_FULL_MASK, x[q], k & 31);
+                        if ((k >> 5) == q) xk = v;
+                    }
+                    return xk;
+                };
+                if ((num & NUM_DOT2_RESIDUAL) != 0) {
+                    Dot2 d[R][2];
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        const int i = lane + 32 * q;
+                        d[q][0].init((i < n) ? B.cget(b, i, c) : 0.f);
+                        d[q][1].init(0.f);
+                    }
 #pragma unroll 4
-                for (int k = 0; k < NMAX; ++k) {
-                    if (k < n) {
-                        float xk = 0.f;
+                    for (int k = 0; k < NMAX; ++k) {
+                        if (k < n) {
+                            const float xk = xk_of(k);
 #pragma unroll
-                        for (int q = 0; q < R; ++q) {
-                            const float v = __shfl_sync(GLASS_FULL_MASK, x[q], k & 31);
-                            if ((k >> 5) == q) xk = v;
-                        }
-#pragma unroll
-                        for (int q = 0; q < R; ++q) {
-                            const int i = lane + 32 * q;
-                            if (i < n) {
-                                const float aik = (k <= i) ? As[k * AP + i] : As[i * AP + k];
-                                acc[q][k & 3] = fma(-(double)aik, (double)xk, acc[q][k & 3]);
+                            for (int q = 0; q < R; ++q) {
+                                const int i = lane + 32 * q;
+                                if (i < n) d[q][k & 1].sub((k <= i) ? As[k * AP + i] : As[i * AP + k], xk);
                             }
                         }
                     }
-                }
-                float r[R];
 #pragma unroll
-                for (int q = 0; q < R; ++q) r[q] = (float)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]));
+                    for (int q = 0; q < R; ++q) {
+                        d[q][0].merge(d[q][1]);
+                        r[q] = d[q][0].value();
+                    }
+                } else {
+                    double acc[R][4];
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        const int i = lane + 32 * q;
+                        acc[q][0] = (i < n) ? (double)B.cget(b, i, c) : 0.0;
+                        acc[q][1] = acc[q][2] = acc[q][3] = 0.0;
+                    }
+#pragma unroll 4
+                    for (int k = 0; k < NMAX; ++k) {
+                        if (k < n) {
+                            const float xk = xk_of(k);
+#pragma unroll
+                            for (int q = 0; q < R; ++q) {
+                                const int i = lane + 32 * q;
+                                if (i < n) {
+                                    const float aik = (k <= i) ? As[k * AP + i] : As[i * AP + k];
+                                    acc[q][k & 3] = fma(-(double)aik, (double)xk, acc[q][k & 3]);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < R; ++q) r[q] = (float)((acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]));
+                }
                 warp::forward<NMAX>(a, rd, r, n);
                 warp::backward_t<NMAX>(a, rd, r, n);
 #pragma unroll
@@ -308,30 +351,88 @@ __global__ void __launch_bounds__(256, NMAX <= 16 ? 3 : (NMAX == 32 ? 2 : 1)) k_
     }
 }
 
-// Per-warp shared memory (floats) of k_chol_tc: A, 1/l_jj, two 16-float
-// broadcast segments, and (RF) the first solution of the refinement step as
-// NMAX doubles.
-template <int NMAX, bool RF = false>
+// Per-warp shared memory (floats) of k_chol_tc: A, 1/l_jj and two 16-float
+// broadcast segments.  The refinement step keeps the first solution in the
+// padding rows NMAX..NMAX+7 of A's first columns (rows no kernel step
+// touches), so refinement costs no shared memory and no resident warps.
+template <int NMAX>
 constexpr int tc_floats() {
-    return NMAX * tcwarp::Shape<NMAX>::LD + NMAX + 32 + (RF ? 2 * NMAX : 0);
+    return NMAX * tcwarp::Shape<NMAX>::LD + NMAX + 32;
 }
 
-// r = b - A x in FP64 for one right-hand side of the tensor-core posv: A
-// the ORIGINAL symmetric operand in global memory (lower triangle, still
-// intact: the factor is written back last), x widened to FP64 in shared
-// memory (xd, NMAX doubles, zero beyond n), lane rows i = lane + 32 q.  One
-// step per column k, every lane busy: a_ik is read from column k below its
-// diagonal (coalesced over the lanes) or, above it, as a_ki from the row's
-// own column; x_k is a shared-memory broadcast.  The FP64 pipe does n fused
-// multiply-adds per row (two partial sums each) and, in the 64-row kernel,
-// the widening of A's entries (the 32-row kernel widens them on the integer
-// pipe, f2d_bits).
+// x_k of the refinement in A's padding: as a double (four per column) for
+// the FP64 residual, as a float (eight per column) for the compensated one.
 template <int NMAX>
-__device__ __forceinline__ void residual_f64(const float *ga, long long lda, const double *xd,
+__device__ __forceinline__ double *xpad_d(float *As, int k) {
+    return reinterpret_cast<double *>(As + (k >> 2) * tcwarp::Shape<NMAX>::LD + NMAX) + (k & 3);
+}
+template <int NMAX>
+__device__ __forceinline__ float *xpad_f(float *As, int k) {
+    return As + (k >> 3) * tcwarp::Shape<NMAX>::LD + NMAX + (k & 7);
+}
+
+// The entries a_ik of the ORIGINAL symmetric operand in global memory (lower
+// triangle, still intact: the factor is written back last) for the lane's
+// rows i = lane + 32 q and the CW columns k0..k0+CW-1, all loads issued before
+// any is used (the residual waits on these loads, not on its arithmetic):
+// below the diagonal from column k (coalesced over the lanes), above it as
+// a_ki from the row's own column; zero outside the order.
+template <int R, int CW>
+__device__ __forceinline__ void residual_chunk(const float *ga, long long lda, int n, int k0, float (&av)[R][CW]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int kk = 0; kk < CW; ++kk)
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = lane + 32 * q, k = k0 + kk;
+            av[q][kk] = (i < n && k < n) ? (i >= k ? ga[(long long)k * lda + i] : ga[(long long)i * lda + k]) : 0.f;
+        }
+}
+
+// Runs use(av, k0) over the column chunks of the residual (CW = kResCW<NMAX>
+// columns).  The 64-row kernel keeps the loads of the next 8-column chunk in
+// flight while a chunk is used (two register buffers; refined posv n = 64
+// at batch 16384: 536 -> 519 us with the FP64 residual, 445 -> 425 us with
+// the compensated one); the 32-row kernel loads 16 columns at a time into
+// one buffer (the second buffer cost it resident warps: 113 -> 131 us).
+// k0 < n <= NMAX, so every chunk used lies inside the operand's columns,
+// and a chunk past n is never loaded.
+template <int NMAX>
+constexpr int kResCW = NMAX == 64 ? 8 : 16;
+template <int NMAX, typename Use>
+__device__ __forceinline__ void residual_pipeline(const float *ga, long long lda, int n, Use use) {
+    constexpr int R = tcwarp::Shape<NMAX>::R, CW = kResCW<NMAX>;
+    float a0[R][CW];
+    if constexpr (NMAX == 64) {
+        float a1[R][CW];
+        residual_chunk<R, CW>(ga, lda, n, 0, a0);
+        for (int k0 = 0; k0 < n; k0 += 2 * CW) {
+            const bool second = k0 + CW < n;
+            if (second) residual_chunk<R, CW>(ga, lda, n, k0 + CW, a1);
+            use(a0, k0);
+            if (second) {
+                if (k0 + 2 * CW < n) residual_chunk<R, CW>(ga, lda, n, k0 + 2 * CW, a0);
+                use(a1, k0 + CW);
+            }
+        }
+    } else {
+        for (int k0 = 0; k0 < n; k0 += CW) {
+            residual_chunk<R, CW>(ga, lda, n, k0, a0);
+            use(a0, k0);
+        }
+    }
+}
+
+// r = b - A x in FP64 for one right-hand side of the tensor-core posv (lane
+// rows i = lane + 32 q, x_k from A's padding as FP64): n fused multiply-adds
+// per row in two partial sums, and, in the 64-row kernel, the widening of
+// A's entries on the FP64 pipe (the 32-row kernel widens them on the
+// integer pipe, f2d_bits).
+template <int NMAX>
+__device__ __forceinline__ void residual_f64(const float *ga, long long lda, float *As,
                                              const float (&bq)[tcwarp::Shape<NMAX>::R], int n,
                                              float (&r)[tcwarp::Shape<NMAX>::R]) {
     constexpr int R = tcwarp::Shape<NMAX>::R;
-    const int lane = threadIdx.x & 31;
     double acc[R][2];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
@@ -342,52 +443,72 @@ __device__ __forceinline__ void residual_f64(const float *ga, long long lda, con
     // (refined solve at batch 16384: 128 vs 155 us) and slower for the
     // 64-row one (731 vs 605 us), which keeps the hardware conversion.
     auto widen = [](float a) { return NMAX == 32 ? f2d_bits(a) : (double)a; };
-    auto step = [&](int k, int s) {
-        const double xk = xd[k];
+    residual_pipeline<NMAX>(ga, lda, n, [&](const float (&av)[R][kResCW<NMAX>], int k0) {
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int i = lane + 32 * q;
-            if (i < n) {
-                const float aik = i >= k ? ga[(long long)k * lda + i] : ga[(long long)i * lda + k];
-                acc[q][s] = fma(-widen(aik), xk, acc[q][s]);
-            }
+        for (int kk = 0; kk < kResCW<NMAX>; ++kk) {
+            const double xk = *xpad_d<NMAX>(As, k0 + kk);  // zero beyond n
+#pragma unroll
+            for (int q = 0; q < R; ++q) acc[q][kk & 1] = fma(-widen(av[q][kk]), xk, acc[q][kk & 1]);
         }
-    };
-    int k = 0;
-#pragma unroll 4
-    for (; k + 1 < n; k += 2) {
-        step(k, 0);
-        step(k + 1, 1);
-    }
-    if (k < n) step(k, 0);
+    });
 #pragma unroll
     for (int q = 0; q < R; ++q) r[q] = (float)(acc[q][0] + acc[q][1]);
+}
+
+// The same residual as a compensated FP32 dot product (Dot2), x_k from A's
+// padding as FP32, two partial sums per row merged at the end: about ten
+// FP32 operations per term on the wide FP32 pipe instead of a widening and
+// a fused multiply-add on the FP64 one.
+template <int NMAX>
+__device__ __forceinline__ void residual_dot2(const float *ga, long long lda, float *As,
+                                              const float (&bq)[tcwarp::Shape<NMAX>::R], int n,
+                                              float (&r)[tcwarp::Shape<NMAX>::R]) {
+    constexpr int R = tcwarp::Shape<NMAX>::R;
+    Dot2 d[R][2];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        d[q][0].init(bq[q]);
+        d[q][1].init(0.f);
+    }
+    residual_pipeline<NMAX>(ga, lda, n, [&](const float (&av)[R][kResCW<NMAX>], int k0) {
+#pragma unroll
+        for (int kk = 0; kk < kResCW<NMAX>; ++kk) {
+            const float xk = *xpad_f<NMAX>(As, k0 + kk);  // zero beyond n
+#pragma unroll
+            for (int q = 0; q < R; ++q) d[q][kk & 1].sub(av[q][kk], xk);
+        }
+    });
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        d[q][0].merge(d[q][1]);
+        r[q] = d[q][0].value();
+    }
 }
 
 // Warp scope, orders 17..64: blocked Cholesky with tensor-core trailing
 // updates (dev_chol_tc.cuh) on the problem held in the warp's shared memory;
 // the solves run against L in shared memory.  RF: one refinement step per
-// right-hand side -- r = b - A x0 in FP64 from the original A (still intact
-// in global memory: the factor is written back last), dx = A^{-1} r with
+// right-hand side -- r = b - A x0 in FP64 (or as a compensated FP32 dot
+// product) from the original A (still intact in global memory: the factor
+// is written back last), dx = A^{-1} r with
 // the factor, x1 = x0 + dx.  (A shared-memory copy of A halves the resident
-// warps and measured slower: the residual is bound by the FP64 pipe.)
+// warps and measured slower.)
 // Orders 17..32 without refinement cap the registers at 64, so 32 warps fit
 // on an SM instead of 28 (posv n = 32 at batch 16384: 60 -> 58 us).
 template <int OP, int NMAX, bool RF>
-__global__ void __launch_bounds__(256, NMAX == 32 && !RF ? 4 : 1) k_chol_tc(int n, int nrhs, Mat A, Mat B, int *info, int batch, int fp64diag) {
+__global__ void __launch_bounds__(256, NMAX == 32 && !RF ? 4 : 1) k_chol_tc(int n, int nrhs, Mat A, Mat B, int *info, int batch, int num) {
     constexpr int LD = tcwarp::Shape<NMAX>::LD;
     constexpr int R = tcwarp::Shape<NMAX>::R;
     extern __shared__ __align__(16) float smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *As = smem + w * tc_floats<NMAX, RF>();
+    float *As = smem + w * tc_floats<NMAX>();
     float *dv = As + NMAX * LD;
     float *bc = dv + NMAX;
-    double *xd = reinterpret_cast<double *>(bc + 32);  // NMAX doubles (RF), 16-byte aligned
     const int b = blockIdx.x * (blockDim.x >> 5) + w;
     if (b >= batch) return;  // whole warp
     tcwarp::stage_async<NMAX, true>(As, A.p + (long long)b * A.s, A.ld, n);
     tcwarp::wait_first();  // the first panel starts while columns 16.. arrive
-    const int inf = tcwarp::potrf<NMAX>(As, n, dv, bc, fp64diag != 0);
+    const int inf = tcwarp::potrf<NMAX>(As, n, dv, bc, (num & NUM_FP64_DIAG) != 0);
     if (lane == 0) info[b] = inf;
     if (has_rhs(OP)) {
         for (int c = 0; c < nrhs; ++c) {
@@ -402,12 +523,19 @@ __global__ void __launch_bounds__(256, NMAX == 32 && !RF ? 4 : 1) k_chol_tc(int 
             for (int q = 0; q < R; ++q) bq[q] = x[q];
             tcwarp::potrs<NMAX>(As, dv, x, n);
             if constexpr (RF) {
-#pragma unroll
-                for (int q = 0; q < R; ++q) xd[lane + 32 * q] = (double)x[q];  // rows >= n hold 0
-                __syncwarp();
                 float r[R];
-                residual_f64<NMAX>(A.p + (long long)b * A.s, A.ld, xd, bq, n, r);
-                __syncwarp();  // xd is rewritten for the next right-hand side
+                if ((num & NUM_DOT2_RESIDUAL) != 0) {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) *xpad_f<NMAX>(As, lane + 32 * q) = x[q];  // rows >= n hold 0
+                    __syncwarp();
+                    residual_dot2<NMAX>(A.p + (long long)b * A.s, A.ld, As, bq, n, r);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < R; ++q) *xpad_d<NMAX>(As, lane + 32 * q) = (double)x[q];
+                    __syncwarp();
+                    residual_f64<NMAX>(A.p + (long long)b * A.s, A.ld, As, bq, n, r);
+                }
+                __syncwarp();  // x is rewritten for the next right-hand side
                 tcwarp::potrs<NMAX>(As, dv, r, n);
 #pragma unroll
                 for (int q = 0; q < R; ++q) x[q] += r[q];
@@ -551,8 +679,9 @@ __global__ void __launch_bounds__(256, 1) k_solve_cols(int n, int nrhs, Mat L, M
 // ------------------------------------------------------------- block scope
 // Row team (dev_rows.cuh): 64 threads per problem, thread i owns row i,
 // right-hand sides handled RS = 4 at a time.  The refinement residual
-// r = b - A x0 is formed in FP64 from A re-read in global memory (L is
-// written back last) and the solved x broadcast through shared memory.
+// r = b - A x0 is formed in FP64 (or as a compensated FP32 dot product) from
+// A re-read in global memory (L is written back last) and the solved x
+// broadcast through shared memory.
 constexpr int kRSmax = 4;
 
 template <int NMAX>
@@ -562,7 +691,7 @@ constexpr int rows_team_floats() {
 
 template <int OP, int NMAX, bool REFINE, int kRS>
 __global__ void __launch_bounds__(256, 1) k_chol_rows(int n, int nrhs, Mat A, Mat B, int *info, int batch,
-                                                   int fp64diag) {
+                                                   int num) {
     extern __shared__ __align__(16) float smem[];
     const int team = threadIdx.x / rows::T, i = threadIdx.x % rows::T;
     const int b = blockIdx.x * (blockDim.x / rows::T) + team;
@@ -574,7 +703,7 @@ __global__ void __launch_bounds__(256, 1) k_chol_rows(int n, int nrhs, Mat A, Ma
     float a[NMAX];
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) a[k] = (k < n && i < n && k <= i) ? A.cget(b, i, k) : 0.f;
-    const int inf = rows::potrf<NMAX, kRS>(a, n, i, fp64diag != 0, s, bid);
+    const int inf = rows::potrf<NMAX, kRS>(a, n, i, (num & NUM_FP64_DIAG) != 0, s, bid);
     if (i == 0) info[b] = inf;
     if (has_rhs(OP)) {
         for (int c0 = 0; c0 < nrhs; c0 += kRS) {
@@ -589,15 +718,26 @@ __global__ void __launch_bounds__(256, 1) k_chol_rows(int n, int nrhs, Mat A, Ma
                     for (int c = 0; c < kRS; ++c) xall[i * kRS + c] = x[c];
                 rows::bar(bid);
                 float r[kRS];
+                const bool dot2 = (num & NUM_DOT2_RESIDUAL) != 0;
 #pragma unroll
                 for (int c = 0; c < kRS; ++c) {
-                    double acc = (i < n && c0 + c < nrhs) ? (double)B.cget(b, i, c0 + c) : 0.0;
-                    if (i < n)
-                        for (int k = 0; k < n; ++k) {
-                            const float aik = (k <= i) ? A.cget(b, i, k) : A.cget(b, k, i);
-                            acc = fma(-(double)aik, (double)xall[k * kRS + c], acc);
-                        }
-                    r[c] = (float)acc;
+                    const float bi = (i < n && c0 + c < nrhs) ? B.cget(b, i, c0 + c) : 0.f;
+                    if (dot2) {
+                        Dot2 d;
+                        d.init(bi);
+                        if (i < n)
+                            for (int k = 0; k < n; ++k)
+                                d.sub((k <= i) ? A.cget(b, i, k) : A.cget(b, k, i), xall[k * kRS + c]);
+                        r[c] = d.value();
+                    } else {
+                        double acc = (double)bi;
+                        if (i < n)
+                            for (int k = 0; k < n; ++k) {
+                                const float aik = (k <= i) ? A.cget(b, i, k) : A.cget(b, k, i);
+                                acc = fma(-(double)aik, (double)xall[k * kRS + c], acc);
+                            }
+                        r[c] = (float)acc;
+                    }
                 }
                 rows::forward<NMAX, kRS>(a, r, n, i, s, bid);
                 rows::backward_t<NMAX, kRS>(a, r, n, i, s, bid);
@@ -638,7 +778,7 @@ inline int nmax_bucket(int n) { return n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 
 // buckets (runtime order <= NMAX) for the rest.
 template <int OP, bool RF>
 cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, int pack,
-                            int fp64diag, cudaStream_t st) {
+                            int num, cudaStream_t st) {
     const int G = 32 * pack;
     const bool aligned = ((reinterpret_cast<uintptr_t>(A.p) | (has_rhs(OP) ? reinterpret_cast<uintptr_t>(B.p) : 0)) &
                           15) == 0;
@@ -654,7 +794,7 @@ cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *in
         mode == TM_STAGE ? (size_t)G * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4 : 0;
     const int grid = ceil_div(batch, G);
 #define GL_T(N, EX) \
-    launch_k(k_chol_thread<OP, N, EX, RF>, grid, G, smem, st, n, nrhs, A, B, info, batch, fp64diag, mode)
+    launch_k(k_chol_thread<OP, N, EX, RF>, grid, G, smem, st, n, nrhs, A, B, info, batch, num, mode)
     switch (n) {
         case 3: return GL_T(3, true);
         case 6: return GL_T(6, true);
@@ -673,8 +813,8 @@ cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *in
 
 // Shared memory of the blocked tensor-core Cholesky, per warp (bytes).
 inline size_t tc_smem(int n, bool rf = false) {
-    return (size_t)(n > 32 ? (rf ? tc_floats<64, true>() : tc_floats<64>())
-                           : (rf ? tc_floats<32, true>() : tc_floats<32>())) * 4;
+    (void)rf;  // the refinement step lives in A's padding
+    return (size_t)(n > 32 ? tc_floats<64>() : tc_floats<32>()) * 4;
 }
 
 // Shared memory of the many-right-hand-side solve kernels, per problem
@@ -716,7 +856,7 @@ cudaError_t solve_cols_dispatch(int n, int nrhs, const Mat &L, const Mat &B, int
 
 template <int OP, bool RF>
 cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, int pack,
-                          int fp64diag, cudaStream_t st) {
+                          int num, cudaStream_t st) {
     if constexpr (OP == C_TRSM) {
         return solve_cols_dispatch<32, false>(n, nrhs, A, B, batch, pack, st);
     } else {
@@ -725,16 +865,16 @@ cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info
                 const int grid = ceil_div(batch, pack);
                 if (n > 32)
                     return launch_k(k_chol_tc<OP, 64, RF>, grid, 32 * pack, tc_smem(n, RF) * pack, st, n, nrhs, A, B,
-                                    info, batch, fp64diag);
+                                    info, batch, num);
                 return launch_k(k_chol_tc<OP, 32, RF>, grid, 32 * pack, tc_smem(n, RF) * pack, st, n, nrhs, A, B, info,
-                                batch, fp64diag);
+                                batch, num);
             }
         }
         const int threads = 32 * pack;
         const int grid = ceil_div(batch, pack);
         const int N = nmax_bucket(n);
         const size_t sm = (size_t)pack * (N + (RF ? N * (N + 1) : 0)) * 4;
-#define GL_W(NN) launch_k(k_chol_warp<OP, NN, RF>, grid, threads, sm, st, n, nrhs, A, B, info, batch, fp64diag)
+#define GL_W(NN) launch_k(k_chol_warp<OP, NN, RF>, grid, threads, sm, st, n, nrhs, A, B, info, batch, num)
         switch (N) {
             case 8: return GL_W(8);
             case 16: return GL_W(16);
@@ -756,7 +896,7 @@ inline size_t rows_team_bytes(int n) {
 
 template <int OP, bool RF>
 cudaError_t block_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, int pack,
-                           int fp64diag, cudaStream_t st) {
+                           int num, cudaStream_t st) {
     if constexpr (OP == C_TRSM) {
         return solve_cols_dispatch<64, false>(n, nrhs, A, B, batch, pack, st);
     } else if constexpr (OP == C_POTRS) {
@@ -765,8 +905,8 @@ cudaError_t block_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *inf
         const size_t smem = rows_team_bytes(n) * pack;
         const int grid = ceil_div(batch, pack);
         const int th = rows::T * pack;
-#define GL_R(NN) (nrhs <= 1 ? launch_k(k_chol_rows<OP, NN, RF, 1>, grid, th, smem, st, n, nrhs, A, B, info, batch, fp64diag) \
-                         : launch_k(k_chol_rows<OP, NN, RF, 4>, grid, th, smem, st, n, nrhs, A, B, info, batch, fp64diag))
+#define GL_R(NN) (nrhs <= 1 ? launch_k(k_chol_rows<OP, NN, RF, 1>, grid, th, smem, st, n, nrhs, A, B, info, batch, num) \
+                         : launch_k(k_chol_rows<OP, NN, RF, 4>, grid, th, smem, st, n, nrhs, A, B, info, batch, num))
         switch (nmax_bucket(n)) {
             case 8: return GL_R(8);
             case 16: return GL_R(16);
@@ -804,20 +944,20 @@ bool feasible_of(int n, int nrhs, Placement pl, int refine) {
 }
 
 template <int OP>
-cudaError_t run(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, Placement pl, int fp64diag,
+cudaError_t run(int n, int nrhs, const Mat &A, const Mat &B, int *info, int batch, Placement pl, int num,
                 int refine, cudaStream_t st) {
     if (!feasible_of<OP>(n, nrhs, pl, refine)) return cudaErrorInvalidConfiguration;
     if constexpr (OP == C_POSV) {
         if (refine) switch (pl.scope) {
-            case SCOPE_THREAD: return thread_dispatch<OP, true>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
-            case SCOPE_WARP: return warp_dispatch<OP, true>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
-            default: return block_dispatch<OP, true>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
+            case SCOPE_THREAD: return thread_dispatch<OP, true>(n, nrhs, A, B, info, batch, pl.pack, num, st);
+            case SCOPE_WARP: return warp_dispatch<OP, true>(n, nrhs, A, B, info, batch, pl.pack, num, st);
+            default: return block_dispatch<OP, true>(n, nrhs, A, B, info, batch, pl.pack, num, st);
         }
     }
     switch (pl.scope) {
-        case SCOPE_THREAD: return thread_dispatch<OP, false>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
-        case SCOPE_WARP: return warp_dispatch<OP, false>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
-        default: return block_dispatch<OP, false>(n, nrhs, A, B, info, batch, pl.pack, fp64diag, st);
+        case SCOPE_THREAD: return thread_dispatch<OP, false>(n, nrhs, A, B, info, batch, pl.pack, num, st);
+        case SCOPE_WARP: return warp_dispatch<OP, false>(n, nrhs, A, B, info, batch, pl.pack, num, st);
+        default: return block_dispatch<OP, false>(n, nrhs, A, B, info, batch, pl.pack, num, st);
     }
 }
 

@@ -3,9 +3,9 @@
 #include "k_chol_impl.cuh"
 
 namespace glass {
-cudaError_t launch_posv(int n, int nrhs, Mat A, Mat B, int *info, int batch, Placement pl, int fp64diag,
+cudaError_t launch_posv(int n, int nrhs, Mat A, Mat B, int *info, int batch, Placement pl, int num,
                         int refine, cudaStream_t st) {
-    return run<C_POSV>(n, nrhs, A, B, info, batch, pl, fp64diag, refine, st);
+    return run<C_POSV>(n, nrhs, A, B, info, batch, pl, num, refine, st);
 }
 
 // op: GLASS_OP_POTRF / POTRS / TRSM / POSV

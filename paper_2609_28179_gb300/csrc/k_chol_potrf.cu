@@ -3,9 +3,9 @@
 #include "k_chol_impl.cuh"
 
 namespace glass {
-cudaError_t launch_potrf(int n, Mat A, int *info, int batch, Placement pl, int fp64diag, cudaStream_t st) {
+cudaError_t launch_potrf(int n, Mat A, int *info, int batch, Placement pl, int num, cudaStream_t st) {
     Mat none = A;
-    return run<C_POTRF>(n, 0, A, none, info, batch, pl, fp64diag, 0, st);
+    return run<C_POTRF>(n, 0, A, none, info, batch, pl, num, 0, st);
 }
 
 }  // namespace glass

@@ -172,6 +172,14 @@ def test_fp64_storage_argument_rules(L):
     assert g.glass_batched_gemm(4, 4, 4, BAD, 4, 16, BAD, 4, 16, BAD, 4, 16, 4, o, 0) == g.GLASS_ERR_UNSUPPORTED
 
 
+def test_refinement_residual_option_is_validated(L):
+    for resid in (-1, 2, 7):
+        o = g.make_opts(refine_steps=1, residual=resid)
+        assert g.glass_batched_posv(6, 1, BAD, 6, 36, BAD, 6, 6, BAD, 4, o, 0) == g.GLASS_ERR_INVALID_VALUE
+    o = g.make_opts(refine_steps=1, residual=g.GLASS_RESIDUAL_DOT2)
+    assert g.glass_batched_posv(6, 1, BAD, 6, 36, BAD, 6, 6, BAD, 0, o, 0) == g.GLASS_OK   # empty batch
+
+
 def test_selftest_wait_timeout_rejects_bad_arguments(L):
     assert g.glass_selftest_wait_timeout(BAD, BAD, BAD, 4, 0, 0) == g.GLASS_ERR_INVALID_VALUE
     assert g.glass_selftest_wait_timeout(BAD, BAD, BAD, 4, (1 << 31) + 1, 0) == g.GLASS_ERR_INVALID_VALUE

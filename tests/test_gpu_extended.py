@@ -1,4 +1,4 @@
-"""Parity of the precision path (tensor-core GEMM, FP64-residual refinement),
+"""Parity of the precision path (tensor-core GEMM, FP64- and compensated-residual refinement),
 the mixed-size persistent posv, and the learned cost model's kernels against
 the FP64 oracle, through the C ABI."""
 import numpy as np
@@ -189,6 +189,42 @@ def test_refined_posv_improves_forward_error(n, kappa):
         f0, f1 = res[(0, 0)][0], res[(1, 0)][0]
         assert np.median(f1) <= np.median(f0), (n, kappa, scope, np.median(f0), np.median(f1))
         assert res[(1, 0)][1].max() <= res[(0, 0)][1].max() * 1.5 + 1e-7
+
+
+@pytest.mark.parametrize("n", [5, 16, 32, 64])
+@pytest.mark.parametrize("kappa", [1e1, 1e3, 1e6])
+def test_dot2_residual_matches_the_fp64_residual(n, kappa):
+    """The compensated FP32 residual (Dot2) is as accurate as one evaluated
+    in twice the FP32 precision, about 2^-48 |A||x| against 2^-53 n |A||x|
+    for FP64 accumulation: both are far below the FP32 rounding of x1, so
+    the refined solutions of the two residuals agree to a few FP32 units of
+    x1 at every conditioning, element by element -- and the Dot2 solve
+    keeps the FP64 one's accuracy against the oracle (forward error no
+    worse than the unrefined solve's, backward error within 1e-4)."""
+    batch = 96
+    A = W.kappa_spd(n, batch, kappa, 2460 + n)
+    b = W.gaussian(batch * n, 2461 + n)
+    _, Xs, _ = oracle.posv(n, 1, A.astype(np.float64), b.astype(np.float64), batch)
+    Am = mats(A, batch, n, n).astype(np.float64)
+    scopes = [(1, 1), (2, 1)] + ([(0, 1)] if n <= 16 else [])
+    for scope, pack in scopes:
+        X = {}
+        for resid in (g.GLASS_RESIDUAL_FP64, g.GLASS_RESIDUAL_DOT2):
+            dA, dB, info = to_dev(A), to_dev(b), zeros_i32(batch)
+            o = g.make_opts(scope=scope, pack=pack, refine_steps=1, residual=resid)
+            g.check(g.glass_batched_posv(n, 1, dA, n, n * n, dB, n, n, info, batch, o))
+            sync()
+            assert (host(info)[:batch] == 0).all()
+            X[resid] = host(dB).reshape(batch, n).astype(np.float64)
+        x64, xd2 = X[g.GLASS_RESIDUAL_FP64], X[g.GLASS_RESIDUAL_DOT2]
+        scale = np.abs(x64).max(1, keepdims=True)
+        assert (np.abs(xd2 - x64) <= 8 * 2.0 ** -24 * scale).all(), (n, kappa, scope, np.abs(xd2 - x64).max())
+        be = backward_error(Am, xd2.reshape(batch, n, 1), mats(b, batch, n, 1).astype(np.float64))
+        assert be.max() <= 1e-4, (n, kappa, scope, be.max())
+        Xs2 = Xs.reshape(batch, n)
+        f64 = np.abs(x64 - Xs2).max(1) / np.abs(Xs2).max(1)
+        fd2 = np.abs(xd2 - Xs2).max(1) / np.abs(Xs2).max(1)
+        assert np.median(fd2) <= 1.5 * np.median(f64) + 1e-7, (n, kappa, scope, np.median(f64), np.median(fd2))
 
 
 def test_fp64_diag_reciprocal_is_the_rounded_fp64_value():
