@@ -8,11 +8,14 @@
 //
 // Work split: n/16 warps per product, warp w owns rows 16w .. 16w+15 of C
 // and every 8-column block, so one A fragment serves n/8 MMAs.  A CTA holds
-// 4 warps (4/(n/16) products).  Operands are staged into shared memory with
+// 4 warps (4/(n/16) products); the TF32 modes of order 16 run a persistent
+// streaming form instead (one warp per product, next product prefetched).  Operands are staged into shared memory with
 // coalesced 16-byte streaming loads, in padded layouts whose leading
 // dimensions make every fragment load bank-conflict free; C goes back
 // through shared memory for coalesced 16-byte stores.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "dev_umma.cuh"
@@ -130,6 +133,94 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(const float *__restrict__ A, 
         for (int v = threadIdx.x; v < N * N / 4; v += blockDim.x) {
             const int col = (4 * v) / N, row = (4 * v) % N;
             __stcs(gc + v, *reinterpret_cast<const float4 *>(cs + col * S::LDC + row));
+        }
+    }
+}
+
+// ------------------------------------------------------- TF32, order 16
+// Persistent streaming form for n = 16 (one warp per product, 3 KB of HBM
+// traffic against 12 KFLOP: a stream, not a contraction): each warp walks
+// the batch with a stride of the grid's warp count; the next product's A
+// and B are copied by cp.async into the warp's second buffer while the
+// current one is multiplied, so no barrier stands between a load and its
+// use.  C leaves straight from the accumulator fragments (lanes g = 0..7 of
+// a fragment row cover one 32-byte column segment: whole sectors).
+constexpr int kS16 = 16, kS16LDA = 24, kS16LDB = 20;  // conflict-free fragment loads
+constexpr int kS16Buf = kS16 * kS16LDA + kS16 * kS16LDB;  // floats per buffer
+constexpr int kS16Warps = 8;                              // warps per CTA
+constexpr int kS16Ctas = 5;                               // resident CTAs per SM (45 KB of shared memory each)
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(32 * kS16Warps) k_gemm_tf32_stream16(const float *__restrict__ A,
+                                                                   const float *__restrict__ B,
+                                                                   float *__restrict__ C, int batch) {
+    extern __shared__ __align__(16) float smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    float *buf = smem + warp * 2 * kS16Buf;
+    const int stride = gridDim.x * kS16Warps;
+    // lane's 16-byte chunks of one operand: columns lane / 4 and lane / 4 + 8, rows 4 (lane % 4)
+    const int c0 = lane >> 2, r0 = 4 * (lane & 3);
+    auto issue = [&](int b, float *dst) {
+        const float *ga = A + (long long)b * 256, *gb = B + (long long)b * 256;
+        float *As = dst, *Bs = dst + kS16 * kS16LDA;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = c0 + 8 * h;
+            cp_async16(As + c * kS16LDA + r0, ga + c * 16 + r0);
+            cp_async16(Bs + c * kS16LDB + r0, gb + c * 16 + r0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    int b = blockIdx.x * kS16Warps + warp;
+    if (b >= batch) return;  // whole warp
+    issue(b, buf);
+    for (int it = 0; b < batch; b += stride, ++it) {
+        float *cur = buf + (it & 1) * kS16Buf;
+        const int nb = b + stride;
+        if (nb < batch) {
+            issue(nb, buf + ((it + 1) & 1) * kS16Buf);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncwarp();
+        const float *As = cur, *Bs = cur + kS16 * kS16LDA;
+        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int k0 = 0; k0 < 16; k0 += 8) {
+            float af[4];
+            af[0] = As[(k0 + t) * kS16LDA + g];
+            af[1] = As[(k0 + t) * kS16LDA + g + 8];
+            af[2] = As[(k0 + t + 4) * kS16LDA + g];
+            af[3] = As[(k0 + t + 4) * kS16LDA + g + 8];
+            unsigned ah[4], al[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ah[u] = tf32_rna(af[u]);
+                if (SPLIT) al[u] = tf32_rna(af[u] - __uint_as_float(ah[u]));
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float b0v = Bs[(8 * j + g) * kS16LDB + k0 + t], b1v = Bs[(8 * j + g) * kS16LDB + k0 + t + 4];
+                unsigned bh[2] = {tf32_rna(b0v), tf32_rna(b1v)};
+                if (SPLIT) {
+                    unsigned bl[2] = {tf32_rna(b0v - __uint_as_float(bh[0])), tf32_rna(b1v - __uint_as_float(bh[1]))};
+                    mma_tf32(acc[j], al, bh);
+                    mma_tf32(acc[j], ah, bl);
+                }
+                mma_tf32(acc[j], ah, bh);
+            }
+        }
+        __syncwarp();  // the buffer is refilled two products on
+        float *gc = C + (long long)b * 256;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int c = 8 * j + 2 * t;
+            __stcs(gc + c * 16 + g, acc[j][0]);
+            __stcs(gc + (c + 1) * 16 + g, acc[j][1]);
+            __stcs(gc + c * 16 + g + 8, acc[j][2]);
+            __stcs(gc + (c + 1) * 16 + g + 8, acc[j][3]);
         }
     }
 }
@@ -281,8 +372,19 @@ cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float 
     const float *a = static_cast<const float *>(A), *b = static_cast<const float *>(B);
 #define TF(NN, SP) do { if ((e = prepare(k_gemm_tf32<NN, SP>, smem)) != cudaSuccess) return e;           \
         k_gemm_tf32<NN, SP><<<grid, 128, smem, st>>>(a, b, C, batch); return cudaPeekAtLastError(); } while (0)
+    if (n == 16) {  // persistent streaming kernel: grid of resident CTAs, warps stride over the batch
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const size_t sm16 = (size_t)kS16Warps * 2 * kS16Buf * 4;
+        const int g16 = std::min(ceil_div(batch, kS16Warps), kS16Ctas * sms);
+#define TS(SP) do { if ((e = prepare(k_gemm_tf32_stream16<SP>, sm16)) != cudaSuccess) return e;          \
+        k_gemm_tf32_stream16<SP><<<g16, 32 * kS16Warps, sm16, st>>>(a, b, C, batch); return cudaPeekAtLastError(); } while (0)
+        if (math == GLASS_MATH_TF32_TC) TS(false);
+        TS(true);
+#undef TS
+    }
     if (math == GLASS_MATH_TF32_TC) {
-        if (n == 16) TF(16, false);
         if (n == 32) TF(32, false);
         TF(64, false);
     }
