@@ -371,14 +371,15 @@ cudaError_t launch_gemm(int m, int n, int k, Mat A, Mat B, Mat C, int batch, Pla
                           ((reinterpret_cast<uintptr_t>(A.p) | reinterpret_cast<uintptr_t>(B.p) |
                             reinterpret_cast<uintptr_t>(C.p)) & 15) == 0;
     if (async_ok && m == 64) return launch_gemm_umma64(A.p, B.p, C.p, batch, st);
-    // order 16, block x1 on packed aligned operands: the split-TF32 mma.sync
-    // kernel (each product within 3 * 2^-22 of exact, inside the FP32 bound
-    // 2k u |A||B| = 2^-19 |A||B| every FP32 GEMM here meets)
-    if (pl.scope == SCOPE_BLOCK && pl.pack == 1 && m == 16 && n == 16 && k == 16 && A.packed() && B.packed() &&
-        C.packed() &&
+    // orders 16, 24 and 32, block x1 on packed aligned operands: the
+    // streaming split-TF32 mma.sync kernel (each product within 3 * 2^-22 of
+    // exact, FP32 accumulation: inside the FP32 bound 2k u |A||B| every FP32
+    // GEMM here meets)
+    if (pl.scope == SCOPE_BLOCK && pl.pack == 1 && m == n && n == k && (n == 16 || n == 24 || n == 32) &&
+        A.packed() && B.packed() && C.packed() &&
         ((reinterpret_cast<uintptr_t>(A.p) | reinterpret_cast<uintptr_t>(B.p) | reinterpret_cast<uintptr_t>(C.p)) &
          15) == 0)
-        return launch_gemm_tc(16, GLASS_MATH_3XTF32_TC, A.p, B.p, C.p, batch, st);
+        return launch_gemm_tc(n, GLASS_MATH_3XTF32_TC, A.p, B.p, C.p, batch, st);
     if (async_ok) {
         const size_t sm = (size_t)2 * N * (N + 4) * 4;
         cudaError_t e;

@@ -8,8 +8,9 @@
 //
 // Work split: n/16 warps per product, warp w owns rows 16w .. 16w+15 of C
 // and every 8-column block, so one A fragment serves n/8 MMAs.  A CTA holds
-// 4 warps (4/(n/16) products); the TF32 modes of order 16 run a persistent
-// streaming form instead (one warp per product, next product prefetched).  Operands are staged into shared memory with
+// 4 warps (4/(n/16) products); the TF32 modes of orders up to 32 run a
+// persistent streaming form instead (one warp per product, the next
+// product prefetched).  Operands are staged into shared memory with
 // coalesced 16-byte streaming loads, in padded layouts whose leading
 // dimensions make every fragment load bank-conflict free; C goes back
 // through shared memory for coalesced 16-byte stores.
@@ -137,91 +138,121 @@ __global__ void __launch_bounds__(128) k_gemm_tf32(const float *__restrict__ A, 
     }
 }
 
-// ------------------------------------------------------- TF32, order 16
-// Persistent streaming form for n = 16 (one warp per product, 3 KB of HBM
-// traffic against 12 KFLOP: a stream, not a contraction): each warp walks
-// the batch with a stride of the grid's warp count; the next product's A
-// and B are copied by cp.async into the warp's second buffer while the
-// current one is multiplied, so no barrier stands between a load and its
-// use.  C leaves straight from the accumulator fragments (lanes g = 0..7 of
-// a fragment row cover one 32-byte column segment: whole sectors).
-constexpr int kS16 = 16, kS16LDA = 24, kS16LDB = 20;  // conflict-free fragment loads
-constexpr int kS16Buf = kS16 * kS16LDA + kS16 * kS16LDB;  // floats per buffer
-constexpr int kS16Warps = 8;                              // warps per CTA
-constexpr int kS16Ctas = 5;                               // resident CTAs per SM (45 KB of shared memory each)
+// ------------------------------------------------ TF32, orders 16 .. 32
+// Persistent streaming form for n in {16, 24, 32} (one warp per product;
+// 3 n^2 floats of HBM traffic against 2 n^3 flops: a stream, not a
+// contraction): each warp walks the batch with a stride of the grid's warp
+// count; the next product's A and B are copied by cp.async into the warp's
+// second buffer while the current one is multiplied, so no barrier stands
+// between a load and its use.  C leaves straight from the accumulator
+// fragments (lanes g = 0..7 of a fragment row cover one 32-byte column
+// segment: whole sectors).  Row tiles are 16 high: at n = 24 the second one
+// reads rows 24..31 of A's padding, zeroed once, and its rows past n are not
+// stored.
+template <int N>
+struct Stream {
+    static constexpr int LDA = N == 24 ? 40 : N + 8;  // 8 mod 32: conflict-free A fragments
+    static constexpr int LDB = N + 4;                 // 4 mod 8: conflict-free B fragments
+    static constexpr int MT = (N + 15) / 16, NT = N / 8;
+    static constexpr int BUF = N * LDA + N * LDB;     // floats per buffer
+    static constexpr int WARPS = N == 32 ? 2 : 8;     // warps per CTA
+    static constexpr int CTAS = N == 24 ? 2 : 5;      // resident CTAs per SM (shared memory)
+    static constexpr size_t SMEM = (size_t)WARPS * 2 * BUF * 4;
+};
 
-template <bool SPLIT>
-__global__ void __launch_bounds__(32 * kS16Warps) k_gemm_tf32_stream16(const float *__restrict__ A,
-                                                                   const float *__restrict__ B,
-                                                                   float *__restrict__ C, int batch) {
+template <int N, bool SPLIT>
+__global__ void __launch_bounds__(32 * Stream<N>::WARPS) k_gemm_tf32_stream(const float *__restrict__ A,
+                                                                          const float *__restrict__ B,
+                                                                          float *__restrict__ C, int batch) {
+    using S = Stream<N>;
     extern __shared__ __align__(16) float smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
-    float *buf = smem + warp * 2 * kS16Buf;
-    const int stride = gridDim.x * kS16Warps;
-    // lane's 16-byte chunks of one operand: columns lane / 4 and lane / 4 + 8, rows 4 (lane % 4)
-    const int c0 = lane >> 2, r0 = 4 * (lane & 3);
-    auto issue = [&](int b, float *dst) {
-        const float *ga = A + (long long)b * 256, *gb = B + (long long)b * 256;
-        float *As = dst, *Bs = dst + kS16 * kS16LDA;
+    float *buf = smem + warp * 2 * S::BUF;
+    const int stride = gridDim.x * S::WARPS;
+    int b = blockIdx.x * S::WARPS + warp;
+    if (b >= batch) return;  // whole warp
+    if (N == 24) {           // rows 24..31 of both A buffers are read as zero
+        for (int e = lane; e < 2 * N * 8; e += 32) {
+            const int h = e / (N * 8), c = (e / 8) % N, r = 24 + e % 8;
+            buf[h * S::BUF + c * S::LDA + r] = 0.f;
+        }
+    }
+    auto issue = [&](int bb, float *dst) {
+        const float *ga = A + (long long)bb * N * N, *gb = B + (long long)bb * N * N;
+        float *As = dst, *Bs = dst + N * S::LDA;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = c0 + 8 * h;
-            cp_async16(As + c * kS16LDA + r0, ga + c * 16 + r0);
-            cp_async16(Bs + c * kS16LDB + r0, gb + c * 16 + r0);
+        for (int e = lane; e < N * N / 4; e += 32) {
+            const int c = e / (N / 4), r = 4 * (e % (N / 4));
+            cp_async16(As + c * S::LDA + r, ga + c * N + r);
+            cp_async16(Bs + c * S::LDB + r, gb + c * N + r);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    int b = blockIdx.x * kS16Warps + warp;
-    if (b >= batch) return;  // whole warp
     issue(b, buf);
     for (int it = 0; b < batch; b += stride, ++it) {
-        float *cur = buf + (it & 1) * kS16Buf;
+        float *cur = buf + (it & 1) * S::BUF;
         const int nb = b + stride;
         if (nb < batch) {
-            issue(nb, buf + ((it + 1) & 1) * kS16Buf);
+            issue(nb, buf + ((it + 1) & 1) * S::BUF);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncwarp();
-        const float *As = cur, *Bs = cur + kS16 * kS16LDA;
-        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        const float *As = cur, *Bs = cur + N * S::LDA;
+        float acc[S::MT][S::NT][4];
 #pragma unroll
-        for (int k0 = 0; k0 < 16; k0 += 8) {
-            float af[4];
-            af[0] = As[(k0 + t) * kS16LDA + g];
-            af[1] = As[(k0 + t) * kS16LDA + g + 8];
-            af[2] = As[(k0 + t + 4) * kS16LDA + g];
-            af[3] = As[(k0 + t + 4) * kS16LDA + g + 8];
-            unsigned ah[4], al[4];
+        for (int mt = 0; mt < S::MT; ++mt)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                ah[u] = tf32_rna(af[u]);
-                if (SPLIT) al[u] = tf32_rna(af[u] - __uint_as_float(ah[u]));
+            for (int nt = 0; nt < S::NT; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.f;
+#pragma unroll
+        for (int k0 = 0; k0 < N; k0 += 8) {
+            unsigned ah[S::MT][4], al[S::MT][4];
+#pragma unroll
+            for (int mt = 0; mt < S::MT; ++mt) {
+                const float af[4] = {As[(k0 + t) * S::LDA + 16 * mt + g], As[(k0 + t) * S::LDA + 16 * mt + g + 8],
+                                     As[(k0 + t + 4) * S::LDA + 16 * mt + g],
+                                     As[(k0 + t + 4) * S::LDA + 16 * mt + g + 8]};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ah[mt][u] = tf32_rna(af[u]);
+                    if (SPLIT) al[mt][u] = tf32_rna(af[u] - __uint_as_float(ah[mt][u]));
+                }
             }
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float b0v = Bs[(8 * j + g) * kS16LDB + k0 + t], b1v = Bs[(8 * j + g) * kS16LDB + k0 + t + 4];
+            for (int nt = 0; nt < S::NT; ++nt) {
+                const float b0v = Bs[(8 * nt + g) * S::LDB + k0 + t], b1v = Bs[(8 * nt + g) * S::LDB + k0 + t + 4];
                 unsigned bh[2] = {tf32_rna(b0v), tf32_rna(b1v)};
+                unsigned bl[2] = {0u, 0u};
                 if (SPLIT) {
-                    unsigned bl[2] = {tf32_rna(b0v - __uint_as_float(bh[0])), tf32_rna(b1v - __uint_as_float(bh[1]))};
-                    mma_tf32(acc[j], al, bh);
-                    mma_tf32(acc[j], ah, bl);
+                    bl[0] = tf32_rna(b0v - __uint_as_float(bh[0]));
+                    bl[1] = tf32_rna(b1v - __uint_as_float(bh[1]));
                 }
-                mma_tf32(acc[j], ah, bh);
+#pragma unroll
+                for (int mt = 0; mt < S::MT; ++mt) {
+                    if (SPLIT) {
+                        mma_tf32(acc[mt][nt], al[mt], bh);
+                        mma_tf32(acc[mt][nt], ah[mt], bl);
+                    }
+                    mma_tf32(acc[mt][nt], ah[mt], bh);
+                }
             }
         }
         __syncwarp();  // the buffer is refilled two products on
-        float *gc = C + (long long)b * 256;
+        float *gc = C + (long long)b * N * N;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int c = 8 * j + 2 * t;
-            __stcs(gc + c * 16 + g, acc[j][0]);
-            __stcs(gc + (c + 1) * 16 + g, acc[j][1]);
-            __stcs(gc + c * 16 + g + 8, acc[j][2]);
-            __stcs(gc + (c + 1) * 16 + g + 8, acc[j][3]);
-        }
+        for (int mt = 0; mt < S::MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < S::NT; ++nt) {
+                const int c = 8 * nt + 2 * t, r = 16 * mt + g;
+                __stcs(gc + c * N + r, acc[mt][nt][0]);
+                __stcs(gc + (c + 1) * N + r, acc[mt][nt][1]);
+                if (r + 8 < N) {
+                    __stcs(gc + c * N + r + 8, acc[mt][nt][2]);
+                    __stcs(gc + (c + 1) * N + r + 8, acc[mt][nt][3]);
+                }
+            }
     }
 }
 
@@ -351,6 +382,27 @@ cudaError_t launch_gemm_umma64_bf16(const void *A, const void *B, float *C, int 
     return cudaPeekAtLastError();
 }
 
+// The streaming TF32 kernels of orders 16, 24 and 32: a grid of resident
+// CTAs whose warps stride over the batch.  Operands packed (ld = n, stride
+// n^2) and 16-byte aligned, as launch_gemm_tc requires.
+cudaError_t launch_gemm_tf32_stream(int n, bool split, const float *A, const float *B, float *C, int batch,
+                                    cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+#define TS(NN, SP) do { using S = Stream<NN>;                                                              \
+        if ((e = prepare(k_gemm_tf32_stream<NN, SP>, S::SMEM)) != cudaSuccess) return e;                    \
+        const int grid = std::min(ceil_div(batch, S::WARPS), S::CTAS * sms);                                \
+        k_gemm_tf32_stream<NN, SP><<<grid, 32 * S::WARPS, S::SMEM, st>>>(A, B, C, batch);                    \
+        return cudaPeekAtLastError(); } while (0)
+    if (n == 16) { if (split) TS(16, true); TS(16, false); }
+    if (n == 24) { if (split) TS(24, true); TS(24, false); }
+    if (n == 32) { if (split) TS(32, true); TS(32, false); }
+#undef TS
+    return cudaErrorInvalidConfiguration;
+}
+
 cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float *C, int batch, cudaStream_t st) {
     // 16-byte staging needs 16-byte aligned operands
     if (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15) != 0)
@@ -372,24 +424,8 @@ cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float 
     const float *a = static_cast<const float *>(A), *b = static_cast<const float *>(B);
 #define TF(NN, SP) do { if ((e = prepare(k_gemm_tf32<NN, SP>, smem)) != cudaSuccess) return e;           \
         k_gemm_tf32<NN, SP><<<grid, 128, smem, st>>>(a, b, C, batch); return cudaPeekAtLastError(); } while (0)
-    if (n == 16) {  // persistent streaming kernel: grid of resident CTAs, warps stride over the batch
-        int dev = 0, sms = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        const size_t sm16 = (size_t)kS16Warps * 2 * kS16Buf * 4;
-        const int g16 = std::min(ceil_div(batch, kS16Warps), kS16Ctas * sms);
-#define TS(SP) do { if ((e = prepare(k_gemm_tf32_stream16<SP>, sm16)) != cudaSuccess) return e;          \
-        k_gemm_tf32_stream16<SP><<<g16, 32 * kS16Warps, sm16, st>>>(a, b, C, batch); return cudaPeekAtLastError(); } while (0)
-        if (math == GLASS_MATH_TF32_TC) TS(false);
-        TS(true);
-#undef TS
-    }
-    if (math == GLASS_MATH_TF32_TC) {
-        if (n == 32) TF(32, false);
-        TF(64, false);
-    }
-    if (n == 16) TF(16, true);
-    if (n == 32) TF(32, true);
+    if (n <= 32) return launch_gemm_tf32_stream(n, math == GLASS_MATH_3XTF32_TC, a, b, C, batch, st);
+    if (math == GLASS_MATH_TF32_TC) TF(64, false);
     return launch_gemm_umma64(a, b, C, batch, st);
 #undef TF
 }
