@@ -3,9 +3,12 @@
 // warp scope loads rows straight into registers up to order 16 -- two
 // problems per warp, one per half -- and runs the blocked tensor-core
 // factorization (dev_lu_tc.cuh) on the problem in shared memory above that;
-// block scope is a 64-thread row team (dev_rows.cuh), one row per thread.
+// block scope is a 64-thread row team (dev_rows.cuh), one row per thread,
+// up to order 32 and a two-warp team on the blocked tensor-core
+// factorization (dev_lu_tc2.cuh) above.
 #include "dev_lu.cuh"
 #include "dev_lu_tc.cuh"
+#include "dev_lu_tc2.cuh"
 #include "dev_rows.cuh"
 
 namespace glass {
@@ -158,6 +161,48 @@ __global__ void __launch_bounds__(256, NMAX == 32 ? 3 : 1) k_lu_tc(int n, int nr
     tcwarp::unstage<NMAX, false, LD>(A.p + (long long)b * A.s, A.ld, As, n);
 }
 
+// Block scope, orders 33..64: the blocked tensor-core LU run by a team of
+// two warps per problem (dev_lu_tc2.cuh); afterwards warp 0 solves and
+// warp 1 writes the factor, the interchanges and info back.
+__global__ void __launch_bounds__(256) k_lu_tc2(int n, int nrhs, Mat A, int *ipiv, Mat B, int *info, int batch) {
+    constexpr int NMAX = tclu2::NMAX, LD = tclu2::LD;
+    extern __shared__ __align__(16) float smem[];
+    const int team = threadIdx.x / tclu2::T, rank = threadIdx.x % tclu2::T;
+    const int b = blockIdx.x * (blockDim.x / tclu2::T) + team;
+    const int bid = 1 + team;
+    float *As = smem + team * tclu2::floats();
+    float *dv = As + NMAX * LD;
+    int *ps = reinterpret_cast<int *>(dv + NMAX);
+    int *prow = ps + NMAX;
+    float *xch = reinterpret_cast<float *>(prow + NMAX);
+    if (b >= batch) return;  // the whole team leaves together
+    prow[rank] = rank;
+    tclu2::stage(As, A.p + (long long)b * A.s, A.ld, n, rank, bid);  // ends with a team barrier
+    const int inf = tclu2::getrf(As, n, prow, ps, dv, xch, rank, bid);
+    const int lane = rank & 31;
+    if (rank < 32) {
+        for (int c = 0; c < nrhs; ++c) {
+            float x[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int i = lane + 32 * q;
+                x[q] = (i < n) ? B.cget(b, prow[i], c) : 0.f;
+            }
+            tclu::getrs<NMAX>(As, dv, x, n);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int i = lane + 32 * q;
+                if (i < n) B.cset(b, i, c, x[q]);
+            }
+        }
+    } else {
+        if (lane == 0) info[b] = inf;
+        int *gp = ipiv + (long long)b * n;
+        for (int j = lane; j < n; j += 32) gp[j] = ps[j];
+        tcwarp::unstage<NMAX, false, LD>(A.p + (long long)b * A.s, A.ld, As, n);
+    }
+}
+
 constexpr int kRS = 4;
 
 template <int NMAX>
@@ -217,9 +262,9 @@ size_t smem_lu(int n, int nrhs, Placement pl) {
                    : n > 16 ? (size_t)pl.pack * lu_tc_floats<32>() * 4
                             : (size_t)pl.pack * 4 * 16 * 4;
         default: {
-            const int N = n <= 8 ? 8 : n <= 16 ? 16 : n <= 32 ? 32 : 64;
-            const int f = N == 8 ? lu_team_floats<8>() : N == 16 ? lu_team_floats<16>()
-                        : N == 32 ? lu_team_floats<32>() : lu_team_floats<64>();
+            if (n > 32) return (size_t)pl.pack * tclu2::floats() * 4;
+            const int N = n <= 8 ? 8 : n <= 16 ? 16 : 32;
+            const int f = N == 8 ? lu_team_floats<8>() : N == 16 ? lu_team_floats<16>() : lu_team_floats<32>();
             return (size_t)pl.pack * f * 4;
         }
     }
@@ -270,10 +315,10 @@ cudaError_t launch_getrf_getrs(int n, int nrhs, Mat A, int *ipiv, Mat B, int *in
         return go(k_lu_half<16>, g2, th, sw, st, n, nrhs, A, ipiv, B, info, batch);
     }
     const int th = rows::T * pl.pack;
+    if (n > 32) return go(k_lu_tc2, grid, tclu2::T * pl.pack, smem, st, n, nrhs, A, ipiv, B, info, batch);
     if (n <= 8) return go(k_lu_rows<8>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
     if (n <= 16) return go(k_lu_rows<16>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
-    if (n <= 32) return go(k_lu_rows<32>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
-    return go(k_lu_rows<64>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
+    return go(k_lu_rows<32>, grid, th, smem, st, n, nrhs, A, ipiv, B, info, batch);
 }
 
 }  // namespace glass
