@@ -506,7 +506,8 @@ KERNEL_SOURCES = {
              "dev_rows.cuh", "dev_trsm_tc.cuh"],
     "trsm": ["common.cuh", "k_chol_impl.cuh", "k_chol_trsm.cu", "dev_chol.cuh", "dev_chol_tc.cuh",
              "dev_rows.cuh", "dev_trsm_tc.cuh"],
-    "getrf_getrs": ["common.cuh", "k_lu.cu", "dev_lu.cuh", "dev_lu_tc.cuh", "dev_chol_tc.cuh", "dev_rows.cuh"],
+    "getrf_getrs": ["common.cuh", "k_lu.cu", "dev_lu.cuh", "dev_lu_tc.cuh", "dev_lu_tc2.cuh", "dev_chol_tc.cuh",
+                    "dev_rows.cuh"],
     "rot3": ["common.cuh", "k_geom.cu"],
     "se3": ["common.cuh", "k_geom.cu"],
 }

@@ -8,9 +8,9 @@
 //
 // Work split: n/16 warps per product, warp w owns rows 16w .. 16w+15 of C
 // and every 8-column block, so one A fragment serves n/8 MMAs.  A CTA holds
-// 4 warps (4/(n/16) products); the TF32 modes of orders up to 32 run a
-// persistent streaming form instead (one warp per product, the next
-// product prefetched).  Operands are staged into shared memory with
+// 4 warps (4/(n/16) products); orders 16 to 32 (TF32 modes) and 16, 32
+// (BF16) run a persistent streaming form instead (one warp per product,
+// the next product prefetched).  Operands are staged into shared memory with
 // coalesced 16-byte streaming loads, in padded layouts whose leading
 // dimensions make every fragment load bank-conflict free; C goes back
 // through shared memory for coalesced 16-byte stores.
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(32 * Stream<N>::WARPS) k_gemm_tf32_stream(cons
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
     float *buf = smem + warp * 2 * S::BUF;
-    const int stride = gridDim.x * S::WARPS;
+    const int stride = gridDim.x * S::WARPS;  // <= CTAS * SMs * WARPS
     int b = blockIdx.x * S::WARPS + warp;
     if (b >= batch) return;  // whole warp
     if (N == 24) {           // rows 24..31 of both A buffers are read as zero
@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(32 * Stream<N>::WARPS) k_gemm_tf32_stream(cons
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     issue(b, buf);
-    for (int it = 0; b < batch; b += stride, ++it) {
+    for (int it = 0; b < batch; ++it) {
         float *cur = buf + (it & 1) * S::BUF;
-        const int nb = b + stride;
+        const int nb = b < batch - stride ? b + stride : batch;  // no int overflow near 2^31
         if (nb < batch) {
             issue(nb, buf + ((it + 1) & 1) * S::BUF);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -253,89 +253,108 @@ __global__ void __launch_bounds__(32 * Stream<N>::WARPS) k_gemm_tf32_stream(cons
                     __stcs(gc + (c + 1) * N + r + 8, acc[mt][nt][3]);
                 }
             }
+        b = nb;
     }
 }
 
-// ------------------------------------------------------------------ BF16
-// As: A row-major (transposed on staging), lda = N + 8 halves; Bs: B
-// column-major, ldb = N + 8 halves.  A fragment pairs run along k.
+// ------------------------------------------------- BF16, orders 16 and 32
+// The streaming form of the BF16 product (as k_gemm_tf32_stream: one warp
+// per product, the next product's operands copied by cp.async into the
+// warp's second buffer while the current one multiplies, C written from
+// the accumulator fragments).  A stays column-major in shared memory as
+// copied; ldmatrix.trans forms its row-major m16n8k16 fragments (pairs
+// along k) from four 8 x 8 sub-blocks, and B's column-major pairs are
+// single 32-bit loads.  Pitch N + 8 halves: the eight 16-byte rows of every
+// ldmatrix sub-block and the B fragments fall in distinct banks.
 template <int N>
-__global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16 *__restrict__ A,
-                                                   const __nv_bfloat16 *__restrict__ B, float *__restrict__ C,
-                                                   int batch) {
-    using S = TcShape<N>;
-    constexpr int LD = N + 8;
-    constexpr int PERH = 2 * N * LD;  // halves per product
-    static_assert(PERH / 2 >= N * S::LDC, "C staging must fit in the operand staging");
+struct StreamBf {
+    static constexpr int LD = N + 8;                  // halves per column
+    static constexpr int MT = N / 16, NT = N / 8;
+    static constexpr int BUF = 2 * N * LD;            // halves per buffer (A, then B)
+    static constexpr int WARPS = 8;
+    static constexpr int CTAS = N == 16 ? 8 : 2;      // resident CTAs per SM (shared memory)
+    static constexpr size_t SMEM = (size_t)WARPS * 2 * BUF * 2;
+};
+
+__device__ __forceinline__ void ldmatrix_x4_trans(unsigned (&r)[4], const void *smem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+template <int N>
+__global__ void __launch_bounds__(32 * StreamBf<N>::WARPS) k_gemm_bf16_stream(const __nv_bfloat16 *__restrict__ A,
+                                                                            const __nv_bfloat16 *__restrict__ B,
+                                                                            float *__restrict__ C, int batch) {
+    using S = StreamBf<N>;
     extern __shared__ __align__(16) unsigned short hsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int lp = warp / S::WP, wq = warp % S::WP;
-    const int b0 = blockIdx.x * S::PPC;
-    for (int p = 0; p < S::PPC; ++p) {
-        const int b = b0 + p;
-        if (b >= batch) break;
-        unsigned short *As = hsm + p * PERH, *Bs = As + N * LD;
-        const uint4 *ga = reinterpret_cast<const uint4 *>(A + (long long)b * N * N);
-        const uint4 *gb = reinterpret_cast<const uint4 *>(B + (long long)b * N * N);
-        for (int v = threadIdx.x; v < N * N / 8; v += blockDim.x) {
-            const int col = (8 * v) / N, row = (8 * v) % N;
-            const uint4 xa = __ldcs(ga + v);
-            const uint4 xb = __ldcs(gb + v);
-            *reinterpret_cast<uint4 *>(Bs + col * LD + row) = xb;
-            const unsigned short *h = reinterpret_cast<const unsigned short *>(&xa);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) As[(row + u) * LD + col] = h[u];
-        }
-    }
-    __syncthreads();
-    const int b = b0 + lp;
     const int g = lane >> 2, t = lane & 3;
-    const int m0 = 16 * wq;
-    float acc[S::NB][4];
+    unsigned short *buf = hsm + warp * 2 * S::BUF;
+    const int stride = gridDim.x * S::WARPS;  // <= CTAS * SMs * WARPS
+    int b = blockIdx.x * S::WARPS + warp;
+    if (b >= batch) return;  // whole warp
+    auto issue = [&](int bb, unsigned short *dst) {
+        const __nv_bfloat16 *ga = A + (long long)bb * N * N, *gb = B + (long long)bb * N * N;
 #pragma unroll
-    for (int j = 0; j < S::NB; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const unsigned short *As = hsm + lp * PERH, *Bs = As + N * LD;
-    if (b < batch) {
+        for (int e = lane; e < N * N / 8; e += 32) {  // 16-byte chunks: 8 halves of one column
+            const int c = e / (N / 8), r = 8 * (e % (N / 8));
+            cp_async16(dst + c * S::LD + r, ga + c * N + r);
+            cp_async16(dst + N * S::LD + c * S::LD + r, gb + c * N + r);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // this lane's ldmatrix row: sub-block lane / 8 (rows +8 for odd, k +8 for the upper two)
+    const int lr = lane & 7, lm = lane >> 3;
+    const int a_row = 8 * (lm & 1), a_k = lr + 8 * (lm >> 1);
+    issue(b, buf);
+    for (int it = 0; b < batch; ++it) {
+        unsigned short *cur = buf + (it & 1) * S::BUF;
+        const int nb = b < batch - stride ? b + stride : batch;  // no int overflow near 2^31
+        if (nb < batch) {
+            issue(nb, buf + ((it + 1) & 1) * S::BUF);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncwarp();
+        const unsigned short *As = cur, *Bs = cur + N * S::LD;
+        float acc[S::MT][S::NT][4];
+#pragma unroll
+        for (int mt = 0; mt < S::MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < S::NT; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.f;
 #pragma unroll
         for (int k0 = 0; k0 < N; k0 += 16) {
-            unsigned a[4];
-            a[0] = *reinterpret_cast<const unsigned *>(As + (m0 + g) * LD + k0 + 2 * t);
-            a[1] = *reinterpret_cast<const unsigned *>(As + (m0 + g + 8) * LD + k0 + 2 * t);
-            a[2] = *reinterpret_cast<const unsigned *>(As + (m0 + g) * LD + k0 + 2 * t + 8);
-            a[3] = *reinterpret_cast<const unsigned *>(As + (m0 + g + 8) * LD + k0 + 2 * t + 8);
+            unsigned a[S::MT][4];
 #pragma unroll
-            for (int j = 0; j < S::NB; ++j) {
+            for (int mt = 0; mt < S::MT; ++mt) ldmatrix_x4_trans(a[mt], As + (k0 + a_k) * S::LD + 16 * mt + a_row);
+#pragma unroll
+            for (int nt = 0; nt < S::NT; ++nt) {
                 unsigned bq[2];
-                bq[0] = *reinterpret_cast<const unsigned *>(Bs + (8 * j + g) * LD + k0 + 2 * t);
-                bq[1] = *reinterpret_cast<const unsigned *>(Bs + (8 * j + g) * LD + k0 + 2 * t + 8);
-                mma_bf16(acc[j], a, bq);
+                bq[0] = *reinterpret_cast<const unsigned *>(Bs + (8 * nt + g) * S::LD + k0 + 2 * t);
+                bq[1] = *reinterpret_cast<const unsigned *>(Bs + (8 * nt + g) * S::LD + k0 + 2 * t + 8);
+#pragma unroll
+                for (int mt = 0; mt < S::MT; ++mt) mma_bf16(acc[mt][nt], a[mt], bq);
             }
         }
-    }
-    __syncthreads();
-    float *Cs = reinterpret_cast<float *>(hsm) + lp * (PERH / 2);
-    if (b < batch) {
+        __syncwarp();  // the buffer is refilled two products on
+        float *gc = C + (long long)b * N * N;
 #pragma unroll
-        for (int j = 0; j < S::NB; ++j) {
-            const int c0 = 8 * j + 2 * t;
-            Cs[c0 * S::LDC + m0 + g] = acc[j][0];
-            Cs[(c0 + 1) * S::LDC + m0 + g] = acc[j][1];
-            Cs[c0 * S::LDC + m0 + g + 8] = acc[j][2];
-            Cs[(c0 + 1) * S::LDC + m0 + g + 8] = acc[j][3];
-        }
-    }
-    __syncthreads();
-    for (int p = 0; p < S::PPC; ++p) {
-        const int bb = b0 + p;
-        if (bb >= batch) break;
-        const float *cs = reinterpret_cast<const float *>(hsm) + p * (PERH / 2);
-        float4 *gc = reinterpret_cast<float4 *>(C + (long long)bb * N * N);
-        for (int v = threadIdx.x; v < N * N / 4; v += blockDim.x) {
-            const int col = (4 * v) / N, row = (4 * v) % N;
-            __stcs(gc + v, *reinterpret_cast<const float4 *>(cs + col * S::LDC + row));
-        }
+        for (int mt = 0; mt < S::MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < S::NT; ++nt) {
+                const int c = 8 * nt + 2 * t, r = 16 * mt + g;
+                __stcs(gc + c * N + r, acc[mt][nt][0]);
+                __stcs(gc + (c + 1) * N + r, acc[mt][nt][1]);
+                __stcs(gc + c * N + r + 8, acc[mt][nt][2]);
+                __stcs(gc + (c + 1) * N + r + 8, acc[mt][nt][3]);
+            }
+        b = nb;
     }
 }
+
 
 }  // namespace
 
@@ -411,10 +430,15 @@ cudaError_t launch_gemm_tc(int n, int math, const void *A, const void *B, float 
     const int grid = ceil_div(batch, ppc);
     cudaError_t e;
     if (math == GLASS_MATH_BF16_TC) {
-        const size_t smem = (size_t)ppc * 2 * n * (n + 8) * 2;
         const __nv_bfloat16 *a = static_cast<const __nv_bfloat16 *>(A), *b = static_cast<const __nv_bfloat16 *>(B);
-#define BF(NN) do { if ((e = prepare(k_gemm_bf16<NN>, smem)) != cudaSuccess) return e;                     \
-        k_gemm_bf16<NN><<<grid, 128, smem, st>>>(a, b, C, batch); return cudaPeekAtLastError(); } while (0)
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+#define BF(NN) do { using S = StreamBf<NN>;                                                               \
+        if ((e = prepare(k_gemm_bf16_stream<NN>, S::SMEM)) != cudaSuccess) return e;                       \
+        const int gs = std::min(ceil_div(batch, S::WARPS), S::CTAS * sms);                                  \
+        k_gemm_bf16_stream<NN><<<gs, 32 * S::WARPS, S::SMEM, st>>>(a, b, C, batch);                         \
+        return cudaPeekAtLastError(); } while (0)
         if (n == 16) BF(16);
         if (n == 32) BF(32);
 #undef BF
