@@ -57,6 +57,33 @@ def test_tc_gemm_integer_bit_exact(n, math):
     assert np.array_equal(host(dC).astype(np.float64), ref)
 
 
+@pytest.mark.parametrize("n", [16, 24, 32])
+def test_streaming_gemm_every_problem_of_a_large_batch(n):
+    """The FP32 block placement of orders 16-32 runs the streaming split-TF32
+    kernel, whose warps each walk several products (the next one's operands
+    in flight): at batch 20011 -- more products than the grid has warps, and
+    a ragged last round -- every product is checked, integer operands bit
+    for bit and Gaussian ones at the FP32 bound against the FP64 oracle."""
+    batch = 20011
+    o = g.make_opts(scope=g.GLASS_SCOPE_BLOCK, pack=1)
+    Ai = W.colmajor(W.int_matrix(n, n, batch, 2150 + n))
+    Bi = W.colmajor(W.int_matrix(n, n, batch, 2160 + n))
+    dC = to_dev(np.full(batch * n * n, np.nan, np.float32))
+    g.check(g.glass_batched_gemm(n, n, n, to_dev(Ai), n, n * n, to_dev(Bi), n, n * n, dC, n, n * n, batch, o))
+    sync()
+    assert np.array_equal(host(dC).astype(np.float64),
+                          oracle.gemm(n, n, n, Ai.astype(np.float64), Bi.astype(np.float64), batch))
+    A = W.gaussian(batch * n * n, 2170 + n)
+    B = W.gaussian(batch * n * n, 2180 + n)
+    dC = to_dev(np.full(batch * n * n, np.nan, np.float32))
+    g.check(g.glass_batched_gemm(n, n, n, to_dev(A), n, n * n, to_dev(B), n, n * n, dC, n, n * n, batch, o))
+    sync()
+    ref = mats(oracle.gemm(n, n, n, A.astype(np.float64), B.astype(np.float64), batch), batch, n, n)
+    got = mats(host(dC).astype(np.float64), batch, n, n)
+    absab = np.abs(mats(A, batch, n, n).astype(np.float64)) @ np.abs(mats(B, batch, n, n).astype(np.float64))
+    assert (np.abs(got - ref) <= 2 * n * U32 * absab + 1e-30).all(), n
+
+
 @pytest.mark.parametrize("n", [16, 32, 64])
 def test_tc_gemm_gaussian_errors(n):
     """BF16 and TF32 products match the FP64 product of the ROUNDED operands
