@@ -812,8 +812,7 @@ cudaError_t thread_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *in
 }
 
 // Shared memory of the blocked tensor-core Cholesky, per warp (bytes).
-inline size_t tc_smem(int n, bool rf = false) {
-    (void)rf;  // the refinement step lives in A's padding
+inline size_t tc_smem(int n) {  // the refinement step lives in A's padding: no extra
     return (size_t)(n > 32 ? tc_floats<64>() : tc_floats<32>()) * 4;
 }
 
@@ -864,9 +863,9 @@ cudaError_t warp_dispatch(int n, int nrhs, const Mat &A, const Mat &B, int *info
             if (n > 16) {
                 const int grid = ceil_div(batch, pack);
                 if (n > 32)
-                    return launch_k(k_chol_tc<OP, 64, RF>, grid, 32 * pack, tc_smem(n, RF) * pack, st, n, nrhs, A, B,
+                    return launch_k(k_chol_tc<OP, 64, RF>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B,
                                     info, batch, num);
-                return launch_k(k_chol_tc<OP, 32, RF>, grid, 32 * pack, tc_smem(n, RF) * pack, st, n, nrhs, A, B, info,
+                return launch_k(k_chol_tc<OP, 32, RF>, grid, 32 * pack, tc_smem(n) * pack, st, n, nrhs, A, B, info,
                                 batch, num);
             }
         }
@@ -924,7 +923,7 @@ size_t smem_of(int n, int nrhs, Placement pl, int refine) {
             return (size_t)32 * pl.pack * (odd_stride(n * n) + (has_rhs(OP) ? odd_stride(n * nrhs) : 0)) * 4;
         case SCOPE_WARP: {
             if (OP == C_TRSM) return solve_cols_per(n, nrhs, 32) * pl.pack;
-            if (has_factor(OP) && n > 16) return tc_smem(n, refine != 0) * pl.pack;
+            if (has_factor(OP) && n > 16) return tc_smem(n) * pl.pack;
             const int N = nmax_bucket(n);
             return (size_t)pl.pack * (N + (refine ? N * (N + 1) : 0)) * 4;
         }
