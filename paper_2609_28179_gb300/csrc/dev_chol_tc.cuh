@@ -385,11 +385,16 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
     static_assert(NMAX == 32 || NMAX == 64, "orders 17..32 or 33..64");
     constexpr int LD = Shape<NMAX>::LD;
     const int lane = threadIdx.x & 31;
+    // 1/l_ii of the lane's own rows (zero past n): step i multiplies in
+    // lane i before the broadcast, so no step reads dv[i]
+    float d[Shape<NMAX>::R];
+#pragma unroll
+    for (int q = 0; q < Shape<NMAX>::R; ++q) d[q] = lane + 32 * q < n ? dv[lane + 32 * q] : 0.f;
     if constexpr (NMAX == 32) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             if (i < n) {
-                const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+                const float yi = __shfl_sync(GLASS_FULL_MASK, x[0] * d[0], i);
                 const float c0 = As[i * LD + lane];
                 if (lane == i) x[0] = yi;
                 else if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
@@ -398,7 +403,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
 #pragma unroll
         for (int i = 31; i >= 0; --i) {
             if (i < n) {
-                const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+                const float xi = __shfl_sync(GLASS_FULL_MASK, x[0] * d[0], i);
                 const float c0 = As[i * LD + lane];
                 if (lane == i) x[0] = xi;
                 else if (lane < i) x[0] = fmaf(-c0, xi, x[0]);
@@ -408,7 +413,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
     } else {
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
-        const float yi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+        const float yi = __shfl_sync(GLASS_FULL_MASK, x[0] * d[0], i);
         const float c0 = As[i * LD + lane], c1 = As[i * LD + lane + 32];
         if (lane == i) x[0] = yi;
         else if (lane > i) x[0] = fmaf(-c0, yi, x[0]);
@@ -417,7 +422,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
 #pragma unroll
     for (int i = 32; i < 64; ++i) {
         if (i < n) {
-            const float yi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
+            const float yi = __shfl_sync(GLASS_FULL_MASK, x[1] * d[1], i - 32);
             const float c1 = As[i * LD + lane + 32];
             if (lane + 32 == i) x[1] = yi;
             else if (lane + 32 > i) x[1] = fmaf(-c1, yi, x[1]);
@@ -426,7 +431,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
 #pragma unroll
     for (int i = 63; i >= 32; --i) {
         if (i < n) {
-            const float xi = __shfl_sync(GLASS_FULL_MASK, x[1], i - 32) * dv[i];
+            const float xi = __shfl_sync(GLASS_FULL_MASK, x[1] * d[1], i - 32);
             const float c0 = As[i * LD + lane], c1 = As[i * LD + lane + 32];  // mirror: l_{i,row}
             if (lane + 32 == i) x[1] = xi;
             else if (lane + 32 < i) x[1] = fmaf(-c1, xi, x[1]);
@@ -435,7 +440,7 @@ __device__ __forceinline__ void potrs(const float *As, const float *dv, float (&
     }
 #pragma unroll
     for (int i = 31; i >= 0; --i) {
-        const float xi = __shfl_sync(GLASS_FULL_MASK, x[0], i) * dv[i];
+        const float xi = __shfl_sync(GLASS_FULL_MASK, x[0] * d[0], i);
         const float c0 = As[i * LD + lane];
         if (lane == i) x[0] = xi;
         else if (lane < i) x[0] = fmaf(-c0, xi, x[0]);
