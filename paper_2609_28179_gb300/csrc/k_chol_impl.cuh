@@ -819,9 +819,13 @@ inline size_t tc_smem(int n) {  // the refinement step lives in A's padding: no 
 // Shared memory of the many-right-hand-side solve kernels, per problem
 // (bytes), for a team of T threads: column-per-thread up to order 32,
 // blocked tensor-core form above.
+// Order bucket of the column solve: an exact 24 besides the powers of two
+// (trsm n = 24 at batch 16384 ran padded to 32 rows).
+inline int cols_bucket(int n) { return n <= 8 ? 8 : n <= 16 ? 16 : n <= 24 ? 24 : n <= 32 ? 32 : 64; }
+
 inline size_t solve_cols_per(int n, int nrhs, int T) {
     if (n > 32) return (size_t)(T == 32 ? tctrsm::floats<32>() : tctrsm::floats<64>()) * 4;
-    const int N = nmax_bucket(n);
+    const int N = cols_bucket(n);
     return (size_t)(N * N + N + (size_t)nrhs * col_pitch(n)) * 4;
 }
 
@@ -845,9 +849,10 @@ cudaError_t solve_cols_dispatch(int n, int nrhs, const Mat &L, const Mat &B, int
         kern<<<ceil_div(batch, pack), T * pack, sm, st>>>(n, nrhs, L, B, batch);
         return cudaPeekAtLastError();
     }
-    switch (nmax_bucket(n)) {
+    switch (cols_bucket(n)) {
         case 8: return launch_solve_cols<8, T, BOTH>(n, nrhs, L, B, batch, pack, st);
         case 16: return launch_solve_cols<16, T, BOTH>(n, nrhs, L, B, batch, pack, st);
+        case 24: return launch_solve_cols<24, T, BOTH>(n, nrhs, L, B, batch, pack, st);
         case 32: return launch_solve_cols<32, T, BOTH>(n, nrhs, L, B, batch, pack, st);
         default: return launch_solve_cols<64, T, BOTH>(n, nrhs, L, B, batch, pack, st);
     }
