@@ -4,7 +4,7 @@ its shape, trained on the GPU by the library's own kernels
 (glass_mlp_loss_grad / glass_mlp_adam) on measurements taken by
 ``tune.py random``.  The paper measures every cell exhaustively and looks
 the placement up in a table (Sec. III-A); the model predicts placements for
-shapes off that grid, and exhaustive measurement stays its judge (regret).
+shapes off that grid, and exhaustive measurement stays the arbiter of its regret.
 
 Features: one-hot over the 4 matrix operations (gemm, posv, trsm,
 getrf_getrs), log2 n, log2 k, log2 batch, dtype (0 = FP32), standardised
