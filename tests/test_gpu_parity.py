@@ -179,6 +179,35 @@ def test_trsm_square_rhs_all_placements(n):
         assert per_problem_rel(X, ref, batch) <= 1e-4, (n, scope, pack)
 
 
+@pytest.mark.parametrize("n", [19, 21, 23])
+def test_solves_of_orders_17_to_23(n):
+    """Orders 17..23 (the column solve's order-24 bucket, staged element by
+    element since n is not a multiple of 4): trsm with n right-hand sides at
+    every placement against the oracle, and potrf + potrs recovering integer
+    solutions bit for bit at every placement."""
+    batch = 70
+    g0 = W.rng(760 + n)
+    L = np.tril(g0.standard_normal((batch, n, n))) + 3.0 * np.eye(n)
+    Lcm = W.colmajor(L)
+    B = W.gaussian(batch * n * n, 761 + n)
+    ref = oracle.trsm(n, n, Lcm.astype(np.float64), B.astype(np.float64), batch)
+    for scope, pack in placements(g.GLASS_OP_TRSM, n, n):
+        dB = to_dev(B)
+        g.check(g.glass_batched_trsm(n, n, to_dev(Lcm), n, n * n, dB, n, n * n, batch, opts_for(scope, pack)))
+        sync()
+        assert per_problem_rel(host(dB).astype(np.float64), ref, batch) <= 1e-4, (n, scope, pack)
+    A, L0 = W.int_cholesky_factor(n, batch, 770 + n)
+    X0 = W.int_matrix(n, 6, batch, 771 + n, -3, 3)
+    Acm, Bcm = W.colmajor(A), W.colmajor(A @ X0)
+    for scope, pack in placements(g.GLASS_OP_POSV, n, 6):
+        dA, dB, info = to_dev(Acm), to_dev(Bcm), zeros_i32(batch)
+        g.check(g.glass_batched_potrf(n, dA, n, n * n, info, batch, opts_for(scope, pack)))
+        g.check(g.glass_batched_potrs(n, 6, dA, n, n * n, dB, n, 6 * n, batch, opts_for(scope, pack)))
+        sync()
+        assert (host(info)[:batch] == 0).all()
+        assert np.array_equal(mats(host(dB), batch, n, 6), X0), (n, scope, pack)
+
+
 @pytest.mark.parametrize("n", [4, 17, 64])
 def test_trsm_integer_bit_exact(n):
     batch, k = 40, 5
