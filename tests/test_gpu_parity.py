@@ -208,6 +208,28 @@ def test_solves_of_orders_17_to_23(n):
         assert np.array_equal(mats(host(dB), batch, n, 6), X0), (n, scope, pack)
 
 
+@pytest.mark.parametrize("n", [33, 40, 64])
+def test_lu_team_of_two_warps_matches_one_warp_bit_for_bit(n):
+    """The block placement of orders 33..64 runs the tensor-core LU with two
+    warps per problem; every element goes through the same operations in the
+    same order as in the one-warp form, so factors, interchanges and
+    solutions agree bit for bit (Gaussian inputs, where pivots are decided
+    by FP32 comparisons of every candidate)."""
+    batch = 301
+    A = W.general(n, batch, 820 + n)
+    b = W.gaussian(batch * n, 821 + n)
+    out = {}
+    for scope in (g.GLASS_SCOPE_WARP, g.GLASS_SCOPE_BLOCK):
+        dA, dB = to_dev(A), to_dev(b)
+        ipiv, info = zeros_i32(batch * n), zeros_i32(batch)
+        g.check(g.glass_batched_getrf_getrs(n, 1, dA, n, n * n, ipiv, dB, n, n, info, batch, opts_for(scope, 1)))
+        sync()
+        out[scope] = (host(dA), host(ipiv)[:batch * n], host(dB), host(info)[:batch])
+    for a, c in zip(out[g.GLASS_SCOPE_WARP], out[g.GLASS_SCOPE_BLOCK]):
+        assert np.array_equal(a.view(np.uint32) if a.dtype == np.float32 else a,
+                              c.view(np.uint32) if c.dtype == np.float32 else c), n
+
+
 @pytest.mark.parametrize("n", [4, 17, 64])
 def test_trsm_integer_bit_exact(n):
     batch, k = 40, 5
